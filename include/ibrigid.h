@@ -1,0 +1,216 @@
+/*
+ * ibrigid.h -- C ABI of the GB300 (sm_103a) rigid-body immersed-boundary solver.
+ *
+ * The library solves the rigidly constrained Stokes saddle-point system of
+ * Kallemov, Bhalla, Griffith, Donev, "An Immersed Boundary Method for Rigid
+ * Bodies" (arXiv:1505.07865), Sec. III.B, Eq. constrained_Stokes
+ *
+ *     [ A   G  -S~ ] [v     ]   [g]
+ *     [-D   0   0  ] [pi    ] = [h]        A = rho/dt I - eta h^-2 Lap (Eq. A_def)
+ *     [-J   0   0  ] [Lambda]   [W]        W = -K U  (rigid no-slip, Sec. II)
+ *
+ * with S~ = S - vol^-1 1^T for periodic steady Stokes (Sec. III.D, Eq.
+ * constrained_periodic, together with <v> = 0), by flexible GMRES (Sec. V)
+ * right-preconditioned with the Schur-complement preconditioner of Sec. V.A:
+ * an inner GMRES(N_s) Stokes solve preconditioned by the projection
+ * preconditioner P_S (Sec. V.B, Eq. P1_practical) built from geometric
+ * multigrid V-cycles, followed by the approximate mobility solve
+ * M~ Lambda = dU (Eq. mob_subproblem) with the dense analytic M~ of Sec. IV
+ * (Eq. M_tilde_ij), factorised once per geometry (Sec. V.C).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns IBR_OK (0) or a negative IBR_E* code and never
+ *    throws; ibr_last_error() gives a thread-local message for the last
+ *    failure on the calling thread.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Output
+ *    buffers are caller-allocated.  The library owns all device memory of a
+ *    grid and frees it in ibr_destroy_grid.
+ *  - Pointers documented as "device" must point to memory of the CUDA device
+ *    that was current when the grid was created; "host" means pageable or
+ *    pinned host memory.
+ *  - Work is issued on the grid's stream (the cuda_stream given to
+ *    ibr_create_grid, or a library-created stream when NULL).  Entry points
+ *    that return host data synchronise that stream; the op-level entry points
+ *    on device data (ibr_apply_*, ibr_op_*) are asynchronous on that stream.
+ *  - Grid layout: a cell-centred scalar is n[0]*n[1](*n[2]) doubles, x index
+ *    fastest.  Velocity component alpha is stored on the faces normal to
+ *    axis alpha, entry (i,j,k) being the lower face of cell (i,j,k), i.e. at
+ *    (i + 1/2 - delta_{alpha,0}/2, ...) h.  A system vector is
+ *    [v_0 | ... | v_{d-1} | pi | Lambda], Lambda marker-major (i*d + alpha),
+ *    markers in the order bodies were added and, within a body, the order
+ *    given to ibr_set_markers.
+ *  - Sign convention (Sec. III.B): Lambda is the force of the markers on the
+ *    fluid (it enters the momentum equation as +S Lambda); the force and
+ *    torque of a body on the fluid is K^T Lambda, the drag on the body is its
+ *    negative.
+ */
+#ifndef IBRIGID_H
+#define IBRIGID_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define IBR_OK        0
+#define IBR_EINVAL   -1   /* bad argument (size, pointer, option)                 */
+#define IBR_ENOMEM   -2   /* device or host allocation failed                     */
+#define IBR_ENOTCONV -3   /* FGMRES hit max_iters; results are still readable     */
+#define IBR_ETIMEOUT -4   /* time_cap_ms exceeded; results are still readable     */
+#define IBR_ENUMERIC -5   /* NaN/Inf in data or a non-positive pivot in M~        */
+#define IBR_ECUDA    -6   /* a CUDA runtime call failed                           */
+#define IBR_ESTATE   -7   /* call out of order (e.g. solve before markers)        */
+
+/* ---- boundary conditions per axis side (bc[axis][0]=low, [1]=high) -------- */
+#define IBR_PERIODIC 0
+#define IBR_NOSLIP   1
+#define IBR_VELOCITY 2
+
+/* ---- kernels, precisions, kinematics, preconditioner variants ------------- */
+#define IBR_KERNEL_PESKIN4 4   /* 4-point Peskin kernel (Sec. III.A)            */
+#define IBR_FP64  0            /* every step in float64                           */
+#define IBR_MIXED 1            /* FP64 outer FGMRES / matvec / true residual;     */
+                               /* FP32 preconditioner (MG, P_S, inner GMRES,      */
+                               /* spread/interp inside it, M~^-1)                 */
+#define IBR_PRESCRIBED 0       /* body velocity given (Sec. II)                   */
+#define IBR_PC_LOWER 0         /* lower block-triangular Schur preconditioner     */
+#define IBR_PC_FULL  1         /* full Schur preconditioner (steps 1-4, Sec. V.A) */
+#define IBR_MOB_AUTO  0        /* RPY (3-D) / App. B steady form (2-D)            */
+#define IBR_MOB_RPY   1        /* Eq. RPYTensor (+ periodic correction, App. A)   */
+#define IBR_MOB_FIT2D 2        /* App. B Eq. fg_steady_2d                          */
+
+typedef struct ibr_grid ibr_grid;   /* opaque */
+
+typedef struct ibr_solve_opts {
+    double tol;            /* relative residual ||b - A x||_2 / ||b||_2 (true)   */
+    int    restart;        /* FGMRES restart length m                           */
+    int    max_iters;      /* cap on outer iterations (all restarts)            */
+    int    n_s;            /* inner Stokes GMRES iterations N_s (Sec. V.A)      */
+    int    variant;        /* IBR_PC_LOWER or IBR_PC_FULL                       */
+    int    mg_pre;         /* pre-smoothing sweeps per V-cycle level            */
+    int    mg_post;        /* post-smoothing sweeps per V-cycle level           */
+    int    mob_model;      /* IBR_MOB_*                                          */
+    double mob_a_over_h;   /* marker hydrodynamic radius a/h for M~ (0: default) */
+    double mob_coef[9];    /* App. B coefficients a0..a4, b0..b3 (2-D steady)   */
+    double time_cap_ms;    /* <= 0: none                                         */
+} ibr_solve_opts;
+
+typedef struct ibr_solve_info {
+    int    status;         /* same as the return code of ibr_solve_coupled      */
+    int    iters;          /* outer FGMRES iterations                            */
+    int    restarts;       /* completed restart cycles                           */
+    int    ps_applications;/* applications of P_S (the paper's cost unit)      */
+    double rel_res_est;    /* Givens estimate at exit                            */
+    double rel_res_true;   /* recomputed ||b - A x|| / ||b|| in FP64             */
+    double ms_setup;       /* marker binning + M~ build/factor, wall ms          */
+    double ms_solve;       /* FGMRES, wall ms                                    */
+} ibr_solve_info;
+
+/* Fills opts with the defaults: tol 1e-8, restart 50, max_iters 1000, N_s 2,
+ * IBR_PC_LOWER, mg 2/2, IBR_MOB_AUTO, a/h 0 (=1.25 in 3-D, see ibr_solve_coupled),
+ * the library's 2-D coefficient set, no time cap. */
+int ibr_solve_opts_default(ibr_solve_opts* opts);
+
+/* Creates a uniform MAC grid (Sec. III).  dim in {2,3}; n[0..dim-1] cells per
+ * axis (each even, >= 4); L[0..dim-1] box lengths (cubic cells: L[a]/n[a]
+ * equal for all a).  bc[a][s]: only IBR_PERIODIC is accepted by this build.
+ * eta > 0 viscosity; rho, dt >= 0 (rho == 0 or dt == 0: steady Stokes, A =
+ * -eta h^-2 Lap).  kernel: IBR_KERNEL_PESKIN4.  precision: IBR_FP64 or
+ * IBR_MIXED.  cuda_stream: a cudaStream_t or NULL.  On success *out owns the
+ * grid's device memory.  Errors: IBR_EINVAL, IBR_ENOMEM, IBR_ECUDA. */
+int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L,
+                    const int* bc /* dim*2 */, double eta, double rho, double dt,
+                    int kernel, int precision, void* cuda_stream);
+
+/* Adds a rigid body with reference point x_c[dim] and orientation quat[4]
+ * (w,x,y,z; unit; 2-D uses the rotation about z it describes).  kinematics:
+ * IBR_PRESCRIBED.  Writes the body index (0,1,...) to *body_id. */
+int ibr_add_body(ibr_grid* g, const double* x_c, const double* quat, int kinematics, int* body_id);
+
+/* Sets the N markers of a body from body-frame offsets r_body[N*dim] (host).
+ * Lab positions q_i = x_c + Q(quat) r_i are wrapped into [0, L) on periodic
+ * axes.  Marks the geometry dirty: the next solve (or ibr_prepare) rebins the
+ * markers and rebuilds and refactors M~.  N >= 1. */
+int ibr_set_markers(ibr_grid* g, int body_id, const double* r_body, int N);
+
+/* Inhomogeneous boundary data for IBR_VELOCITY faces.  Not supported by this
+ * build (periodic only): returns IBR_EINVAL. */
+int ibr_set_boundary_velocity(ibr_grid* g, int face, const double* values);
+
+/* Runs the geometry set-up now (marker lab positions, kernel weights, the
+ * sorted face-gather lists of S, M~ build and factorisation) with the
+ * mobility options of opts (NULL: defaults). */
+int ibr_prepare(ibr_grid* g, const ibr_solve_opts* opts);
+
+/* Solves the constrained system for prescribed body velocities
+ * body_UO[B*(dim+rot)] (host; per body U then Omega; rot = 1 in 2-D, 3 in
+ * 3-D) with momentum forcing g (NULL: zero; else dim face arrays laid out as
+ * above, on the device if g_on_device != 0, else on the host; for periodic
+ * steady Stokes each component must have zero mean) and h = 0.  FGMRES starts
+ * from x0 = 0 and stops when the true relative residual is <= opts->tol.
+ * The solution stays resident (ibr_get_forces / ibr_get_fields / ibr_get_solution).
+ * Returns IBR_OK, IBR_ENOTCONV, IBR_ETIMEOUT (results readable), or an error. */
+int ibr_solve_coupled(ibr_grid* g, const double* body_UO, const double* gforce, int g_on_device,
+                      const ibr_solve_opts* opts, ibr_solve_info* info);
+
+/* Copies the marker forces Lambda[N*dim] (may be NULL) and the per-body
+ * K^T Lambda = [force; torque] of each body on the fluid, body_FT[B*(dim+rot)]
+ * (may be NULL), of the last solve to host memory. */
+int ibr_get_forces(ibr_grid* g, double* Lambda, double* body_FT);
+
+/* Copies the velocity (dim face arrays, concatenated) and pressure of the last
+ * solve.  to_device != 0: v and p are device pointers; else host. */
+int ibr_get_fields(ibr_grid* g, double* v, double* p, int to_device);
+
+/* Total length of a system vector, (dim+1)*cells + dim*N, and the marker and
+ * body counts (any output pointer may be NULL). */
+int ibr_sizes(const ibr_grid* g, long long* system_len, int* n_markers, int* n_bodies);
+
+/* ---- op-level entry points (device pointers, FP64, asynchronous) ----------
+ * These expose each step of the hot path separately so each can be checked
+ * against an independent implementation.  They require ibr_prepare (or a
+ * solve) after the last ibr_set_markers. */
+
+/* y = (system matrix) x for the full constrained operator above, x and y of
+ * length ibr_sizes().system_len (Sec. III.B / III.D). */
+int ibr_apply_system(ibr_grid* g, const double* x, double* y);
+
+/* f = S~ Lambda (Sec. III.A Eq. S_unweighted; minus vol^-1 sum Lambda for
+ * periodic steady Stokes, Sec. III.D).  lam[N*dim], f: dim face arrays. */
+int ibr_op_spread(ibr_grid* g, const double* lam, double* f);
+
+/* U = J v (Sec. III.A).  v: dim face arrays, U[N*dim]. */
+int ibr_op_interp(ibr_grid* g, const double* v, double* U);
+
+/* V = K UO (marker velocities [N*dim]) and FT = K^T Lambda ([B*(dim+rot)]). */
+int ibr_op_rigid(ibr_grid* g, const double* UO, double* V);
+int ibr_op_rigid_T(ibr_grid* g, const double* lam, double* FT);
+
+/* Copies the dense M~ block of body b (row-major, (dim N_b)^2 doubles,
+ * Eq. M_tilde_ij) into out. */
+int ibr_op_mtilde(ibr_grid* g, int body, double* out);
+
+/* out = M~^-1 rhs (block diagonal over bodies, [N*dim]) with the factorised
+ * M~ in the grid's preconditioner precision. */
+int ibr_op_mtilde_solve(ibr_grid* g, const double* rhs, double* out);
+
+/* One application z = P_S^-1 r of the Stokes preconditioner (Sec. V.B,
+ * Eq. P1_practical) in the preconditioner precision, r and z of length
+ * (dim+1)*cells (velocity then pressure). */
+int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
+
+/* k V-cycles of the scalar multigrid for (sigma I - kappa Delta_h) u = f on the
+ * cell grid (periodic), starting from u (in/out).  sigma = 0 requires mean-zero
+ * f and returns mean-zero u. */
+int ibr_op_vcycle(ibr_grid* g, double sigma, double kappa, const double* f, double* u, int k);
+
+/* Destroys the grid and frees its device memory. NULL is accepted. */
+int ibr_destroy_grid(ibr_grid* g);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* ibr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBRIGID_H */

@@ -69,6 +69,21 @@ def stokes_solve(grid, f, hd=None):
     return v, p
 
 
+def helmholtz_solve(grid, sigma, kappa, f):
+    """Exact (sigma I - kappa h^-2 Lap) u = f on the periodic cell grid; for
+    sigma == 0 the mean of f is ignored and <u> = 0 (the scalar operators of
+    the V-cycles in P_S, Sec. V.B)."""
+    _, _, _, DG = _symbols(grid)
+    sym = sigma - kappa * DG  # DG = -h^-2 sum 4 sin^2
+    zero = tuple([0] * grid.d)
+    fh = np.fft.fftn(f)
+    if sigma == 0.0:
+        sym = sym.copy()
+        sym[zero] = 1.0
+        fh[zero] = 0.0
+    return np.real(np.fft.ifftn(fh / sym))
+
+
 def mobility_true(prob):
     """The true marker mobility M = J L^-1 S~ (Eq. mob_def), dense, formed
     column by column with exact DFT Stokes solves."""

@@ -1,0 +1,269 @@
+"""ctypes binding of libibrigid (include/ibrigid.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name (without
+the ``ibr_`` prefix).  Device arrays are passed as torch CUDA tensors (their
+``data_ptr()``), host arrays as NumPy float64 arrays.  Any non-zero status
+raises ``IbrError`` carrying ``ibr_last_error()``; ``IBR_ENOTCONV`` and
+``IBR_ETIMEOUT`` are returned in ``SolveInfo.status`` instead (the solution is
+still readable) unless ``raise_on_notconv`` is set.
+
+There is no fallback: if the shared library is missing, importing this module
+raises ``ImportError`` telling how to build it.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libibrigid.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, ETIMEOUT, ENUMERIC, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PERIODIC, NOSLIP, VELOCITY = 0, 1, 2
+KERNEL_PESKIN4 = 4
+FP64, MIXED = 0, 1
+PRESCRIBED = 0
+PC_LOWER, PC_FULL = 0, 1
+MOB_AUTO, MOB_RPY, MOB_FIT2D = 0, 1, 2
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("restart", ctypes.c_int),
+        ("max_iters", ctypes.c_int),
+        ("n_s", ctypes.c_int),
+        ("variant", ctypes.c_int),
+        ("mg_pre", ctypes.c_int),
+        ("mg_post", ctypes.c_int),
+        ("mob_model", ctypes.c_int),
+        ("mob_a_over_h", ctypes.c_double),
+        ("mob_coef", ctypes.c_double * 9),
+        ("time_cap_ms", ctypes.c_double),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("ps_applications", ctypes.c_int),
+        ("rel_res_est", ctypes.c_double),
+        ("rel_res_true", ctypes.c_double),
+        ("ms_setup", ctypes.c_double),
+        ("ms_solve", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IbrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+if not os.path.exists(LIBPATH):
+    raise ImportError(f"{LIBPATH} is not built: run `python -m paper_1505_07865_gb300.build` "
+                      "(or __graft_entry__.build()) first")
+
+_lib = ctypes.CDLL(LIBPATH)
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "ibr_solve_opts_default": (ctypes.c_int, [ctypes.POINTER(SolveOpts)]),
+    "ibr_create_grid": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I, _D, _I, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P]),
+    "ibr_add_body": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _I]),
+    "ibr_set_markers": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_int]),
+    "ibr_set_boundary_velocity": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "ibr_prepare": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts)]),
+    "ibr_solve_coupled": (ctypes.c_int, [_P, _D, _P, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                                         ctypes.POINTER(SolveInfo)]),
+    "ibr_get_forces": (ctypes.c_int, [_P, _D, _D]),
+    "ibr_get_fields": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "ibr_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), _I, _I]),
+    "ibr_apply_system": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_spread": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_interp": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_rigid": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_rigid_T": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_mtilde": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "ibr_op_mtilde_solve": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_stokes_pc": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_vcycle": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_int]),
+    "ibr_destroy_grid": (ctypes.c_int, [_P]),
+    "ibr_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def last_error():
+    return _lib.ibr_last_error().decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise IbrError(rc, last_error())
+    return rc
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _host(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _dev(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch.float64" or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def solve_opts_default():
+    o = SolveOpts()
+    _check(_lib.ibr_solve_opts_default(ctypes.byref(o)))
+    return o
+
+
+def create_grid(dim, n, L, bc=None, eta=1.0, rho=0.0, dt=0.0, kernel=KERNEL_PESKIN4, precision=MIXED,
+                stream=None):
+    k = max(3, len(n), len(L), int(dim))
+    n_arr = (ctypes.c_int * k)(*(list(n) + [0] * (k - len(n))))
+    L_arr = (ctypes.c_double * k)(*(list(L) + [0.0] * (k - len(L))))
+    if bc is None:
+        bc = [PERIODIC] * (2 * k)
+    bc_arr = (ctypes.c_int * (2 * k))(*(list(bc) + [0] * (2 * k - len(bc))))
+    h = _P()
+    s = None if stream is None else _P(int(stream))
+    _check(_lib.ibr_create_grid(ctypes.byref(h), int(dim), n_arr, L_arr, bc_arr, float(eta), float(rho), float(dt),
+                                int(kernel), int(precision), s))
+    return h
+
+
+def add_body(grid, x_c, quat=None, kinematics=PRESCRIBED):
+    xc = _host(x_c)
+    q = None if quat is None else _dptr(_host(quat, 4))
+    bid = ctypes.c_int()
+    _check(_lib.ibr_add_body(grid, _dptr(xc), q, int(kinematics), ctypes.byref(bid)))
+    return bid.value
+
+
+def set_markers(grid, body_id, r_body):
+    r = _host(r_body)
+    N = r.shape[0] if r.ndim == 2 else r.size
+    _check(_lib.ibr_set_markers(grid, int(body_id), _dptr(r), int(N)))
+
+
+def set_boundary_velocity(grid, face, values):
+    v = _host(values)
+    _check(_lib.ibr_set_boundary_velocity(grid, int(face), _dptr(v)))
+
+
+def prepare(grid, opts=None):
+    _check(_lib.ibr_prepare(grid, None if opts is None else ctypes.byref(opts)))
+
+
+def solve_coupled(grid, body_UO, g=None, opts=None, raise_on_notconv=False):
+    uo = _host(body_UO)
+    info = SolveInfo()
+    if g is None:
+        gp, on_dev = None, 0
+    elif hasattr(g, "is_cuda"):
+        gp, on_dev = _dev(g), 1
+    else:
+        garr = _host(g)
+        gp, on_dev = garr.ctypes.data_as(_P), 0
+    rc = _lib.ibr_solve_coupled(grid, _dptr(uo), gp, on_dev, None if opts is None else ctypes.byref(opts),
+                                ctypes.byref(info))
+    if rc in (ENOTCONV, ETIMEOUT) and not raise_on_notconv:
+        return info
+    _check(rc)
+    return info
+
+
+def sizes(grid):
+    ln = ctypes.c_longlong()
+    nm = ctypes.c_int()
+    nb = ctypes.c_int()
+    _check(_lib.ibr_sizes(grid, ctypes.byref(ln), ctypes.byref(nm), ctypes.byref(nb)))
+    return ln.value, nm.value, nb.value
+
+
+def get_forces(grid, dim):
+    _, N, B = sizes(grid)
+    lam = np.zeros(N * dim)
+    ft = np.zeros(B * (dim + (1 if dim == 2 else 3)))
+    _check(_lib.ibr_get_forces(grid, _dptr(lam), _dptr(ft)))
+    return lam.reshape(N, dim), ft.reshape(B, -1)
+
+
+def get_fields(grid, v=None, p=None):
+    """Copies v (dim face arrays, concatenated) and p into the given buffers:
+    NumPy arrays (host) or torch CUDA tensors (device, both)."""
+    if v is not None and hasattr(v, "is_cuda"):
+        _check(_lib.ibr_get_fields(grid, _dev(v), None if p is None else _dev(p), 1))
+    else:
+        vp = None if v is None else v.ctypes.data_as(_P)
+        pp = None if p is None else p.ctypes.data_as(_P)
+        _check(_lib.ibr_get_fields(grid, vp, pp, 0))
+    return v, p
+
+
+def apply_system(grid, x, y):
+    _check(_lib.ibr_apply_system(grid, _dev(x), _dev(y)))
+
+
+def op_spread(grid, lam, f):
+    _check(_lib.ibr_op_spread(grid, _dev(lam), _dev(f)))
+
+
+def op_interp(grid, v, U):
+    _check(_lib.ibr_op_interp(grid, _dev(v), _dev(U)))
+
+
+def op_rigid(grid, UO, V):
+    _check(_lib.ibr_op_rigid(grid, _dev(UO), _dev(V)))
+
+
+def op_rigid_T(grid, lam, FT):
+    _check(_lib.ibr_op_rigid_T(grid, _dev(lam), _dev(FT)))
+
+
+def op_mtilde(grid, body, out):
+    _check(_lib.ibr_op_mtilde(grid, int(body), _dev(out)))
+
+
+def op_mtilde_solve(grid, rhs, out):
+    _check(_lib.ibr_op_mtilde_solve(grid, _dev(rhs), _dev(out)))
+
+
+def op_stokes_pc(grid, r, z):
+    _check(_lib.ibr_op_stokes_pc(grid, _dev(r), _dev(z)))
+
+
+def op_vcycle(grid, sigma, kappa, f, u, k):
+    _check(_lib.ibr_op_vcycle(grid, float(sigma), float(kappa), _dev(f), _dev(u), int(k)))
+
+
+def destroy_grid(grid):
+    _check(_lib.ibr_destroy_grid(grid))

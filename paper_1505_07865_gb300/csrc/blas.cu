@@ -1,0 +1,372 @@
+// Vector kernels of the Krylov solvers (Sec. V: FGMRES outer, GMRES(N_s) inner).
+// Dot products use a fixed grid and a fixed-order final sum, so results are
+// bitwise reproducible run to run.
+#include "ibr_internal.cuh"
+
+namespace ibr {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-reduce NV values per thread into out[0..NV) by thread 0 (double)
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* out) {
+    __shared__ double sm[RED_THREADS / 32][NV];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = warp_sum(v[q]);
+        if (lane == 0) sm[wid][q] = s;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = lane < RED_THREADS / 32 ? sm[lane][q] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) out[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+__global__ void k_scale_copy(long long n, const double* __restrict__ sc, int invert, const T* __restrict__ x,
+                             T* __restrict__ y) {
+    double s = *sc;
+    T a = (T)(invert ? (s != 0.0 ? 1.0 / s : 0.0) : s);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(long long n, const Ti* __restrict__ x, To* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (To)x[i];
+}
+
+// partial[blk*k + j] = sum over this block's elements of V_j . w, j in [j0, j0+CH)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(long long n, const T* __restrict__ V, long long ld, int k,
+                                                      const T* __restrict__ w, double* __restrict__ partial) {
+    for (int j0 = 0; j0 < k; j0 += MDOT_CHUNK) {
+        double acc[MDOT_CHUNK];
+        T tacc[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
+        int nq = min(MDOT_CHUNK, k - j0);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            T wi = w[i];
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q)
+                if (q < nq) tacc[q] += V[(long long)(j0 + q) * ld + i] * wi;
+        }
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q];
+        __shared__ double outv[MDOT_CHUNK];
+        block_sum<MDOT_CHUNK>(acc, outv);
+        if (threadIdx.x < nq) partial[(long long)blockIdx.x * k + j0 + threadIdx.x] = outv[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// out[j] = sum_blk partial[blk*k + j]   (grid: k blocks)
+__global__ void k_finalize(const double* __restrict__ partial, int nblk, int k, double* __restrict__ out) {
+    int j = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(long long)b * k + j];
+    double v[1] = {s};
+    __shared__ double o[1];
+    block_sum<1>(v, o);
+    if (threadIdx.x == 0) out[j] = o[0];
+}
+
+// w -= sum_j h_j V_j ; then partial dots V_j . w (second CGS pass)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_update_mdot(long long n, const T* __restrict__ V, long long ld,
+                                                             int k, const double* __restrict__ h,
+                                                             T* __restrict__ w, double* __restrict__ partial) {
+    __shared__ double hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        w[i] = w[i] - s;
+    }
+    // the elements this thread wrote are re-read by the same thread below
+    for (int j0 = 0; j0 < k; j0 += MDOT_CHUNK) {
+        double acc[MDOT_CHUNK];
+        T tacc[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
+        int nq = min(MDOT_CHUNK, k - j0);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            T wi = w[i];
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q)
+                if (q < nq) tacc[q] += V[(long long)(j0 + q) * ld + i] * wi;
+        }
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q];
+        __shared__ double outv[MDOT_CHUNK];
+        block_sum<MDOT_CHUNK>(acc, outv);
+        if (threadIdx.x < nq) partial[(long long)blockIdx.x * k + j0 + threadIdx.x] = outv[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// w -= sum_j h_j V_j ; partial |w|^2
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_update_norm(long long n, const T* __restrict__ V, long long ld,
+                                                             int k, const double* __restrict__ h,
+                                                             T* __restrict__ w, double* __restrict__ partial) {
+    __shared__ double hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    T acc = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        T wi = w[i] - s;
+        w[i] = wi;
+        acc += wi * wi;
+    }
+    double v[1] = {(double)acc};
+    __shared__ double o[1];
+    block_sum<1>(v, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = o[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_norm2(long long n, const T* __restrict__ w,
+                                                       double* __restrict__ partial) {
+    T acc = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T wi = w[i];
+        acc += wi * wi;
+    }
+    double v[1] = {(double)acc};
+    __shared__ double o[1];
+    block_sum<1>(v, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = o[0];
+}
+
+template <typename T, typename Tz>
+__global__ void k_combine(long long n, const Tz* __restrict__ Z, long long ld, int k, const double* __restrict__ y,
+                          T* __restrict__ x, int accumulate) {
+    __shared__ double ys[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double s = accumulate ? (double)x[i] : 0.0;
+        for (int j = 0; j < k; ++j) s += ys[j] * (double)Z[(long long)j * ld + i];
+        x[i] = (T)s;
+    }
+}
+
+// partial[blk*C + c] = sum of block c's elements handled by this CTA
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_block_sums(long long m, int C, const T* __restrict__ x,
+                                                            double* __restrict__ partial) {
+    for (int c = 0; c < C; ++c) {
+        double acc = 0.0;
+        T tacc = T(0);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+             i += (long long)gridDim.x * blockDim.x)
+            tacc += x[(long long)c * m + i];
+        acc = (double)tacc;
+        double v[1] = {acc};
+        __shared__ double o[1];
+        block_sum<1>(v, o);
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * C + c] = o[0];
+    }
+}
+
+__global__ void k_scale_vals(int C, double s, double* v) {
+    int c = threadIdx.x;
+    if (c < C) v[c] *= s;
+}
+
+template <typename T>
+__global__ void k_subtract_means(long long m, int C, T* __restrict__ x, const double* __restrict__ means) {
+    long long n = m * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] -= (T)means[i / m];
+}
+
+// ---- small FP64 bookkeeping kernels (one thread) --------------------------
+__global__ void k_arnoldi_column(double* H, int ldh, const double* h1, const double* h2, const double* nrm2, int j,
+                                 double* cs, double* sn, double* gv, double* res_out, double* inv_norm_out) {
+    double* col = H + (long long)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
+    double nr = sqrt(fmax(*nrm2, 0.0));
+    col[j + 1] = nr;
+    *inv_norm_out = nr > 0.0 ? 1.0 / nr : 0.0;
+    for (int i = 0; i < j; ++i) {
+        double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    double a = col[j], b = col[j + 1];
+    double r = hypot(a, b);
+    double c = 1.0, s = 0.0;
+    if (r > 0.0) {
+        c = a / r;
+        s = b / r;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    double gj = gv[j];
+    gv[j] = c * gj;
+    gv[j + 1] = -s * gj;
+    *res_out = fabs(gv[j + 1]);
+}
+
+__global__ void k_givens_init(const double* nrm2, double* gv, int m1, double* beta_out, double* inv_beta_out) {
+    double b = sqrt(fmax(*nrm2, 0.0));
+    for (int i = 0; i < m1; ++i) gv[i] = 0.0;
+    gv[0] = b;
+    if (beta_out) *beta_out = b;
+    *inv_beta_out = b > 0.0 ? 1.0 / b : 0.0;
+}
+
+__global__ void k_hess_solve(const double* H, int ldh, const double* gv, int k, double* y) {
+    for (int i = k - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int l = i + 1; l < k; ++l) s -= H[(long long)l * ldh + i] * y[l];
+        double d = H[(long long)i * ldh + i];
+        y[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+inline int blocks_for(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 4 * 152 * 4) b = 4 * 152 * 4;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+template <typename T>
+void vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStream_t s) {
+    k_axpby<T><<<blocks_for(n), 256, 0, s>>>(n, (T)a, x, (T)b, y);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void vec_scale_copy(long long n, const double* scale_dev, bool invert, const T* x, T* y, cudaStream_t s) {
+    k_scale_copy<T><<<blocks_for(n), 256, 0, s>>>(n, scale_dev, invert ? 1 : 0, x, y);
+    IBR_CHECK_LAUNCH();
+}
+template <typename Ti, typename To>
+void vec_convert(long long n, const Ti* x, To* y, cudaStream_t s) {
+    k_convert<Ti, To><<<blocks_for(n), 256, 0, s>>>(n, x, y);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void mdot(long long n, const T* V, long long ld, int k, const T* w, double* partial, double* out, cudaStream_t s) {
+    k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial);
+    IBR_CHECK_LAUNCH();
+    k_finalize<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k, out);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void update_mdot(long long n, const T* V, long long ld, int k, const double* h, T* w, double* partial, double* out,
+                 cudaStream_t s) {
+    k_update_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h, w, partial);
+    IBR_CHECK_LAUNCH();
+    k_finalize<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k, out);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void update_norm2(long long n, const T* V, long long ld, int k, const double* h, T* w, double* partial, double* out,
+                  cudaStream_t s) {
+    k_update_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h, w, partial);
+    IBR_CHECK_LAUNCH();
+    k_finalize<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, 1, out);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void norm2(long long n, const T* w, double* partial, double* out, cudaStream_t s) {
+    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w, partial);
+    IBR_CHECK_LAUNCH();
+    k_finalize<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, 1, out);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T, typename Tz>
+void combine(long long n, const Tz* Z, long long ld, int k, const double* y, T* x, bool accumulate, cudaStream_t s) {
+    k_combine<T, Tz><<<blocks_for(n), 256, 0, s>>>(n, Z, ld, k, y, x, accumulate ? 1 : 0);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void block_means(long long m, int C, const T* x, double* partial, double* out, cudaStream_t s) {
+    k_block_sums<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(m, C, x, partial);
+    IBR_CHECK_LAUNCH();
+    k_finalize<<<C, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, C, out);
+    IBR_CHECK_LAUNCH();
+    k_scale_vals<<<1, 32, 0, s>>>(C, 1.0 / (double)m, out);
+    IBR_CHECK_LAUNCH();
+}
+template <typename T>
+void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t s) {
+    k_subtract_means<T><<<blocks_for(m * C), 256, 0, s>>>(m, C, x, means);
+    IBR_CHECK_LAUNCH();
+}
+
+void arnoldi_column(double* H, int ldh, const double* h1, const double* h2, const double* nrm2, int j, double* cs,
+                    double* sn, double* gv, double* res_out, double* inv_norm_out, cudaStream_t s) {
+    k_arnoldi_column<<<1, 1, 0, s>>>(H, ldh, h1, h2, nrm2, j, cs, sn, gv, res_out, inv_norm_out);
+    IBR_CHECK_LAUNCH();
+}
+void givens_init(const double* nrm2, double* gv, int m1, double* beta_out, double* inv_beta_out, cudaStream_t s) {
+    k_givens_init<<<1, 1, 0, s>>>(nrm2, gv, m1, beta_out, inv_beta_out);
+    IBR_CHECK_LAUNCH();
+}
+void hess_solve(const double* H, int ldh, const double* gv, int k, double* y, cudaStream_t s) {
+    k_hess_solve<<<1, 1, 0, s>>>(H, ldh, gv, k, y);
+    IBR_CHECK_LAUNCH();
+}
+
+#define IBR_INST(T)                                                                                              \
+    template void vec_axpby<T>(long long, double, const T*, double, T*, cudaStream_t);                          \
+    template void vec_scale_copy<T>(long long, const double*, bool, const T*, T*, cudaStream_t);                \
+    template void mdot<T>(long long, const T*, long long, int, const T*, double*, double*, cudaStream_t);       \
+    template void update_mdot<T>(long long, const T*, long long, int, const double*, T*, double*, double*,      \
+                                 cudaStream_t);                                                                 \
+    template void update_norm2<T>(long long, const T*, long long, int, const double*, T*, double*, double*,     \
+                                  cudaStream_t);                                                                \
+    template void norm2<T>(long long, const T*, double*, double*, cudaStream_t);                                \
+    template void block_means<T>(long long, int, const T*, double*, double*, cudaStream_t);                     \
+    template void subtract_means<T>(long long, int, T*, const double*, cudaStream_t);
+IBR_INST(double)
+IBR_INST(float)
+#undef IBR_INST
+template void vec_convert<double, float>(long long, const double*, float*, cudaStream_t);
+template void vec_convert<float, double>(long long, const float*, double*, cudaStream_t);
+template void vec_convert<double, double>(long long, const double*, double*, cudaStream_t);
+template void combine<double, double>(long long, const double*, long long, int, const double*, double*, bool,
+                                      cudaStream_t);
+template void combine<float, float>(long long, const float*, long long, int, const double*, float*, bool,
+                                    cudaStream_t);
+template void combine<double, float>(long long, const float*, long long, int, const double*, double*, bool,
+                                     cudaStream_t);
+
+}  // namespace ibr

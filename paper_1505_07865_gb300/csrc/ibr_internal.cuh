@@ -1,0 +1,191 @@
+// Internal declarations shared by the translation units of libibrigid.
+// Device kernels are launched only through the host wrappers declared here.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "../../include/ibrigid.h"
+
+namespace ibr {
+
+// ---------------------------------------------------------------------------
+// errors
+void set_error(const std::string& msg);
+struct Error {
+    int code;
+    std::string msg;
+};
+#define IBR_CUDA_TRY(expr)                                                         \
+    do {                                                                          \
+        cudaError_t _e = (expr);                                                  \
+        if (_e != cudaSuccess)                                                    \
+            throw ::ibr::Error{IBR_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
+    } while (0)
+#define IBR_CHECK_LAUNCH() IBR_CUDA_TRY(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// periodic cell grid (x fastest); n2 == 1 in 2-D
+struct Geo {
+    int d;
+    int n0, n1, n2;
+    long long ncell;
+    double h;
+};
+
+inline Geo make_geo(int d, const int* n, double h) {
+    Geo g;
+    g.d = d;
+    g.n0 = n[0];
+    g.n1 = n[1];
+    g.n2 = d == 3 ? n[2] : 1;
+    g.ncell = (long long)g.n0 * g.n1 * g.n2;
+    g.h = h;
+    return g;
+}
+
+inline int grid_1d(long long work, int block) {
+    long long b = (work + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > 2147483647LL) b = 2147483647LL;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// stencil.cu -- MAC operators and multigrid (templated on scalar T)
+// y = [A v + G p + shift ; -D v] for the unconstrained Stokes operator.
+template <typename T>
+void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, const double* shift_dev,
+                  cudaStream_t s);
+// red-black Gauss-Seidel half sweep on C stacked scalar fields:
+// (sigma u - kappa Delta_h u) = f
+template <typename T>
+void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int color, bool zero_init,
+               cudaStream_t s);
+template <typename T>
+void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
+                          double kappa, cudaStream_t s);
+template <typename T>
+void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, cudaStream_t s);
+template <typename T>
+void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int sweeps,
+                     cudaStream_t s);
+// q = -D y - hd ; (P_S middle factor, Sec. V.B)
+template <typename T>
+void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s);
+// v = y + h^2 G phi ; pi = c_q q + c_phi phi   (P_S first factor)
+template <typename T>
+void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double c_q, double c_phi,
+               cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// blas.cu -- vector kernels; dots reduce deterministically (fixed blocks)
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int MDOT_CHUNK = 8;
+template <typename T>
+void vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStream_t s);   // y = a x + b y
+template <typename T>
+void vec_scale_copy(long long n, const double* scale_dev, bool invert, const T* x, T* y,
+                    cudaStream_t s);  // y = x * (invert ? 1/scale : scale)
+template <typename Ti, typename To>
+void vec_convert(long long n, const Ti* x, To* y, cudaStream_t s);
+// partial dots of w against k vectors V + j*ld, summed into out[0..k) (double)
+template <typename T>
+void mdot(long long n, const T* V, long long ld, int k, const T* w, double* partial, double* out,
+          cudaStream_t s);
+// w -= sum_j h[j] V_j, then out[j] = V_j . w (CGS2 second pass); h device
+template <typename T>
+void update_mdot(long long n, const T* V, long long ld, int k, const double* h, T* w, double* partial,
+                 double* out, cudaStream_t s);
+// w -= sum_j h[j] V_j, then out[0] = w . w
+template <typename T>
+void update_norm2(long long n, const T* V, long long ld, int k, const double* h, T* w, double* partial,
+                  double* out, cudaStream_t s);
+template <typename T>
+void norm2(long long n, const T* w, double* partial, double* out, cudaStream_t s);
+// x (+)= sum_j y[j] Z_j  (y device)
+template <typename T, typename Tz>
+void combine(long long n, const Tz* Z, long long ld, int k, const double* y, T* x, bool accumulate,
+             cudaStream_t s);
+// means of C consecutive blocks of length m (partial sums, double), then
+// x_c -= mean_c for the blocks selected by mask
+template <typename T>
+void block_means(long long m, int C, const T* x, double* partial, double* out, cudaStream_t s);
+template <typename T>
+void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t s);
+
+// small single-thread kernels for the Arnoldi/Givens bookkeeping (FP64)
+// H column j (k = j+2 entries) assembled from h1 + h2 and the norm; Givens
+// rotations applied, new rotation formed, res_out = |g[j+1]|.
+void arnoldi_column(double* H, int ldh, const double* h1, const double* h2, const double* nrm2, int j,
+                    double* cs, double* sn, double* gv, double* res_out, double* inv_norm_out,
+                    cudaStream_t s);
+// g = [beta, 0, ...]; beta from nrm2 (sqrt), inv_beta out
+void givens_init(const double* nrm2, double* gv, int m1, double* beta_out, double* inv_beta_out,
+                 cudaStream_t s);
+void hess_solve(const double* H, int ldh, const double* gv, int k, double* y, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// ib.cu -- markers, kernel weights, spread gather lists, J, S, K, K^T
+struct MarkerData {
+    int N = 0;
+    int B = 0;
+    double* q = nullptr;        // [N][d] lab positions (wrapped)
+    double* rel = nullptr;      // [N][d] q - X_body (unwrapped lever arm)
+    int* body = nullptr;        // [N]
+    int* body_start = nullptr;  // [B+1]
+    int* base = nullptr;        // [N][d][d] first node of the 4-wide window, comp alpha, axis beta
+    double* w64 = nullptr;      // [N][d][d][4]
+    float* w32 = nullptr;       // [N][d][d][4]
+    // face-major gather lists of S: faces F, entries E
+    long long F = 0, E = 0;
+    long long* face = nullptr;  // [F] alpha*ncell + cell
+    int* off = nullptr;         // [F+1]
+    int* ent_m = nullptr;       // [E] marker*d + alpha
+    double* ent_w64 = nullptr;  // [E]
+    float* ent_w32 = nullptr;   // [E]
+};
+void markers_positions(int d, int N, const double* rbody, const int* body, const double* xc_R /*[B][12]*/,
+                       const double* Lbox, double* q, double* rel, cudaStream_t s);
+void markers_weights(const Geo& g, int N, const double* q, int* base, double* w64, float* w32,
+                     cudaStream_t s);
+// builds the face-major gather lists (allocates md.face/off/ent_* on device)
+void markers_build_gather(const Geo& g, MarkerData& md, cudaStream_t s);
+// y[face] += scale * sum w * lam   (no atomics; one thread per touched face)
+template <typename T>
+void spread_gather(const MarkerData& md, const T* lam, T* y, double scale, cudaStream_t s);
+// out[i*d+a] = sign * (J v)_i^a + (add ? add_scale * add[i*d+a] : 0)
+template <typename T, typename Tadd>
+void interp(const Geo& g, const MarkerData& md, const T* v, T* out, double sign, const Tadd* add,
+            cudaStream_t s, double add_scale);
+// shift[a] = scale * sum_i lam[i*d+a]  (double, a < d)
+template <typename T>
+void lam_sum(int d, int N, const T* lam, double scale, double* shift, cudaStream_t s);
+void rigid_K(int d, int N, const double* rel, const int* body, const double* UO, double* V, double sign,
+             cudaStream_t s);
+void rigid_KT(int d, int B, const int* body_start, const double* rel, const double* lam, double* FT,
+              cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// dense.cu -- approximate mobility blocks
+struct MobParams {
+    int model;        // IBR_MOB_RPY or IBR_MOB_FIT2D
+    double eta, h, l, a;
+    double corr;      // periodic correction subtracted from f (3-D)
+    double coef[9];
+};
+void mtilde_build(int d, int Nb, const double* rel_b, const MobParams& p, double* M, cudaStream_t s);
+// in place: M (n x n, row-major, SPD) -> M^-1 (full symmetric).  info_dev[0]
+// set to (k+1) if the k-th pivot is <= min_pivot.  work >= n*n.
+template <typename T>
+void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStream_t s);
+template <typename Ti, typename To>
+void mat_convert(long long n, const Ti* a, To* b, cudaStream_t s);
+// out[r] = sum_c Minv_b[r][c] rhs[c] for each body block (offsets in elements)
+template <typename T, typename Tv>
+void blockdiag_gemv(int B, const long long* moff_dev, const int* roff_dev, int max_rows, const T* Mall,
+                    const Tv* rhs, Tv* out, cudaStream_t s);
+
+}  // namespace ibr

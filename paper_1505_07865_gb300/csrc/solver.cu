@@ -1,0 +1,1093 @@
+// Host orchestration and the C ABI of libibrigid.
+//
+// Outer solver: right-preconditioned flexible GMRES in FP64 on the
+// constrained system (Sec. V), CGS2 Arnoldi and Givens rotations on the
+// device, true residual recomputed at every restart and at exit.
+// Preconditioner: the Schur-complement preconditioner of Sec. V.A
+//   1. inner GMRES(N_s) on the unconstrained Stokes system, each step
+//      preconditioned by P_S (Sec. V.B, Eq. P1_practical) = one vector
+//      V-cycle for A~^-1, the divergence, one scalar V-cycle for L~p^-1,
+//      the gradient correction and B~^-1;
+//   2. dU = -(J v + W);  3. Lambda = M~^-1 dU (Eq. mob_subproblem);
+//   4. (full variant) a second inner solve with g + S~ Lambda.
+// The preconditioner runs in FP32 (IBR_MIXED) or FP64 (IBR_FP64).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ibr_internal.cuh"
+
+namespace ibr {
+static thread_local std::string g_last_error;
+void set_error(const std::string& m) { g_last_error = m; }
+}  // namespace ibr
+
+using namespace ibr;
+
+namespace {
+
+template <typename T>
+T* dalloc(size_t n) {
+    T* p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error{IBR_ENOMEM, std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) +
+                                    " bytes failed: " + cudaGetErrorString(e)};
+    }
+    return p;
+}
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// geometric multigrid on periodic cell grids (scalar fields, C stacked)
+template <typename T>
+struct Multigrid {
+    std::vector<Geo> lev;
+    std::vector<T*> u, f;  // index 0 unused (caller's buffers)
+    int cmax = 0;
+    int coarse_sweeps = 40;
+
+    static bool can_coarsen(const Geo& g) {
+        int ns[3] = {g.n0, g.n1, g.n2};
+        // the coarse grid must stay even on every axis (red-black ordering)
+        for (int a = 0; a < g.d; ++a)
+            if (ns[a] % 4 != 0) return false;
+        return g.ncell > 64;
+    }
+    void init(const Geo& g0, int cmax_) {
+        release();
+        cmax = cmax_;
+        lev.push_back(g0);
+        u.push_back(nullptr);
+        f.push_back(nullptr);
+        Geo g = g0;
+        while (can_coarsen(g)) {
+            Geo c = g;
+            c.n0 /= 2;
+            c.n1 /= 2;
+            if (g.d == 3) c.n2 /= 2;
+            c.ncell = (long long)c.n0 * c.n1 * c.n2;
+            c.h = g.h * 2.0;
+            lev.push_back(c);
+            u.push_back(dalloc<T>((size_t)cmax * c.ncell));
+            f.push_back(dalloc<T>((size_t)cmax * c.ncell));
+            g = c;
+        }
+        const Geo& cg = lev.back();
+        int nmax = std::max(cg.n0, std::max(cg.n1, cg.n2));
+        coarse_sweeps = std::max(20, 2 * nmax * nmax);
+    }
+    void release() {
+        for (auto& p : u) dfree(p);
+        for (auto& p : f) dfree(p);
+        u.clear();
+        f.clear();
+        lev.clear();
+    }
+    // one V-cycle for (sigma I - kappa Delta_h) u0 = f0 (C stacked fields)
+    void vcycle(T* u0, const T* f0, int C, double sigma, double kappa, bool zero_start, int pre, int post,
+                cudaStream_t s) {
+        int L = (int)lev.size();
+        std::vector<T*> U(L);
+        std::vector<const T*> F(L);
+        U[0] = u0;
+        F[0] = f0;
+        for (int l = 1; l < L; ++l) {
+            U[l] = u[l];
+            F[l] = f[l];
+        }
+        for (int l = 0; l + 1 < L; ++l) {
+            bool zs = (l > 0) || zero_start;
+            if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(T) * C * lev[l].ncell, s));
+            for (int it = 0; it < pre; ++it) {
+                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 0, zs && it == 0, s);
+                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 1, false, s);
+            }
+            mg_residual_restrict<T>(lev[l], lev[l + 1], U[l], F[l], f[l + 1], C, sigma, kappa, s);
+        }
+        if (L == 1 && !zero_start) {
+            // single-level grid: smooth only
+            for (int it = 0; it < coarse_sweeps; ++it) {
+                mg_smooth<T>(lev[0], U[0], F[0], C, sigma, kappa, 0, false, s);
+                mg_smooth<T>(lev[0], U[0], F[0], C, sigma, kappa, 1, false, s);
+            }
+            return;
+        }
+        mg_coarse_solve<T>(lev[L - 1], U[L - 1], F[L - 1], C, sigma, kappa, coarse_sweeps, s);
+        for (int l = L - 2; l >= 0; --l) {
+            mg_prolong_correct<T>(lev[l], lev[l + 1], U[l], U[l + 1], C, s);
+            for (int it = 0; it < post; ++it) {
+                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 1, false, s);
+                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 0, false, s);
+            }
+        }
+    }
+};
+
+struct Body {
+    double xc[3] = {0, 0, 0};
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    int kin = IBR_PRESCRIBED;
+    std::vector<double> rbody;
+    int N = 0;
+};
+
+}  // namespace
+
+template <typename T>
+struct PC;
+
+struct ibr_grid {
+    int d = 3;
+    int n[3] = {1, 1, 1};
+    double L[3] = {1, 1, 1};
+    double h = 1, eta = 1, rho = 0, dt = 0, vol = 1;
+    int precision = IBR_MIXED;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Geo geo;
+    std::vector<Body> bodies;
+    bool dirty = true;
+    ibr_solve_opts prepared_opts;
+    MarkerData md;
+    int N = 0;
+    long long nS = 0, len = 0;
+    // mobility
+    std::vector<long long> moff;
+    std::vector<int> roff;
+    long long* moff_dev = nullptr;
+    int* roff_dev = nullptr;
+    double* Mbuild = nullptr;  // M~ as built (FP64)
+    double* Minv64 = nullptr;
+    float* Minv32 = nullptr;
+    int* info_dev = nullptr;
+    // outer FGMRES workspace
+    int m_alloc = 0;
+    long long len_alloc = 0;
+    double *V = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *w = nullptr;
+    double *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
+    double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr, *shift = nullptr, *means = nullptr;
+    double* host_sc = nullptr;  // pinned
+    double* FT = nullptr;
+    double* UO = nullptr;
+    bool have_solution = false;
+    PC<double>* pc64 = nullptr;
+    PC<float>* pc32 = nullptr;
+    int pc_ns = 0;
+
+    bool steady() const { return rho == 0.0 || dt == 0.0; }
+    double sigma() const { return steady() ? 0.0 : rho / dt; }
+    int rot() const { return d == 2 ? 1 : 3; }
+};
+
+// ---------------------------------------------------------------------------
+// preconditioner state in precision T
+template <typename T>
+struct PC {
+    ibr_grid* G = nullptr;
+    int ns = 2;
+    Multigrid<T> mg;
+    T *Vi = nullptr, *Zi = nullptr, *w = nullptr, *rs = nullptr, *rs2 = nullptr, *xs = nullptr;
+    T *y = nullptr, *phi = nullptr, *q = nullptr, *qr = nullptr, *dU = nullptr, *lamT = nullptr;
+    double *Hi = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr, *h1 = nullptr, *h2 = nullptr;
+    double *sc = nullptr, *partial = nullptr, *means = nullptr, *shift = nullptr;
+    const T* Minv = nullptr;
+    int pre = 2, post = 2, variant = IBR_PC_LOWER;
+    long long ps_count = 0;
+
+    PC(ibr_grid* g, int ns_) : G(g), ns(ns_) {
+        long long n = G->geo.ncell;
+        long long nS = G->nS;
+        mg.init(G->geo, G->d);
+        Vi = dalloc<T>((size_t)(ns + 1) * nS);
+        Zi = dalloc<T>((size_t)ns * nS);
+        w = dalloc<T>(nS);
+        rs = dalloc<T>(nS);
+        rs2 = dalloc<T>(nS);
+        xs = dalloc<T>(nS);
+        y = dalloc<T>((size_t)G->d * n);
+        phi = dalloc<T>(n);
+        q = dalloc<T>(n);
+        qr = dalloc<T>(n);
+        Hi = dalloc<double>((size_t)(ns + 1) * (ns + 1));
+        cs = dalloc<double>(ns + 1);
+        sn = dalloc<double>(ns + 1);
+        gv = dalloc<double>(ns + 2);
+        yv = dalloc<double>(ns + 1);
+        h1 = dalloc<double>(ns + 1);
+        h2 = dalloc<double>(ns + 1);
+        sc = dalloc<double>(8);
+        partial = dalloc<double>((size_t)RED_BLOCKS * std::max(ns + 1, 4));
+        means = dalloc<double>(4);
+        shift = dalloc<double>(4);
+        alloc_markers();
+    }
+    void alloc_markers() {
+        dfree(dU);
+        dfree(lamT);
+        long long dN = (long long)G->N * G->d;
+        dU = dalloc<T>(std::max(dN, 1LL));
+        lamT = dalloc<T>(std::max(dN, 1LL));
+    }
+    ~PC() {
+        mg.release();
+        T* tp[] = {Vi, Zi, w, rs, rs2, xs, y, phi, q, qr, dU, lamT};
+        for (T* p : tp)
+            if (p) cudaFree(p);
+        double* dp[] = {Hi, cs, sn, gv, yv, h1, h2, sc, partial, means, shift};
+        for (double* p : dp)
+            if (p) cudaFree(p);
+    }
+
+    // z = P_S^-1 r (Sec. V.B, Eq. P1_practical)
+    void apply_ps(const T* in, T* out) {
+        cudaStream_t s = G->stream;
+        const Geo& g = G->geo;
+        long long n = g.ncell;
+        int d = G->d;
+        double sigma = G->sigma();
+        mg.vcycle(y, in, d, sigma, G->eta, true, pre, post, s);                 // y = A~^-1 g
+        ps_divergence<T>(g, y, in + d * n, qr, -1.0 / (g.h * g.h), q, s);      // q = -D y - h
+        mg.vcycle(phi, qr, 1, 0.0, 1.0, true, pre, post, s);                    // phi = L~p^-1 q
+        double cphi = G->steady() ? 0.0 : -G->rho * g.h * g.h / G->dt;
+        ps_finish<T>(g, y, phi, q, out, G->eta, cphi, s);                       // v, pi
+        ++ps_count;
+    }
+
+    // x = GMRES(ns) approximation of [A G; -D 0]^-1 rhs, x0 = 0
+    void inner_gmres(const T* rhs, T* xout) {
+        cudaStream_t s = G->stream;
+        const Geo& g = G->geo;
+        long long nS = G->nS;
+        norm2<T>(nS, rhs, partial, sc + 0, s);
+        givens_init(sc + 0, gv, ns + 1, sc + 1, sc + 2, s);
+        vec_scale_copy<T>(nS, sc + 2, false, rhs, Vi, s);
+        for (int j = 0; j < ns; ++j) {
+            T* Vj = Vi + (long long)j * nS;
+            T* Zj = Zi + (long long)j * nS;
+            apply_ps(Vj, Zj);
+            stokes_apply<T>(g, Zj, w, G->sigma(), G->eta, nullptr, s);
+            mdot<T>(nS, Vi, nS, j + 1, w, partial, h1, s);
+            update_mdot<T>(nS, Vi, nS, j + 1, h1, w, partial, h2, s);
+            update_norm2<T>(nS, Vi, nS, j + 1, h2, w, partial, sc + 0, s);
+            arnoldi_column(Hi, ns + 1, h1, h2, sc + 0, j, cs, sn, gv, sc + 3, sc + 4, s);
+            if (j + 1 < ns) vec_scale_copy<T>(nS, sc + 4, false, w, Vi + (long long)(j + 1) * nS, s);
+        }
+        hess_solve(Hi, ns + 1, gv, ns, yv, s);
+        combine<T, T>(nS, Zi, nS, ns, yv, xout, false, s);
+    }
+
+    // z = P^-1 r for the constrained system (Sec. V.A), FP64 in and out
+    void apply(const double* r, double* z) {
+        cudaStream_t s = G->stream;
+        const Geo& g = G->geo;
+        long long n = g.ncell, nS = G->nS;
+        int d = G->d, N = G->N;
+        long long dN = (long long)N * d;
+        const T* rin;
+        if (sizeof(T) == sizeof(double)) {
+            rin = reinterpret_cast<const T*>(r);
+        } else {
+            vec_convert<double, T>(nS, r, rs, s);
+            rin = rs;
+        }
+        inner_gmres(rin, xs);                                                // step 1
+        if (N > 0) {
+            interp<T, double>(g, G->md, xs, dU, -1.0, r + nS, s, -1.0);      // step 2: dU = -(J v + W)
+            blockdiag_gemv<T, T>((int)G->bodies.size(), G->moff_dev, G->roff_dev, (int)dN, Minv, dU, lamT,
+                                 s);                                        // step 3
+            if (variant == IBR_PC_FULL) {                                   // step 4
+                IBR_CUDA_TRY(cudaMemcpyAsync(rs2, rin, sizeof(T) * nS, cudaMemcpyDeviceToDevice, s));
+                spread_gather<T>(G->md, lamT, rs2, 1.0 / std::pow(g.h, d), s);
+                if (G->steady()) {
+                    lam_sum<T>(d, N, lamT, 1.0 / G->vol, shift, s);
+                    subtract_means<T>(n, d, rs2, shift, s);
+                }
+                inner_gmres(rs2, xs);
+            }
+        }
+        // keep the Krylov vectors in the space of the constrained problem:
+        // <v> = 0 (periodic steady Stokes) and <pi> = 0
+        block_means<T>(n, d + 1, xs, partial, means, s);
+        if (G->steady())
+            subtract_means<T>(n, d + 1, xs, means, s);
+        else
+            subtract_means<T>(n, 1, xs + (long long)d * n, means + d, s);
+        vec_convert<T, double>(nS, xs, z, s);
+        if (N > 0) vec_convert<T, double>(dN, lamT, z + nS, s);
+    }
+};
+
+namespace {
+
+void require(bool c, const std::string& msg) {
+    if (!c) throw Error{IBR_EINVAL, msg};
+}
+
+void quat_to_R(const double* q, double* R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double nrm = std::sqrt(w * w + x * x + y * y + z * z);
+    require(nrm > 0, "quaternion must be nonzero");
+    w /= nrm;
+    x /= nrm;
+    y /= nrm;
+    z /= nrm;
+    R[0] = 1 - 2 * (y * y + z * z);
+    R[1] = 2 * (x * y - w * z);
+    R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);
+    R[4] = 1 - 2 * (x * x + z * z);
+    R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);
+    R[7] = 2 * (y * z + w * x);
+    R[8] = 1 - 2 * (x * x + y * y);
+}
+
+void free_markers(ibr_grid* G) {
+    MarkerData& md = G->md;
+    dfree(md.q);
+    dfree(md.rel);
+    dfree(md.body);
+    dfree(md.body_start);
+    dfree(md.base);
+    dfree(md.w64);
+    dfree(md.w32);
+    dfree(md.face);
+    dfree(md.off);
+    dfree(md.ent_m);
+    dfree(md.ent_w64);
+    dfree(md.ent_w32);
+    md.F = md.E = 0;
+    dfree(G->moff_dev);
+    dfree(G->roff_dev);
+    dfree(G->Mbuild);
+    dfree(G->Minv64);
+    dfree(G->Minv32);
+    dfree(G->FT);
+    dfree(G->UO);
+}
+
+void free_outer(ibr_grid* G) {
+    double** ps[] = {&G->V, &G->Z, &G->b, &G->x, &G->w, &G->H, &G->cs, &G->sn, &G->gv, &G->yv,
+                     &G->h1, &G->h2, &G->sc, &G->partial, &G->shift, &G->means};
+    for (double** p : ps) dfree(*p);
+    G->m_alloc = 0;
+}
+
+// fill default options
+void opts_default(ibr_solve_opts* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-8;
+    o->restart = 50;
+    o->max_iters = 1000;
+    o->n_s = 2;
+    o->variant = IBR_PC_LOWER;
+    o->mg_pre = 2;
+    o->mg_post = 2;
+    o->mob_model = IBR_MOB_AUTO;
+    o->mob_a_over_h = 0.0;
+    // App. B functional form; builder-chosen coefficients (see the package's
+    // mobility notes): f~ -> ln x + 0.277 and g~ -> 1 at large x
+    const double c[9] = {0.6, 0.277, 1.0, 0.0, 0.6, 0.25, 1.0, 0.0, 0.5};
+    std::memcpy(o->mob_coef, c, sizeof(c));
+    o->time_cap_ms = 0.0;
+}
+
+// self-mobility f(0), the diagonal of M~ (Sec. IV.B): RPY (6 pi eta a)^-1
+// minus the periodic correction, or the App. B value ln(l/(3.708 a))/(4 pi eta)
+double mob_self(const MobParams& p) {
+    if (p.model == IBR_MOB_RPY) return 1.0 / (6.0 * M_PI * p.eta * p.a) - p.corr;
+    return std::log(p.l / (3.708 * p.a)) / (4.0 * M_PI * p.eta);
+}
+
+MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
+    MobParams p;
+    std::memset(&p, 0, sizeof(p));
+    int model = o.mob_model;
+    if (model == IBR_MOB_AUTO) model = G->d == 3 ? IBR_MOB_RPY : IBR_MOB_FIT2D;
+    require(model == IBR_MOB_RPY || model == IBR_MOB_FIT2D, "unknown mob_model");
+    require(!(model == IBR_MOB_FIT2D && G->d != 2), "IBR_MOB_FIT2D is a 2-D model");
+    require(!(model == IBR_MOB_RPY && G->d != 3), "IBR_MOB_RPY is a 3-D model");
+    double aoh = o.mob_a_over_h > 0 ? o.mob_a_over_h : 1.25;
+    p.model = model;
+    p.eta = G->eta;
+    p.h = G->h;
+    p.l = G->L[0];
+    p.a = aoh * G->h;
+    p.corr = (model == IBR_MOB_RPY) ? 2.84 / (6.0 * M_PI * G->eta * G->L[0]) : 0.0;
+    std::memcpy(p.coef, o.mob_coef, sizeof(p.coef));
+    return p;
+}
+
+void ensure_pc(ibr_grid* G, int ns) {
+    if (G->precision == IBR_FP64) {
+        if (G->pc64 && G->pc_ns >= ns) return;
+        delete G->pc64;
+        G->pc64 = nullptr;
+        G->pc64 = new PC<double>(G, ns);
+    } else {
+        if (G->pc32 && G->pc_ns >= ns) return;
+        delete G->pc32;
+        G->pc32 = nullptr;
+        G->pc32 = new PC<float>(G, ns);
+    }
+    G->pc_ns = ns;
+}
+
+void prepare(ibr_grid* G, const ibr_solve_opts& o) {
+    cudaStream_t s = G->stream;
+    require(!G->bodies.empty(), "no bodies added");
+    int d = G->d;
+    int B = (int)G->bodies.size();
+    int N = 0;
+    for (auto& b : G->bodies) {
+        require(b.N > 0, "every body needs markers (ibr_set_markers)");
+        N += b.N;
+    }
+    free_markers(G);
+    G->N = N;
+    G->md.N = N;
+    G->md.B = B;
+    G->len = G->nS + (long long)N * d;
+    std::vector<double> rb((size_t)N * d);
+    std::vector<int> body(N), bstart(B + 1);
+    std::vector<double> xcR((size_t)B * 12);
+    int k = 0;
+    for (int bi = 0; bi < B; ++bi) {
+        const Body& b = G->bodies[bi];
+        bstart[bi] = k;
+        std::memcpy(&rb[(size_t)k * d], b.rbody.data(), sizeof(double) * b.N * d);
+        for (int i = 0; i < b.N; ++i) body[k + i] = bi;
+        k += b.N;
+        for (int a = 0; a < 3; ++a) xcR[bi * 12 + a] = b.xc[a];
+        for (int a = 0; a < 9; ++a) xcR[bi * 12 + 3 + a] = b.R[a];
+    }
+    bstart[B] = N;
+    MarkerData& md = G->md;
+    double* rb_dev = dalloc<double>(rb.size());
+    double* xcR_dev = dalloc<double>(xcR.size());
+    md.q = dalloc<double>((size_t)N * d);
+    md.rel = dalloc<double>((size_t)N * d);
+    md.body = dalloc<int>(N);
+    md.body_start = dalloc<int>(B + 1);
+    md.base = dalloc<int>((size_t)N * d * d);
+    md.w64 = dalloc<double>((size_t)N * d * d * 4);
+    md.w32 = dalloc<float>((size_t)N * d * d * 4);
+    IBR_CUDA_TRY(cudaMemcpyAsync(rb_dev, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    IBR_CUDA_TRY(cudaMemcpyAsync(xcR_dev, xcR.data(), xcR.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    IBR_CUDA_TRY(cudaMemcpyAsync(md.body, body.data(), body.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    IBR_CUDA_TRY(cudaMemcpyAsync(md.body_start, bstart.data(), bstart.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    markers_positions(d, N, rb_dev, md.body, xcR_dev, G->L, md.q, md.rel, s);
+    markers_weights(G->geo, N, md.q, md.base, md.w64, md.w32, s);
+    markers_build_gather(G->geo, md, s);
+    // approximate mobility, one dense block per body
+    G->moff.assign(B + 1, 0);
+    G->roff.assign(B + 1, 0);
+    for (int bi = 0; bi < B; ++bi) {
+        long long nb = (long long)G->bodies[bi].N * d;
+        G->moff[bi + 1] = G->moff[bi] + nb * nb;
+        G->roff[bi + 1] = G->roff[bi] + (int)nb;
+    }
+    G->moff_dev = dalloc<long long>(B + 1);
+    G->roff_dev = dalloc<int>(B + 1);
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->moff_dev, G->moff.data(), (B + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->roff_dev, G->roff.data(), (B + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    long long mtot = G->moff[B];
+    G->Mbuild = dalloc<double>(mtot);
+    MobParams mp = mob_params(G, o);
+    for (int bi = 0; bi < B; ++bi)
+        mtilde_build(d, G->bodies[bi].N, md.rel + (long long)bstart[bi] * d, mp, G->Mbuild + G->moff[bi], s);
+    if (!G->info_dev) G->info_dev = dalloc<int>(1);
+    IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, sizeof(int), s));
+    // a pivot below this fraction of the self-mobility means M~ is singular
+    // to working precision (e.g. coincident markers)
+    double fself = mob_self(mp);
+    if (!(fself > 0.0))
+        throw Error{IBR_ENUMERIC, "self-mobility f(0) of M~ is not positive (check mob_a_over_h, box size)"};
+    double min_piv64 = 1e-10 * fself, min_piv32 = 1e-5 * fself;
+    long long maxblk = 0;
+    for (int bi = 0; bi < B; ++bi) maxblk = std::max(maxblk, G->moff[bi + 1] - G->moff[bi]);
+    if (G->precision == IBR_FP64) {
+        G->Minv64 = dalloc<double>(mtot);
+        double* work = dalloc<double>(maxblk);
+        mat_convert<double, double>(mtot, G->Mbuild, G->Minv64, s);
+        for (int bi = 0; bi < B; ++bi)
+            spd_inverse<double>(G->bodies[bi].N * d, G->Minv64 + G->moff[bi], work, G->info_dev, min_piv64, s);
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(work);
+    } else {
+        G->Minv32 = dalloc<float>(mtot);
+        float* work = dalloc<float>(maxblk);
+        mat_convert<double, float>(mtot, G->Mbuild, G->Minv32, s);
+        for (int bi = 0; bi < B; ++bi)
+            spd_inverse<float>(G->bodies[bi].N * d, G->Minv32 + G->moff[bi], work, G->info_dev, min_piv32, s);
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(work);
+    }
+    G->FT = dalloc<double>((size_t)B * (d + G->rot()));
+    G->UO = dalloc<double>((size_t)B * (d + G->rot()));
+    cudaFree(rb_dev);
+    cudaFree(xcR_dev);
+    int info = 0;
+    IBR_CUDA_TRY(cudaMemcpy(&info, G->info_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info != 0)
+        throw Error{IBR_ENUMERIC, "approximate mobility M~ is not positive definite (pivot " + std::to_string(info) +
+                                      "); change mob_a_over_h / mob_coef or the marker spacing"};
+    if (G->pc64) G->pc64->alloc_markers();
+    if (G->pc32) G->pc32->alloc_markers();
+    G->prepared_opts = o;
+    G->dirty = false;
+    G->have_solution = false;
+}
+
+bool mob_opts_equal(const ibr_solve_opts& a, const ibr_solve_opts& b) {
+    return a.mob_model == b.mob_model && a.mob_a_over_h == b.mob_a_over_h &&
+           std::memcmp(a.mob_coef, b.mob_coef, sizeof(a.mob_coef)) == 0;
+}
+
+void ensure_outer(ibr_grid* G, int m) {
+    if (G->m_alloc >= m && G->V && G->len_alloc == G->len) return;
+    free_outer(G);
+    long long len = G->len;
+    G->V = dalloc<double>((size_t)(m + 1) * len);
+    G->Z = dalloc<double>((size_t)m * len);
+    G->b = dalloc<double>(len);
+    G->x = dalloc<double>(len);
+    G->w = dalloc<double>(len);
+    G->H = dalloc<double>((size_t)(m + 1) * (m + 1));
+    G->cs = dalloc<double>(m + 1);
+    G->sn = dalloc<double>(m + 1);
+    G->gv = dalloc<double>(m + 2);
+    G->yv = dalloc<double>(m + 1);
+    G->h1 = dalloc<double>(m + 1);
+    G->h2 = dalloc<double>(m + 1);
+    G->sc = dalloc<double>(8);
+    G->partial = dalloc<double>((size_t)RED_BLOCKS * std::max(m + 1, 4));
+    G->shift = dalloc<double>(4);
+    G->means = dalloc<double>(4);
+    G->len_alloc = len;
+    if (!G->host_sc) IBR_CUDA_TRY(cudaMallocHost(&G->host_sc, 8 * sizeof(double)));
+    G->m_alloc = m;
+}
+
+// y = (system matrix) x  (FP64)
+void full_matvec(ibr_grid* G, const double* x, double* y) {
+    cudaStream_t s = G->stream;
+    const Geo& g = G->geo;
+    int d = G->d;
+    long long nS = G->nS;
+    const double* lam = x + nS;
+    const double* shift = nullptr;
+    if (G->steady() && G->N > 0) {
+        lam_sum<double>(d, G->N, lam, 1.0 / G->vol, G->shift, s);  // -S~ = -S + vol^-1 1^T
+        shift = G->shift;
+    }
+    stokes_apply<double>(g, x, y, G->sigma(), G->eta, shift, s);
+    if (G->N > 0) {
+        spread_gather<double>(G->md, lam, y, -1.0 / std::pow(g.h, d), s);
+        interp<double, double>(g, G->md, x, y + nS, -1.0, nullptr, s, 0.0);
+    }
+}
+
+void pc_apply(ibr_grid* G, const double* r, double* z) {
+    if (G->precision == IBR_FP64)
+        G->pc64->apply(r, z);
+    else
+        G->pc32->apply(r, z);
+}
+
+double read_scalar(ibr_grid* G, const double* dev) {
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->host_sc, dev, sizeof(double), cudaMemcpyDeviceToHost, G->stream));
+    IBR_CUDA_TRY(cudaStreamSynchronize(G->stream));
+    return G->host_sc[0];
+}
+
+void project_solution(ibr_grid* G, double* x) {
+    cudaStream_t s = G->stream;
+    long long n = G->geo.ncell;
+    int d = G->d;
+    block_means<double>(n, d + 1, x, G->partial, G->means, s);
+    if (G->steady())
+        subtract_means<double>(n, d + 1, x, G->means, s);
+    else
+        subtract_means<double>(n, 1, x + (long long)d * n, G->means + d, s);
+}
+
+int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
+    cudaStream_t s = G->stream;
+    long long len = G->len;
+    int m = o.restart;
+    double t0 = now_ms();
+    norm2<double>(len, G->b, G->partial, G->sc + 0, s);
+    double bnorm = std::sqrt(read_scalar(G, G->sc + 0));
+    IBR_CUDA_TRY(cudaMemsetAsync(G->x, 0, len * sizeof(double), s));
+    info.iters = 0;
+    info.restarts = 0;
+    if (!(bnorm > 0.0)) {
+        if (std::isnan(bnorm)) throw Error{IBR_ENUMERIC, "right-hand side contains NaN/Inf"};
+        info.rel_res_est = info.rel_res_true = 0.0;
+        return IBR_OK;
+    }
+    double target = o.tol * bnorm;
+    bool first = true;
+    int status = IBR_OK;
+    while (true) {
+        // r = b - A x  (into w)
+        if (first) {
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->w, G->b, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else {
+            full_matvec(G, G->x, G->w);
+            vec_axpby<double>(len, 1.0, G->b, -1.0, G->w, s);
+        }
+        norm2<double>(len, G->w, G->partial, G->sc + 0, s);
+        double rn = std::sqrt(read_scalar(G, G->sc + 0));
+        info.rel_res_true = rn / bnorm;
+        if (std::isnan(rn)) throw Error{IBR_ENUMERIC, "NaN in the FGMRES residual"};
+        if (rn <= target) break;
+        if (info.iters >= o.max_iters) {
+            status = IBR_ENOTCONV;
+            break;
+        }
+        if (o.time_cap_ms > 0 && now_ms() - t0 > o.time_cap_ms) {
+            status = IBR_ETIMEOUT;
+            break;
+        }
+        givens_init(G->sc + 0, G->gv, m + 1, G->sc + 1, G->sc + 2, s);
+        vec_scale_copy<double>(len, G->sc + 2, false, G->w, G->V, s);
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* Vj = G->V + (long long)j * len;
+            double* Zj = G->Z + (long long)j * len;
+            pc_apply(G, Vj, Zj);
+            full_matvec(G, Zj, G->w);
+            mdot<double>(len, G->V, len, j + 1, G->w, G->partial, G->h1, s);
+            update_mdot<double>(len, G->V, len, j + 1, G->h1, G->w, G->partial, G->h2, s);
+            update_norm2<double>(len, G->V, len, j + 1, G->h2, G->w, G->partial, G->sc + 0, s);
+            arnoldi_column(G->H, m + 1, G->h1, G->h2, G->sc + 0, j, G->cs, G->sn, G->gv, G->sc + 3, G->sc + 4, s);
+            vec_scale_copy<double>(len, G->sc + 4, false, G->w, G->V + (long long)(j + 1) * len, s);
+            k = j + 1;
+            info.iters++;
+            double est = read_scalar(G, G->sc + 3);
+            info.rel_res_est = est / bnorm;
+            if (std::isnan(est)) throw Error{IBR_ENUMERIC, "NaN in the FGMRES Arnoldi process"};
+            if (est <= target || info.iters >= o.max_iters) break;
+            if (o.time_cap_ms > 0 && now_ms() - t0 > o.time_cap_ms) break;
+        }
+        hess_solve(G->H, m + 1, G->gv, k, G->yv, s);
+        combine<double, double>(len, G->Z, len, k, G->yv, G->x, true, s);
+        project_solution(G, G->x);
+        info.restarts++;
+        first = false;
+    }
+    return status;
+}
+
+}  // namespace
+
+namespace {
+int run_guarded(const char* fn, const std::function<void()>& body) {
+    try {
+        body();
+        ibr::set_error("");
+        return IBR_OK;
+    } catch (const Error& e) {
+        ibr::set_error(std::string(fn) + ": " + e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        ibr::set_error(std::string(fn) + ": host allocation failed");
+        return IBR_ENOMEM;
+    } catch (const std::exception& e) {
+        ibr::set_error(std::string(fn) + ": " + e.what());
+        return IBR_EINVAL;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+const char* ibr_last_error(void) { return ibr::g_last_error.c_str(); }
+
+int ibr_solve_opts_default(ibr_solve_opts* o) {
+    if (!o) {
+        ibr::set_error("ibr_solve_opts_default: NULL");
+        return IBR_EINVAL;
+    }
+    opts_default(o);
+    return IBR_OK;
+}
+
+int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, const int* bc, double eta, double rho,
+                    double dt, int kernel, int precision, void* cuda_stream) {
+    return run_guarded("ibr_create_grid", [&] {
+        require(out != nullptr, "out is NULL");
+        *out = nullptr;
+        require(dim == 2 || dim == 3, "dim must be 2 or 3");
+        require(n && L && bc, "n, L, bc must be non-NULL");
+        for (int a = 0; a < dim; ++a) {
+            require(n[a] >= 4 && n[a] % 2 == 0, "each n[a] must be even and >= 4");
+            require(L[a] > 0, "L[a] must be positive");
+            require(bc[2 * a] == IBR_PERIODIC && bc[2 * a + 1] == IBR_PERIODIC,
+                    "this build supports periodic boundaries only");
+        }
+        double h = L[0] / n[0];
+        for (int a = 1; a < dim; ++a)
+            require(std::fabs(L[a] / n[a] - h) <= 1e-12 * h, "cells must be cubes (L[a]/n[a] equal)");
+        require(eta > 0, "eta must be positive");
+        require(rho >= 0 && dt >= 0, "rho, dt must be >= 0");
+        require(kernel == IBR_KERNEL_PESKIN4, "kernel must be IBR_KERNEL_PESKIN4");
+        require(precision == IBR_FP64 || precision == IBR_MIXED, "precision must be IBR_FP64 or IBR_MIXED");
+        std::unique_ptr<ibr_grid> G(new ibr_grid());
+        G->d = dim;
+        for (int a = 0; a < dim; ++a) {
+            G->n[a] = n[a];
+            G->L[a] = L[a];
+        }
+        G->h = h;
+        G->eta = eta;
+        G->rho = rho;
+        G->dt = dt;
+        G->vol = 1.0;
+        for (int a = 0; a < dim; ++a) G->vol *= L[a];
+        G->precision = precision;
+        G->geo = make_geo(dim, n, h);
+        G->nS = (long long)(dim + 1) * G->geo.ncell;
+        G->len = G->nS;
+        // the coarsest multigrid level must fit one CTA's shared memory
+        {
+            Geo g = G->geo;
+            while (Multigrid<double>::can_coarsen(g)) {
+                g.n0 /= 2;
+                g.n1 /= 2;
+                if (dim == 3) g.n2 /= 2;
+                g.ncell = (long long)g.n0 * g.n1 * g.n2;
+            }
+            require(g.ncell <= 2048, "grid does not coarsen to <= 2048 cells (use sizes with more factors of 2)");
+        }
+        if (cuda_stream) {
+            G->stream = (cudaStream_t)cuda_stream;
+        } else {
+            IBR_CUDA_TRY(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
+            G->own_stream = true;
+        }
+        opts_default(&G->prepared_opts);
+        *out = G.release();
+    });
+}
+
+int ibr_add_body(ibr_grid* G, const double* x_c, const double* quat, int kinematics, int* body_id) {
+    return run_guarded("ibr_add_body", [&] {
+        require(G && x_c, "grid and x_c must be non-NULL");
+        require(kinematics == IBR_PRESCRIBED, "only IBR_PRESCRIBED kinematics are supported");
+        Body b;
+        for (int a = 0; a < G->d; ++a) b.xc[a] = x_c[a];
+        if (quat) quat_to_R(quat, b.R);
+        b.kin = kinematics;
+        G->bodies.push_back(b);
+        if (body_id) *body_id = (int)G->bodies.size() - 1;
+        G->dirty = true;
+        G->have_solution = false;
+    });
+}
+
+int ibr_set_markers(ibr_grid* G, int body_id, const double* r_body, int N) {
+    return run_guarded("ibr_set_markers", [&] {
+        require(G, "grid is NULL");
+        require(body_id >= 0 && body_id < (int)G->bodies.size(), "bad body_id");
+        require(N >= 1 && r_body, "N >= 1 and r_body non-NULL required");
+        for (long long i = 0; i < (long long)N * G->d; ++i)
+            if (!std::isfinite(r_body[i])) throw Error{IBR_ENUMERIC, "marker offsets contain NaN/Inf"};
+        Body& b = G->bodies[body_id];
+        b.rbody.assign(r_body, r_body + (size_t)N * G->d);
+        b.N = N;
+        G->dirty = true;
+        G->have_solution = false;
+    });
+}
+
+int ibr_set_boundary_velocity(ibr_grid* G, int face, const double* values) {
+    (void)face;
+    (void)values;
+    return run_guarded("ibr_set_boundary_velocity", [&] {
+        require(G != nullptr, "grid is NULL");
+        throw Error{IBR_EINVAL, "this build supports periodic boundaries only"};
+    });
+}
+
+int ibr_prepare(ibr_grid* G, const ibr_solve_opts* opts) {
+    return run_guarded("ibr_prepare", [&] {
+        require(G, "grid is NULL");
+        ibr_solve_opts o;
+        if (opts)
+            o = *opts;
+        else
+            opts_default(&o);
+        prepare(G, o);
+    });
+}
+
+int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, int g_on_device,
+                      const ibr_solve_opts* opts, ibr_solve_info* info_out) {
+    ibr_solve_info info;
+    std::memset(&info, 0, sizeof(info));
+    int status = IBR_OK;
+    int rc = run_guarded("ibr_solve_coupled", [&] {
+        require(G && body_UO, "grid and body_UO must be non-NULL");
+        ibr_solve_opts o;
+        if (opts)
+            o = *opts;
+        else
+            opts_default(&o);
+        require(o.tol > 0 && o.tol < 1, "tol must be in (0,1)");
+        require(o.restart >= 1 && o.restart <= 120, "restart must be in [1,120]");
+        require(o.n_s >= 1 && o.n_s <= 16, "n_s must be in [1,16]");
+        require(o.max_iters >= 1, "max_iters must be >= 1");
+        require(o.variant == IBR_PC_LOWER || o.variant == IBR_PC_FULL, "bad variant");
+        require(o.mg_pre >= 0 && o.mg_post >= 0 && o.mg_pre + o.mg_post >= 1, "bad mg sweeps");
+        cudaStream_t s = G->stream;
+        double t0 = now_ms();
+        if (G->dirty || !mob_opts_equal(o, G->prepared_opts)) prepare(G, o);
+        ensure_pc(G, o.n_s);
+        ensure_outer(G, o.restart);
+        double t1 = now_ms();
+        int B = (int)G->bodies.size();
+        int nuo = B * (G->d + G->rot());
+        for (int i = 0; i < nuo; ++i)
+            if (!std::isfinite(body_UO[i])) throw Error{IBR_ENUMERIC, "body_UO contains NaN/Inf"};
+        IBR_CUDA_TRY(cudaMemcpyAsync(G->UO, body_UO, nuo * sizeof(double), cudaMemcpyHostToDevice, s));
+        // b = [g; 0; W = -K U]
+        long long nS = G->nS;
+        IBR_CUDA_TRY(cudaMemsetAsync(G->b, 0, nS * sizeof(double), s));
+        if (gforce) {
+            size_t bytes = (size_t)G->d * G->geo.ncell * sizeof(double);
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->b, gforce, bytes,
+                                         g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        }
+        rigid_K(G->d, G->N, G->md.rel, G->md.body, G->UO, G->b + nS, -1.0, s);
+        auto setup_pc = [&](auto* pc) {
+            pc->ns = o.n_s;
+            pc->pre = o.mg_pre;
+            pc->post = o.mg_post;
+            pc->variant = o.variant;
+            pc->ps_count = 0;
+        };
+        if (G->precision == IBR_FP64) {
+            setup_pc(G->pc64);
+            G->pc64->Minv = G->Minv64;
+        } else {
+            setup_pc(G->pc32);
+            G->pc32->Minv = G->Minv32;
+        }
+        status = fgmres(G, o, info);
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        double t2 = now_ms();
+        info.ms_setup = t1 - t0;
+        info.ms_solve = t2 - t1;
+        info.ps_applications =
+            (int)(G->precision == IBR_FP64 ? G->pc64->ps_count : G->pc32->ps_count);
+        G->have_solution = true;
+    });
+    if (rc == IBR_OK && status != IBR_OK) {
+        rc = status;
+        ibr::set_error(status == IBR_ENOTCONV ? "ibr_solve_coupled: max_iters reached"
+                                              : "ibr_solve_coupled: time cap reached");
+    }
+    info.status = rc;
+    if (info_out) *info_out = info;
+    return rc;
+}
+
+int ibr_get_forces(ibr_grid* G, double* Lambda, double* body_FT) {
+    return run_guarded("ibr_get_forces", [&] {
+        require(G, "grid is NULL");
+        if (!G->have_solution) throw Error{IBR_ESTATE, "no solution (call ibr_solve_coupled first)"};
+        cudaStream_t s = G->stream;
+        const double* lam = G->x + G->nS;
+        if (Lambda)
+            IBR_CUDA_TRY(cudaMemcpyAsync(Lambda, lam, sizeof(double) * G->N * G->d, cudaMemcpyDeviceToHost, s));
+        if (body_FT) {
+            rigid_KT(G->d, (int)G->bodies.size(), G->md.body_start, G->md.rel, lam, G->FT, s);
+            IBR_CUDA_TRY(cudaMemcpyAsync(body_FT, G->FT, sizeof(double) * G->bodies.size() * (G->d + G->rot()),
+                                         cudaMemcpyDeviceToHost, s));
+        }
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int ibr_get_fields(ibr_grid* G, double* v, double* p, int to_device) {
+    return run_guarded("ibr_get_fields", [&] {
+        require(G, "grid is NULL");
+        if (!G->have_solution) throw Error{IBR_ESTATE, "no solution (call ibr_solve_coupled first)"};
+        cudaStream_t s = G->stream;
+        long long n = G->geo.ncell;
+        cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (v) IBR_CUDA_TRY(cudaMemcpyAsync(v, G->x, sizeof(double) * G->d * n, kind, s));
+        if (p) IBR_CUDA_TRY(cudaMemcpyAsync(p, G->x + (long long)G->d * n, sizeof(double) * n, kind, s));
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int ibr_sizes(const ibr_grid* G, long long* system_len, int* n_markers, int* n_bodies) {
+    return run_guarded("ibr_sizes", [&] {
+        require(G, "grid is NULL");
+        int N = 0;
+        for (auto& b : G->bodies) N += b.N;
+        if (system_len) *system_len = G->nS + (long long)N * G->d;
+        if (n_markers) *n_markers = N;
+        if (n_bodies) *n_bodies = (int)G->bodies.size();
+    });
+}
+
+static void need_prepared(ibr_grid* G) {
+    require(G != nullptr, "grid is NULL");
+    if (G->dirty) throw Error{IBR_ESTATE, "geometry changed: call ibr_prepare or ibr_solve_coupled first"};
+}
+
+int ibr_apply_system(ibr_grid* G, const double* x, double* y) {
+    return run_guarded("ibr_apply_system", [&] {
+        need_prepared(G);
+        require(x && y, "x, y must be non-NULL");
+        if (!G->shift) G->shift = dalloc<double>(4);
+        full_matvec(G, x, y);
+    });
+}
+
+int ibr_op_spread(ibr_grid* G, const double* lam, double* f) {
+    return run_guarded("ibr_op_spread", [&] {
+        need_prepared(G);
+        require(lam && f, "lam, f must be non-NULL");
+        cudaStream_t s = G->stream;
+        long long n = G->geo.ncell;
+        IBR_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(double) * G->d * n, s));
+        spread_gather<double>(G->md, lam, f, 1.0 / std::pow(G->h, G->d), s);
+        if (G->steady()) {
+            if (!G->shift) G->shift = dalloc<double>(4);
+            lam_sum<double>(G->d, G->N, lam, 1.0 / G->vol, G->shift, s);
+            subtract_means<double>(n, G->d, f, G->shift, s);
+        }
+    });
+}
+
+int ibr_op_interp(ibr_grid* G, const double* v, double* U) {
+    return run_guarded("ibr_op_interp", [&] {
+        need_prepared(G);
+        require(v && U, "v, U must be non-NULL");
+        interp<double, double>(G->geo, G->md, v, U, 1.0, nullptr, G->stream, 0.0);
+    });
+}
+
+int ibr_op_rigid(ibr_grid* G, const double* UO, double* V) {
+    return run_guarded("ibr_op_rigid", [&] {
+        need_prepared(G);
+        require(UO && V, "UO, V must be non-NULL");
+        rigid_K(G->d, G->N, G->md.rel, G->md.body, UO, V, 1.0, G->stream);
+    });
+}
+
+int ibr_op_rigid_T(ibr_grid* G, const double* lam, double* FT) {
+    return run_guarded("ibr_op_rigid_T", [&] {
+        need_prepared(G);
+        require(lam && FT, "lam, FT must be non-NULL");
+        rigid_KT(G->d, (int)G->bodies.size(), G->md.body_start, G->md.rel, lam, FT, G->stream);
+    });
+}
+
+int ibr_op_mtilde(ibr_grid* G, int body, double* out) {
+    return run_guarded("ibr_op_mtilde", [&] {
+        need_prepared(G);
+        require(body >= 0 && body < (int)G->bodies.size(), "bad body");
+        require(out, "out must be non-NULL");
+        long long cnt = G->moff[body + 1] - G->moff[body];
+        IBR_CUDA_TRY(cudaMemcpyAsync(out, G->Mbuild + G->moff[body], cnt * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     G->stream));
+    });
+}
+
+int ibr_op_mtilde_solve(ibr_grid* G, const double* rhs, double* out) {
+    return run_guarded("ibr_op_mtilde_solve", [&] {
+        need_prepared(G);
+        require(rhs && out, "rhs, out must be non-NULL");
+        cudaStream_t s = G->stream;
+        int B = (int)G->bodies.size();
+        int dN = G->N * G->d;
+        if (G->precision == IBR_FP64) {
+            blockdiag_gemv<double, double>(B, G->moff_dev, G->roff_dev, dN, G->Minv64, rhs, out, s);
+        } else {
+            ensure_pc(G, std::max(G->pc_ns, 1));
+            float* tin = G->pc32->dU;
+            float* tout = G->pc32->lamT;
+            vec_convert<double, float>(dN, rhs, tin, s);
+            blockdiag_gemv<float, float>(B, G->moff_dev, G->roff_dev, dN, G->Minv32, tin, tout, s);
+            vec_convert<float, double>(dN, tout, out, s);
+        }
+    });
+}
+
+int ibr_op_stokes_pc(ibr_grid* G, const double* r, double* z) {
+    return run_guarded("ibr_op_stokes_pc", [&] {
+        require(G && r && z, "grid, r, z must be non-NULL");
+        cudaStream_t s = G->stream;
+        long long nS = G->nS;
+        ensure_pc(G, std::max(G->pc_ns, 1));
+        if (G->precision == IBR_FP64) {
+            G->pc64->apply_ps(r, z);
+        } else {
+            vec_convert<double, float>(nS, r, G->pc32->rs, s);
+            G->pc32->apply_ps(G->pc32->rs, G->pc32->xs);
+            vec_convert<float, double>(nS, G->pc32->xs, z, s);
+        }
+    });
+}
+
+int ibr_op_vcycle(ibr_grid* G, double sigma, double kappa, const double* f, double* u, int k) {
+    return run_guarded("ibr_op_vcycle", [&] {
+        require(G && f && u, "grid, f, u must be non-NULL");
+        require(k >= 1 && sigma >= 0 && kappa > 0, "k >= 1, sigma >= 0, kappa > 0 required");
+        cudaStream_t s = G->stream;
+        long long n = G->geo.ncell;
+        ensure_pc(G, std::max(G->pc_ns, 1));
+        if (G->precision == IBR_FP64) {
+            auto* pc = G->pc64;
+            for (int i = 0; i < k; ++i) pc->mg.vcycle(u, f, 1, sigma, kappa, false, pc->pre, pc->post, s);
+        } else {
+            auto* pc = G->pc32;
+            vec_convert<double, float>(n, f, pc->rs, s);
+            vec_convert<double, float>(n, u, pc->xs, s);
+            for (int i = 0; i < k; ++i) pc->mg.vcycle(pc->xs, pc->rs, 1, sigma, kappa, false, pc->pre, pc->post, s);
+            vec_convert<float, double>(n, pc->xs, u, s);
+        }
+    });
+}
+
+int ibr_destroy_grid(ibr_grid* G) {
+    if (!G) return IBR_OK;
+    return run_guarded("ibr_destroy_grid", [&] {
+        cudaStreamSynchronize(G->stream);
+        delete G->pc64;
+        delete G->pc32;
+        free_markers(G);
+        free_outer(G);
+        dfree(G->info_dev);
+        if (G->host_sc) cudaFreeHost(G->host_sc);
+        if (G->own_stream) cudaStreamDestroy(G->stream);
+        delete G;
+    });
+}
+
+}  // extern "C"

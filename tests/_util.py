@@ -1,0 +1,33 @@
+"""Shared test helpers: build the same seeded problem for the GPU library
+(through the C ABI) and for the oracle.  Both sides take their geometry from
+``synthetic``; no numerical routine is shared."""
+import numpy as np
+
+from oracle.mac import Grid
+from oracle.system import Problem
+
+
+def oracle_problem(wl):
+    q, rel, body = wl.markers()
+    g = Grid(wl.n, wl.L, wl.eta, wl.rho, wl.dt)
+    q = np.mod(q, np.array(wl.L))
+    return Problem(g, q, rel, body, len(wl.bodies))
+
+
+def gpu_grid(abi, wl, precision):
+    g = abi.create_grid(wl.d, wl.n, wl.L, eta=wl.eta, rho=wl.rho, dt=wl.dt, precision=precision)
+    for b in wl.bodies:
+        bid = abi.add_body(g, b.center)
+        abi.set_markers(g, bid, b.rel)
+    return g
+
+
+def rel_err(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def flat_fields(v):
+    return np.concatenate([np.asarray(x).ravel() for x in v])

@@ -45,6 +45,24 @@ def test_fft_stokes_eigenfunction_closed_form(steady):
     assert np.allclose(p, 0.0, atol=1e-12)
 
 
+@pytest.mark.parametrize("sigma", [0.0, 30.0])
+def test_helmholtz_solve_eigenfunction_and_residual(sigma):
+    n = 16
+    g = Grid((n, n, n))
+    i = np.arange(n)
+    # cos(2 pi m x_i) along x: eigenvalue sigma + kappa h^-2 4 sin^2(pi m / n)
+    m, kappa = 2, 1.5
+    f = np.broadcast_to(np.cos(2 * np.pi * m * (i + 0.5) / n), g.shape).copy()
+    u = fft_stokes.helmholtz_solve(g, sigma, kappa, f)
+    lam = sigma + kappa / g.h ** 2 * 4 * np.sin(np.pi * m / n) ** 2
+    assert np.allclose(u, f / lam, atol=1e-15)
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal(g.shape)
+    u = fft_stokes.helmholtz_solve(g, sigma, kappa, f)
+    res = sigma * u - kappa * g.lap(u) / g.h ** 2 - (f - (f.mean() if sigma == 0 else 0))
+    assert np.abs(res).max() < 1e-9
+
+
 def test_fft_stokes_gradient_forcing_is_pressure():
     # f = G psi is balanced entirely by the pressure: v = 0, pi = psi - <psi>
     g = Grid((12, 10), (1.2, 1.0))
