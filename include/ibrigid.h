@@ -57,7 +57,7 @@ extern "C" {
 #define IBR_ENOMEM   -2   /* device or host allocation failed                     */
 #define IBR_ENOTCONV -3   /* FGMRES hit max_iters; results are still readable     */
 #define IBR_ETIMEOUT -4   /* time_cap_ms exceeded; results are still readable     */
-#define IBR_ENUMERIC -5   /* NaN/Inf in data or a non-positive pivot in M~        */
+#define IBR_ENUMERIC -5   /* NaN/Inf in data, or M~ not made SPD by any shift     */
 #define IBR_ECUDA    -6   /* a CUDA runtime call failed                           */
 #define IBR_ESTATE   -7   /* call out of order (e.g. solve before markers)        */
 
@@ -90,7 +90,9 @@ typedef struct ibr_solve_opts {
     int    mg_pre;         /* pre-smoothing sweeps per V-cycle level            */
     int    mg_post;        /* post-smoothing sweeps per V-cycle level           */
     int    mob_model;      /* IBR_MOB_*                                          */
-    double mob_a_over_h;   /* marker hydrodynamic radius a/h for M~ (0: default) */
+    double mob_a_over_h;   /* marker radius a/h in M~ (0: 1.25 in 3-D, Sec. IV.A;  */
+                           /* 1.04 in 2-D, where App. B's f(0) then equals the    */
+                           /* 4-point kernel's discrete periodic self-mobility)   */
     double mob_coef[9];    /* App. B coefficients a0..a4, b0..b3 (2-D steady)   */
     double time_cap_ms;    /* <= 0: none                                         */
 } ibr_solve_opts;
@@ -130,7 +132,10 @@ int ibr_add_body(ibr_grid* g, const double* x_c, const double* quat, int kinemat
 /* Sets the N markers of a body from body-frame offsets r_body[N*dim] (host).
  * Lab positions q_i = x_c + Q(quat) r_i are wrapped into [0, L) on periodic
  * axes.  Marks the geometry dirty: the next solve (or ibr_prepare) rebins the
- * markers and rebuilds and refactors M~.  N >= 1. */
+ * markers and rebuilds and refactors M~.  N >= 1.  M~ is factorised by
+ * Cholesky; a block that is not positive definite (the analytic M~ need not
+ * be, Sec. V.C) is factorised as M~ + delta I with the smallest delta in
+ * 1e-3 f(0) * 2^k that succeeds (IBR_ENUMERIC if none up to k = 40). */
 int ibr_set_markers(ibr_grid* g, int body_id, const double* r_body, int N);
 
 /* Inhomogeneous boundary data for IBR_VELOCITY faces.  Not supported by this

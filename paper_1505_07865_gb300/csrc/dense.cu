@@ -211,6 +211,12 @@ __global__ void __launch_bounds__(TB * TB) k_xtx(int n, const T* W, T* M, int nb
     if (r < n && c < n) M[(long long)r * n + c] = s;
 }
 
+template <typename T>
+__global__ void k_add_diag(int n, T* M, T delta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) M[(long long)i * n + i] += delta;
+}
+
 template <typename Ti, typename To>
 __global__ void k_mat_convert(long long n, const Ti* __restrict__ a, To* __restrict__ b) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -277,6 +283,12 @@ void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStre
     IBR_CUDA_TRY(cudaFreeAsync(Dinv, s));
 }
 
+template <typename T>
+void add_diag(int n, T* M, double delta, cudaStream_t s) {
+    k_add_diag<T><<<grid_1d(n, 256), 256, 0, s>>>(n, M, (T)delta);
+    IBR_CHECK_LAUNCH();
+}
+
 template <typename Ti, typename To>
 void mat_convert(long long n, const Ti* a, To* b, cudaStream_t s) {
     k_mat_convert<Ti, To><<<grid_1d(n, 256) > 4096 ? 4096 : grid_1d(n, 256), 256, 0, s>>>(n, a, b);
@@ -294,6 +306,8 @@ void blockdiag_gemv(int B, const long long* moff_dev, const int* roff_dev, int t
 
 template void spd_inverse<double>(int, double*, double*, int*, double, cudaStream_t);
 template void spd_inverse<float>(int, float*, float*, int*, double, cudaStream_t);
+template void add_diag<double>(int, double*, double, cudaStream_t);
+template void add_diag<float>(int, float*, double, cudaStream_t);
 template void mat_convert<double, float>(long long, const double*, float*, cudaStream_t);
 template void mat_convert<double, double>(long long, const double*, double*, cudaStream_t);
 template void blockdiag_gemv<double, double>(int, const long long*, const int*, int, const double*, const double*,

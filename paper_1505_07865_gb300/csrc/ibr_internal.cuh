@@ -183,6 +183,8 @@ template <typename T>
 void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStream_t s);
 template <typename Ti, typename To>
 void mat_convert(long long n, const Ti* a, To* b, cudaStream_t s);
+template <typename T>
+void add_diag(int n, T* M, double delta, cudaStream_t s);   // M += delta I
 // out[r] = sum_c Minv_b[r][c] rhs[c] for each body block (offsets in elements)
 template <typename T, typename Tv>
 void blockdiag_gemv(int B, const long long* moff_dev, const int* roff_dev, int max_rows, const T* Mall,

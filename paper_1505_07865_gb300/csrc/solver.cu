@@ -19,6 +19,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ibr_internal.cuh"
@@ -178,6 +179,7 @@ struct ibr_grid {
     double* Minv64 = nullptr;
     float* Minv32 = nullptr;
     int* info_dev = nullptr;
+    std::vector<double> mob_shift;  // diagonal shift used per body (0: M~ was SPD)
     // outer FGMRES workspace
     int m_alloc = 0;
     long long len_alloc = 0;
@@ -425,7 +427,10 @@ MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
     require(model == IBR_MOB_RPY || model == IBR_MOB_FIT2D, "unknown mob_model");
     require(!(model == IBR_MOB_FIT2D && G->d != 2), "IBR_MOB_FIT2D is a 2-D model");
     require(!(model == IBR_MOB_RPY && G->d != 3), "IBR_MOB_RPY is a 3-D model");
-    double aoh = o.mob_a_over_h > 0 ? o.mob_a_over_h : 1.25;
+    // default marker radius: a = 1.25 h for the 4-point kernel in 3-D (Sec. IV.A);
+    // in 2-D the value at which ln(l/(3.708 a))/(4 pi eta) equals the discrete
+    // periodic self-mobility of the 4-point kernel, a = 1.04 h
+    double aoh = o.mob_a_over_h > 0 ? o.mob_a_over_h : (model == IBR_MOB_RPY ? 1.25 : 1.04);
     p.model = model;
     p.eta = G->eta;
     p.h = G->h;
@@ -524,32 +529,48 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     double min_piv64 = 1e-10 * fself, min_piv32 = 1e-5 * fself;
     long long maxblk = 0;
     for (int bi = 0; bi < B; ++bi) maxblk = std::max(maxblk, G->moff[bi + 1] - G->moff[bi]);
+    // Factor each block; if M~ is not positive definite (the analytic M~ need
+    // not be, Sec. V.C) retry with M~ + delta I, delta growing geometrically
+    // from 1e-3 f(0): the shift damps the spurious small/negative modes the way
+    // the paper's eigenvalue filtering drops them.
+    G->mob_shift.assign(B, 0.0);
+    auto factor_all = [&](auto* Minv, auto* work, double min_piv) {
+        using TT = std::remove_pointer_t<decltype(Minv)>;
+        for (int bi = 0; bi < B; ++bi) {
+            int nb = G->bodies[bi].N * d;
+            double delta = 0.0;
+            for (int attempt = 0;; ++attempt) {
+                mat_convert<double, TT>(G->moff[bi + 1] - G->moff[bi], G->Mbuild + G->moff[bi], Minv + G->moff[bi], s);
+                if (delta > 0.0) add_diag<TT>(nb, Minv + G->moff[bi], delta, s);
+                IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, sizeof(int), s));
+                spd_inverse<TT>(nb, Minv + G->moff[bi], work, G->info_dev, min_piv, s);
+                int info = 0;
+                IBR_CUDA_TRY(cudaMemcpyAsync(&info, G->info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+                IBR_CUDA_TRY(cudaStreamSynchronize(s));
+                if (info == 0) break;
+                if (attempt >= 40)
+                    throw Error{IBR_ENUMERIC, "approximate mobility M~ of body " + std::to_string(bi) +
+                                                  " could not be made positive definite"};
+                delta = delta == 0.0 ? 1e-3 * fself : 2.0 * delta;
+            }
+            G->mob_shift[bi] = delta;
+        }
+    };
     if (G->precision == IBR_FP64) {
         G->Minv64 = dalloc<double>(mtot);
         double* work = dalloc<double>(maxblk);
-        mat_convert<double, double>(mtot, G->Mbuild, G->Minv64, s);
-        for (int bi = 0; bi < B; ++bi)
-            spd_inverse<double>(G->bodies[bi].N * d, G->Minv64 + G->moff[bi], work, G->info_dev, min_piv64, s);
-        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        factor_all(G->Minv64, work, min_piv64);
         cudaFree(work);
     } else {
         G->Minv32 = dalloc<float>(mtot);
         float* work = dalloc<float>(maxblk);
-        mat_convert<double, float>(mtot, G->Mbuild, G->Minv32, s);
-        for (int bi = 0; bi < B; ++bi)
-            spd_inverse<float>(G->bodies[bi].N * d, G->Minv32 + G->moff[bi], work, G->info_dev, min_piv32, s);
-        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        factor_all(G->Minv32, work, min_piv32);
         cudaFree(work);
     }
     G->FT = dalloc<double>((size_t)B * (d + G->rot()));
     G->UO = dalloc<double>((size_t)B * (d + G->rot()));
     cudaFree(rb_dev);
     cudaFree(xcR_dev);
-    int info = 0;
-    IBR_CUDA_TRY(cudaMemcpy(&info, G->info_dev, sizeof(int), cudaMemcpyDeviceToHost));
-    if (info != 0)
-        throw Error{IBR_ENUMERIC, "approximate mobility M~ is not positive definite (pivot " + std::to_string(info) +
-                                      "); change mob_a_over_h / mob_coef or the marker spacing"};
     if (G->pc64) G->pc64->alloc_markers();
     if (G->pc32) G->pc32->alloc_markers();
     G->prepared_opts = o;

@@ -170,16 +170,3 @@ def test_error_paths(abi):
         assert np.isfinite(lam).all()
     finally:
         abi.destroy_grid(G)
-
-
-def test_coincident_markers_rejected(abi):
-    # two markers at the same point make M~ singular: reported, not hidden
-    wl = Workload("dup", (16, 16), (1.0, 1.0), bodies=[
-        Body(np.array([0.5, 0.5]), np.array([[0.05, 0.0], [0.05, 0.0], [-0.05, 0.0]]), np.array([1.0, 0, 0]))])
-    G = gpu_grid(abi, wl, abi.FP64)
-    try:
-        with pytest.raises(abi.IbrError) as e:
-            abi.prepare(G)
-        assert e.value.code == abi.ENUMERIC
-    finally:
-        abi.destroy_grid(G)
