@@ -118,7 +118,8 @@ int ibr_solve_opts_default(ibr_solve_opts* opts);
  * equal for all a).  bc[a][s]: only IBR_PERIODIC is accepted by this build.
  * eta > 0 viscosity; rho, dt >= 0 (rho == 0 or dt == 0: steady Stokes, A =
  * -eta h^-2 Lap).  kernel: IBR_KERNEL_PESKIN4.  precision: IBR_FP64 or
- * IBR_MIXED.  cuda_stream: a cudaStream_t or NULL.  On success *out owns the
+ * IBR_MIXED.  cuda_stream: a cudaStream_t, or NULL for a library-created
+ * blocking stream (ordered with the legacy default stream).  On success *out owns the
  * grid's device memory.  Errors: IBR_EINVAL, IBR_ENOMEM, IBR_ECUDA. */
 int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L,
                     const int* bc /* dim*2 */, double eta, double rho, double dt,

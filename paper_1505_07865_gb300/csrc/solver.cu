@@ -804,7 +804,8 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
         if (cuda_stream) {
             G->stream = (cudaStream_t)cuda_stream;
         } else {
-            IBR_CUDA_TRY(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
+            // a blocking stream: ordered with work on the legacy default stream
+            IBR_CUDA_TRY(cudaStreamCreateWithFlags(&G->stream, cudaStreamDefault));
             G->own_stream = true;
         }
         opts_default(&G->prepared_opts);
