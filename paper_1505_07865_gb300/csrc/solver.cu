@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -667,7 +669,14 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
         return IBR_OK;
     }
     double target = o.tol * bnorm;
+    // IBR_VERBOSE=1 prints the Arnoldi residual estimates and the true
+    // residual at each restart to stderr (diagnostics only)
+    const char* ve = std::getenv("IBR_VERBOSE");
+    bool verbose = ve && ve[0] && ve[0] != '0';
     bool first = true;
+    bool last_cycle_converged_est = false;
+    int stalls = 0;
+    double last_rn = 0.0;
     int status = IBR_OK;
     while (true) {
         // r = b - A x  (into w)
@@ -680,8 +689,20 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
         norm2<double>(len, G->w, G->partial, G->sc + 0, s);
         double rn = std::sqrt(read_scalar(G, G->sc + 0));
         info.rel_res_true = rn / bnorm;
+        if (verbose) std::fprintf(stderr, "[ibr] restart %d true rel res %.3e\n", info.restarts, rn / bnorm);
         if (std::isnan(rn)) throw Error{IBR_ENUMERIC, "NaN in the FGMRES residual"};
         if (rn <= target) break;
+        // a cycle that ended on the Givens estimate but left the true residual
+        // where it was has hit the attainable accuracy of FP64 for this
+        // scaling: stop after three such cycles instead of spinning
+        if (!first && last_cycle_converged_est) {
+            stalls = (rn > 0.5 * last_rn) ? stalls + 1 : 0;
+            if (stalls >= 3) {
+                status = IBR_ENOTCONV;
+                break;
+            }
+        }
+        last_rn = rn;
         if (info.iters >= o.max_iters) {
             status = IBR_ENOTCONV;
             break;
@@ -693,6 +714,7 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
         givens_init(G->sc + 0, G->gv, m + 1, G->sc + 1, G->sc + 2, s);
         vec_scale_copy<double>(len, G->sc + 2, false, G->w, G->V, s);
         int k = 0;
+        last_cycle_converged_est = false;
         for (int j = 0; j < m; ++j) {
             double* Vj = G->V + (long long)j * len;
             double* Zj = G->Z + (long long)j * len;
@@ -707,7 +729,14 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
             info.iters++;
             double est = read_scalar(G, G->sc + 3);
             info.rel_res_est = est / bnorm;
+            if (verbose) {
+                double hn = std::sqrt(read_scalar(G, G->sc + 0));
+                double h1j = read_scalar(G, G->h1 + j);
+                std::fprintf(stderr, "[ibr] it %d j %d est %.3e |w_perp| %.3e h1[j] %.3e\n", info.iters, j,
+                             est / bnorm, hn, h1j);
+            }
             if (std::isnan(est)) throw Error{IBR_ENUMERIC, "NaN in the FGMRES Arnoldi process"};
+            if (est <= target) last_cycle_converged_est = true;
             if (est <= target || info.iters >= o.max_iters) break;
             if (o.time_cap_ms > 0 && now_ms() - t0 > o.time_cap_ms) break;
         }

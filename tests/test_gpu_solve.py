@@ -2,11 +2,13 @@
 against the oracle's exact solution, through the C ABI.
 
 Tolerance reasoning: the exact solution x* and a GPU iterate x with true
-relative residual r satisfy ||x - x*|| / ||x*|| <= kappa * r.  The tests
-solve to r = 1e-12 and require 1e-9 on v, pi, Lambda and the body force
-(all-FP64 and mixed paths: the mixed path only changes the preconditioner,
-the FGMRES residual is FP64).  At the benchmark tolerance r = 1e-8 the mixed
-path is required to be within 1e-7 (relative L2) of the oracle.
+relative residual r satisfy ||x - x*|| / ||x*|| <= kappa * r.  With the
+unweighted residual of the system (momentum rows carry eta h^-2) the FP64
+attainable accuracy is about 1e-11, so the parity tests solve to r = 1e-10
+and require 1e-9 on v, pi, Lambda and the body force, for the all-FP64 and
+the mixed path alike (the mixed path only changes the preconditioner; the
+FGMRES residual is FP64).  At the benchmark tolerance r = 1e-8 the mixed path
+must be within 1e-7 (relative L2) of the oracle.
 """
 import numpy as np
 import pytest
@@ -29,7 +31,7 @@ def abi():
     return a
 
 
-def _solve(abi, wl, precision, tol=1e-12, **kw):
+def _solve(abi, wl, precision, tol=1e-10, **kw):
     G = gpu_grid(abi, wl, precision)
     try:
         o = abi.solve_opts_default()
@@ -52,11 +54,12 @@ _ORACLE = {}
 
 
 def _oracle(wl):
-    if wl.name not in _ORACLE:
+    key = (wl.name, wl.rho, wl.dt)
+    if key not in _ORACLE:
         pr = oracle_problem(wl)
         v, p, lam = fft_stokes.solve_coupled(pr, wl.UO())
-        _ORACLE[wl.name] = (pr, flat_fields(v), p.ravel(), lam, drag(pr, lam))
-    return _ORACLE[wl.name]
+        _ORACLE[key] = (pr, flat_fields(v), p.ravel(), lam, drag(pr, lam))
+    return _ORACLE[key]
 
 
 def _mk_cases():
@@ -64,11 +67,11 @@ def _mk_cases():
     two = Workload("two_disks_96x64", (96, 64), (1.5, 1.0), bodies=[
         Body(np.array([0.37, 0.41]), disk_markers(0.12, 1 / 64), rng.standard_normal(3)),
         Body(np.array([1.13, 0.62]), disk_markers(0.08, 1 / 64), rng.standard_normal(3)),
-    ], tol=1e-12)
+    ], tol=1e-10)
     seam = Workload("disk_on_seam_32", (32, 32), (1.0, 1.0), bodies=[
-        Body(np.array([0.01, 0.985]), disk_markers(0.1, 1 / 32), rng.standard_normal(3))], tol=1e-12)
+        Body(np.array([0.01, 0.985]), disk_markers(0.1, 1 / 32), rng.standard_normal(3))], tol=1e-10)
     sph = Workload("sphere_32", (32, 32, 32), (1.0, 1.0, 1.0), bodies=[
-        Body(np.array([0.48, 0.51, 0.53]), sphere_markers(0.2, 150), rng.standard_normal(6))], tol=1e-12)
+        Body(np.array([0.48, 0.51, 0.53]), sphere_markers(0.2, 150), rng.standard_normal(6))], tol=1e-10)
     return [
         small_2d(16),
         small_2d(16, rho=1.0, dt=1e-3),
@@ -89,7 +92,7 @@ def test_solve_matches_oracle(abi, wl, prec):
     pr, vo, po, lo, fo = _oracle(wl)
     info, v, p, lam, ft = _solve(abi, wl, getattr(abi, prec))
     assert info.status == abi.OK, info.as_dict()
-    assert info.rel_res_true <= 1e-12
+    assert info.rel_res_true <= 1e-10 * (1 + 1e-9)
     assert rel_err(v, vo) < 1e-9, info.as_dict()
     assert rel_err(p, po) < 1e-9
     assert rel_err(lam, lo) < 1e-9
@@ -100,7 +103,7 @@ def test_mixed_at_benchmark_tolerance(abi):
     wl = disk_64()
     pr, vo, po, lo, fo = _oracle(wl)
     info, v, p, lam, ft = _solve(abi, wl, abi.MIXED, tol=1e-8)
-    assert info.status == abi.OK and info.rel_res_true <= 1e-8
+    assert info.status == abi.OK and info.rel_res_true <= 1e-8 * (1 + 1e-9)
     for a, b in ((v, vo), (p, po), (lam, lo), (ft, fo)):
         assert rel_err(a, b) < 1e-7
 
