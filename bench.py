@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark: constrained rigid-body immersed-boundary Stokes solves per second.
+
+Workload (one step = one full coupled solve, setup included): periodic unit
+cube, 128^3 MAC grid, steady Stokes (eta = 1), one sphere of radius 0.1 at the
+centre carried by 500 golden-spiral surface markers (spacing ~2.2h, 4-point
+Peskin kernel); each step draws a new rigid velocity U, Omega ~ N(0,1) and
+solves from x0 = 0 to a true relative residual of 1e-8 (FGMRES, lower-
+triangular Schur preconditioner, N_s = 2, restart 50).  Every step re-runs the
+geometry set-up (marker binning, M~ build and factorisation).
+
+  value  : mixed-precision solves/s over all ranks (replicas), device timing
+  e2e    : the same through the C ABI with host buffers: markers and velocities
+           copied in, Lambda, body forces, velocity and pressure copied out
+  fp64   : the all-FP64 GPU solve, for the mixed-vs-FP64 comparison
+  --impl reference : the FP64 CPU oracle on a bounded sample of the workload
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rigid-body IB solves/s at rel. residual 1e-8 (mixed vs FP64 GPU); p50/p99 ms"
+UNIT = "solves/s"
+TOL = 1e-8
+WORKLOAD = "sphere_128^3_periodic_stokes (unit cube, 128^3 MAC, 1 sphere R=0.1, 500 markers, U,Omega~N(0,1))"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the all-FP64 comparison arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1505_07865_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, launch_bytes):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured from the current sources (else None)."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if t.get("source_sha") != source_sha():
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_sample(seconds_budget=20.0):
+    """The oracle (exact Schur/CG route) on the 128^3 workload: a bounded number
+    of its CG iterations is timed; one solve = rhs set-up + n_cg iterations,
+    n_cg from the oracle's own recorded count for this workload."""
+    from oracle import fft_stokes, ib
+    from oracle.mac import Grid
+    from oracle.system import Problem
+    from synthetic import sphere_128
+
+    rec = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_sphere128_cg.json")))
+    wl = sphere_128()
+    q, rel, body = wl.markers()
+    g = Grid(wl.n, wl.L, wl.eta)
+    pr = Problem(g, np.mod(q, 1.0), rel, body, 1)
+    t0 = time.perf_counter()
+    W = -ib.apply_K(pr.rel, pr.body, wl.UO(), 3)
+    vt, _ = fft_stokes.stokes_solve(g, [np.zeros(g.shape)] * 3)
+    rhs = -(W + ib.interp(g, pr.q, vt)).ravel()
+    t_setup = time.perf_counter() - t0
+    x = rhs.copy()
+    times = []
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < seconds_budget or len(times) < 2:
+        ts = time.perf_counter()
+        f = ib.spread_tilde(g, pr.q, x.reshape(pr.N, 3))
+        v, _ = fft_stokes.stokes_solve(g, f)
+        x = ib.interp(g, pr.q, v).ravel()
+        times.append(time.perf_counter() - ts)
+    t_it = float(np.median(times))
+    n_cg = int(rec["cg_iterations"])
+    t_solve = t_setup + (n_cg + 2) * t_it  # + the two exact Stokes solves for v~ and the final v
+    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
+    return {
+        "value": 1.0 / t_solve,
+        "unit": UNIT,
+        "cores": int(threads) if threads else len(os.sched_getaffinity(0)),
+        "kind": "oracle",
+        "sample": (f"{len(times)} CG iterations (each one exact DFT Stokes solve of the 128^3 grid with "
+                   f"spread and interpolation, median {t_it:.3f} s) of the oracle's Schur-complement solve; "
+                   f"one solve = set-up + {n_cg} CG iterations (oracle's recorded count to rel. CG residual "
+                   f"1e-8) + 2 Stokes solves"),
+        "seconds_per_solve": t_solve,
+    }
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_oracle_sample(seconds_budget=budget)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    value = float(np.mean(vals))
+    cb["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tol": TOL},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def make_grid(abi, torch, wl, precision, stream):
+    body = wl.bodies[0]
+    G = abi.create_grid(3, wl.n, wl.L, eta=wl.eta, precision=precision, stream=stream.cuda_stream)
+    abi.add_body(G, body.center)
+    abi.set_markers(G, 0, body.rel)
+    return G
+
+
+def timed_solves(abi, torch, G, wl, stream, UOs, warmup, steps, e2e=False, host_bufs=None):
+    opts = abi.solve_opts_default()
+    opts.tol = TOL
+    rel = wl.bodies[0].rel
+    infos = []
+
+    def one(i):
+        abi.set_markers(G, 0, rel)  # geometry set-up runs inside the solve
+        info = abi.solve_coupled(G, UOs[i], opts=opts, raise_on_notconv=True)
+        if e2e:
+            lam, ft, v, p = host_bufs
+            abi._check(abi._lib.ibr_get_forces(G, lam.ctypes.data_as(abi._D), ft.ctypes.data_as(abi._D)))
+            abi.get_fields(G, v, p)
+        return info
+
+    for i in range(warmup):
+        one(i)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    l0 = abi.launch_count()
+    evs[0].record(stream)
+    for i in range(steps):
+        infos.append(one(warmup + i))
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = abi.launch_count() - l0
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    total = evs[0].elapsed_time(evs[-1])
+    return total, per, infos, launches
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1505_07865_gb300 import abi
+    from synthetic import sphere_128
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    wl = sphere_128()
+    stream = torch.cuda.Stream()
+    nsteps = args.warmup + args.steps
+    rng = np.random.default_rng(1505 + 3 + 1000 * rank)
+    UOs = rng.standard_normal((nsteps, 1, 6))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- mixed precision (the flagship path), device-resident inputs -------
+    G = make_grid(abi, torch, wl, abi.MIXED, stream)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    total_ms, per, infos, launches = timed_solves(abi, torch, G, wl, stream, UOs, args.warmup, args.steps)
+    clk = clocks.stop()
+    barrier()
+    total_ms = max_over_ranks(total_ms)
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- per-kernel CUDA-event profile of the same steps (separate pass) ----
+    abi.profile_reset()
+    abi.profile_enable(True)
+    prof_total, _, _, _ = timed_solves(abi, torch, G, wl, stream, UOs, 0, args.profile_steps)
+    abi.profile_enable(False)
+    prof = abi.profile_read()
+    abi.profile_reset()
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    n = int(np.prod(wl.n))
+    N = wl.bodies[0].rel.shape[0]
+    pin = lambda k: torch.empty(k, dtype=torch.float64).pin_memory().numpy()  # noqa: E731
+    host = (pin(3 * N), pin(6), pin(3 * n), pin(n))
+    barrier()
+    e2e_ms, e2e_per, _, _ = timed_solves(abi, torch, G, wl, stream, UOs, 1, args.steps, e2e=True, host_bufs=host)
+    barrier()
+    e2e_ms = max_over_ranks(e2e_ms)
+    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+    h2d = N * 3 * 8 + 6 * 8
+    d2h = (3 * N + 6 + 3 * n + n) * 8
+    abi.destroy_grid(G)
+
+    # ---- all-FP64 GPU solve (comparison arm) --------------------------------
+    fsteps = args.fp64_steps if args.fp64_steps is not None else max(2, args.steps // 2)
+    G64 = make_grid(abi, torch, wl, abi.FP64, stream)
+    barrier()
+    f_ms, f_per, f_infos, _ = timed_solves(abi, torch, G64, wl, stream, UOs, 1, fsteps)
+    barrier()
+    f_ms = max_over_ranks(f_ms)
+    fp64_value = world * fsteps / (f_ms / 1000.0)
+    abi.destroy_grid(G64)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (kl, kms, kbytes) = top
+    achieved = (kbytes / kl) / (kms / kl * 1e-3) / 1e9
+    roof = {
+        "kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "frac": achieved / hbm, "peak_source": "measured" if pk else "fallback",
+        "traffic": ncu_traffic(kname, kbytes / kl),
+        "algorithmic_bytes_per_launch": kbytes / kl, "launches_per_step": kl / args.profile_steps,
+        "avg_launch_us": kms / kl * 1000.0, "share_of_step": kms / prof_total,
+    }
+    breakdown = {k: {"launches_per_step": v[0] / args.profile_steps, "ms_per_step": v[1] / args.profile_steps,
+                     "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+        cpu.pop("seconds_per_solve", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tol": TOL, "precision": "mixed", "restart": 50, "n_s": 2,
+                   "preconditioner": "lower-triangular Schur", "setup_in_step": True,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (FP64 system vector 67 MB, Krylov basis > 1 GB)"},
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "iters_per_solve": float(np.mean([i.iters for i in infos])),
+        "ps_applications_per_solve": float(np.mean([i.ps_applications for i in infos])),
+        "rel_res_true_max": float(max(i.rel_res_true for i in infos)),
+        "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": f_ms / fsteps,
+                 "p50_ms": float(np.percentile(f_per, 50)), "p99_ms": float(np.percentile(f_per, 99)),
+                 "iters_per_solve": float(np.mean([i.iters for i in f_infos])), "steps": fsteps},
+        "mixed_over_fp64": value / fp64_value,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "p50_ms": float(np.percentile(e2e_per, 50))},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernel_breakdown": breakdown,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -210,6 +210,19 @@ int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
  * f and returns mean-zero u. */
 int ibr_op_vcycle(ibr_grid* g, double sigma, double kappa, const double* f, double* u, int k);
 
+/* ---- instrumentation (measurement support; the paper has no counterpart) ---
+ * Process-wide.  ibr_launch_count: kernels launched by the library since it
+ * was loaded.  ibr_profile_enable(1): from then on every launch is bracketed
+ * by CUDA events on its own stream; ibr_profile_read(idx, ...) returns, for
+ * kernel class idx (0..count-1; IBR_EINVAL past the end), its name, launches,
+ * summed event time in ms and summed algorithmic bytes (each array read or
+ * written once); it synchronises on the recorded events.  ibr_profile_reset
+ * clears the sums. */
+long long ibr_launch_count(void);
+int ibr_profile_enable(int on);
+int ibr_profile_reset(void);
+int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes);
+
 /* Destroys the grid and frees its device memory. NULL is accepted. */
 int ibr_destroy_grid(ibr_grid* g);
 

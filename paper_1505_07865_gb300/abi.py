@@ -98,6 +98,11 @@ _SIGS = {
     "ibr_op_vcycle": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_int]),
     "ibr_destroy_grid": (ctypes.c_int, [_P]),
     "ibr_last_error": (ctypes.c_char_p, []),
+    "ibr_launch_count": (ctypes.c_longlong, []),
+    "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "ibr_profile_reset": (ctypes.c_int, []),
+    "ibr_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_longlong), _D, _D]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -267,3 +272,33 @@ def op_vcycle(grid, sigma, kappa, f, u, k):
 
 def destroy_grid(grid):
     _check(_lib.ibr_destroy_grid(grid))
+
+
+def launch_count():
+    return int(_lib.ibr_launch_count())
+
+
+def profile_enable(on=True):
+    _check(_lib.ibr_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(_lib.ibr_profile_reset())
+
+
+def profile_read():
+    """{kernel class: (launches, total_ms, total_algorithmic_bytes)} for every
+    class with at least one timed launch."""
+    out = {}
+    i = 0
+    buf = ctypes.create_string_buffer(64)
+    while True:
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        if _lib.ibr_profile_read(i, buf, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)) != OK:
+            break
+        if n.value:
+            out[buf.value.decode()] = (n.value, ms.value, by.value)
+        i += 1
+    return out

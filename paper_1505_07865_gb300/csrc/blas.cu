@@ -268,21 +268,25 @@ inline int blocks_for(long long n) {
 
 template <typename T>
 void vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStream_t s) {
+    ProfScope ps(KID_AXPBY, s, 3.0 * n * sizeof(T));
     k_axpby<T><<<blocks_for(n), 256, 0, s>>>(n, (T)a, x, (T)b, y);
     IBR_CHECK_LAUNCH();
 }
 template <typename T>
 void vec_scale_copy(long long n, const double* scale_dev, bool invert, const T* x, T* y, cudaStream_t s) {
+    ProfScope ps(KID_SCALE, s, 2.0 * n * sizeof(T));
     k_scale_copy<T><<<blocks_for(n), 256, 0, s>>>(n, scale_dev, invert ? 1 : 0, x, y);
     IBR_CHECK_LAUNCH();
 }
 template <typename Ti, typename To>
 void vec_convert(long long n, const Ti* x, To* y, cudaStream_t s) {
+    ProfScope ps(KID_CONVERT, s, (double)n * (sizeof(Ti) + sizeof(To)));
     k_convert<Ti, To><<<blocks_for(n), 256, 0, s>>>(n, x, y);
     IBR_CHECK_LAUNCH();
 }
 template <typename T>
 void mdot(long long n, const T* V, long long ld, int k, const T* w, double* partial, double* out, cudaStream_t s) {
+    ProfScope ps(KID_MDOT, s, (k + 1.0) * n * sizeof(T));
     k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k, out);
@@ -291,6 +295,7 @@ void mdot(long long n, const T* V, long long ld, int k, const T* w, double* part
 template <typename T>
 void update_mdot(long long n, const T* V, long long ld, int k, const double* h, T* w, double* partial, double* out,
                  cudaStream_t s) {
+    ProfScope ps(KID_UPD_MDOT, s, (k + 2.0) * n * sizeof(T));
     k_update_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h, w, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k, out);
@@ -299,6 +304,7 @@ void update_mdot(long long n, const T* V, long long ld, int k, const double* h, 
 template <typename T>
 void update_norm2(long long n, const T* V, long long ld, int k, const double* h, T* w, double* partial, double* out,
                   cudaStream_t s) {
+    ProfScope ps(KID_UPD_NORM, s, (k + 2.0) * n * sizeof(T));
     k_update_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h, w, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, 1, out);
@@ -306,6 +312,7 @@ void update_norm2(long long n, const T* V, long long ld, int k, const double* h,
 }
 template <typename T>
 void norm2(long long n, const T* w, double* partial, double* out, cudaStream_t s) {
+    ProfScope ps(KID_NORM2, s, (double)n * sizeof(T));
     k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, 1, out);
@@ -313,11 +320,13 @@ void norm2(long long n, const T* w, double* partial, double* out, cudaStream_t s
 }
 template <typename T, typename Tz>
 void combine(long long n, const Tz* Z, long long ld, int k, const double* y, T* x, bool accumulate, cudaStream_t s) {
+    ProfScope ps(KID_COMBINE, s, (double)n * (k * sizeof(Tz) + (accumulate ? 2 : 1) * sizeof(T)));
     k_combine<T, Tz><<<blocks_for(n), 256, 0, s>>>(n, Z, ld, k, y, x, accumulate ? 1 : 0);
     IBR_CHECK_LAUNCH();
 }
 template <typename T>
 void block_means(long long m, int C, const T* x, double* partial, double* out, cudaStream_t s) {
+    ProfScope ps(KID_BLOCK_MEANS, s, (double)m * C * sizeof(T));
     k_block_sums<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(m, C, x, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<C, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, C, out);
@@ -327,20 +336,24 @@ void block_means(long long m, int C, const T* x, double* partial, double* out, c
 }
 template <typename T>
 void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t s) {
+    ProfScope ps(KID_SUB_MEANS, s, 2.0 * m * C * sizeof(T));
     k_subtract_means<T><<<blocks_for(m * C), 256, 0, s>>>(m, C, x, means);
     IBR_CHECK_LAUNCH();
 }
 
 void arnoldi_column(double* H, int ldh, const double* h1, const double* h2, const double* nrm2, int j, double* cs,
                     double* sn, double* gv, double* res_out, double* inv_norm_out, cudaStream_t s) {
+    ProfScope ps(KID_SMALL, s, 0.0);
     k_arnoldi_column<<<1, 1, 0, s>>>(H, ldh, h1, h2, nrm2, j, cs, sn, gv, res_out, inv_norm_out);
     IBR_CHECK_LAUNCH();
 }
 void givens_init(const double* nrm2, double* gv, int m1, double* beta_out, double* inv_beta_out, cudaStream_t s) {
+    ProfScope ps(KID_SMALL, s, 0.0);
     k_givens_init<<<1, 1, 0, s>>>(nrm2, gv, m1, beta_out, inv_beta_out);
     IBR_CHECK_LAUNCH();
 }
 void hess_solve(const double* H, int ldh, const double* gv, int k, double* y, cudaStream_t s) {
+    ProfScope ps(KID_SMALL, s, 0.0);
     k_hess_solve<<<1, 1, 0, s>>>(H, ldh, gv, k, y);
     IBR_CHECK_LAUNCH();
 }

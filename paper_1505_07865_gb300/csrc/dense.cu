@@ -246,6 +246,7 @@ __global__ void k_bd_gemv(int B, const long long* __restrict__ moff, const int* 
 
 void mtilde_build(int d, int Nb, const double* rel_b, const MobParams& p, double* M, cudaStream_t s) {
     long long n = (long long)Nb * Nb;
+    ProfScope ps(KID_MTILDE, s, (double)n * d * d * 8);
     if (d == 3)
         k_mtilde<3><<<grid_1d(n, 256), 256, 0, s>>>(Nb, rel_b, p, M);
     else
@@ -256,6 +257,7 @@ void mtilde_build(int d, int Nb, const double* rel_b, const MobParams& p, double
 template <typename T>
 void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStream_t s) {
     int nb = (n + TB - 1) / TB;
+    ProfScope ps(KID_SPD_INV, s, 2.0 * n * n * sizeof(T));
     T* Dinv = nullptr;
     IBR_CUDA_TRY(cudaMallocAsync(&Dinv, (size_t)nb * TB * TB * sizeof(T), s));
     dim3 tile(TB, TB);
@@ -285,12 +287,14 @@ void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStre
 
 template <typename T>
 void add_diag(int n, T* M, double delta, cudaStream_t s) {
+    ProfScope ps(KID_SPD_INV, s, 0.0);
     k_add_diag<T><<<grid_1d(n, 256), 256, 0, s>>>(n, M, (T)delta);
     IBR_CHECK_LAUNCH();
 }
 
 template <typename Ti, typename To>
 void mat_convert(long long n, const Ti* a, To* b, cudaStream_t s) {
+    ProfScope ps(KID_SPD_INV, s, (double)n * (sizeof(Ti) + sizeof(To)));
     k_mat_convert<Ti, To><<<grid_1d(n, 256) > 4096 ? 4096 : grid_1d(n, 256), 256, 0, s>>>(n, a, b);
     IBR_CHECK_LAUNCH();
 }
@@ -300,6 +304,7 @@ void blockdiag_gemv(int B, const long long* moff_dev, const int* roff_dev, int t
                     Tv* out, cudaStream_t s) {
     int threads = 256;
     int blocks = grid_1d((long long)total_rows * 32, threads);
+    ProfScope ps(KID_GEMV, s, (double)total_rows * total_rows * sizeof(T));
     k_bd_gemv<T, Tv><<<blocks, threads, 0, s>>>(B, moff_dev, roff_dev, Mall, rhs, out);
     IBR_CHECK_LAUNCH();
 }

@@ -357,6 +357,7 @@ __global__ void k_rigid_KT(int d, const int* __restrict__ bstart, const double* 
 
 void markers_positions(int d, int N, const double* rbody, const int* body, const double* xc_R, const double* Lbox,
                        double* q, double* rel, cudaStream_t s) {
+    ProfScope ps(KID_MARKERS, s, 0.0);
     k_positions<<<grid_1d(N, 128), 128, 0, s>>>(d, N, rbody, body, xc_R, Lbox[0], Lbox[1], d == 3 ? Lbox[2] : 0.0, q,
                                                   rel);
     IBR_CHECK_LAUNCH();
@@ -364,6 +365,7 @@ void markers_positions(int d, int N, const double* rbody, const int* body, const
 
 void markers_weights(const Geo& g, int N, const double* q, int* base, double* w64, float* w32, cudaStream_t s) {
     int n = N * g.d * g.d;
+    ProfScope ps(KID_MARKERS, s, 0.0);
     k_weights<<<grid_1d(n, 128), 128, 0, s>>>(g, N, q, base, w64, w32);
     IBR_CHECK_LAUNCH();
 }
@@ -373,6 +375,7 @@ void markers_build_gather(const Geo& g, MarkerData& md, cudaStream_t s) {
     long long E = (long long)md.N * g.d * S;
     long long P = BS_ELEMS;
     while (P < E) P <<= 1;
+    ProfScope ps(KID_MARKERS, s, 0.0);
     unsigned long long* keys = nullptr;
     int* flag = nullptr;
     int* pos = nullptr;
@@ -431,6 +434,7 @@ void spread_gather(const MarkerData& md, const T* lam, T* y, double scale, cudaS
         ew = reinterpret_cast<const T*>(md.ent_w64);
     else
         ew = reinterpret_cast<const T*>(md.ent_w32);
+    ProfScope ps(KID_SPREAD, s, (double)md.F * (8 + 4 + 2 * sizeof(T)) + (double)md.E * (4 + 2 * sizeof(T)));
     k_spread_gather<T><<<grid_1d(md.F, 128), 128, 0, s>>>(md.F, md.face, md.off, md.ent_m, ew, lam, y, (T)scale);
     IBR_CHECK_LAUNCH();
 }
@@ -441,6 +445,7 @@ void interp(const Geo& g, const MarkerData& md, const T* v, T* out, double sign,
     const T* w = sizeof(T) == 8 ? reinterpret_cast<const T*>(md.w64) : reinterpret_cast<const T*>(md.w32);
     int threads = 128;
     int blocks = grid_1d((long long)md.N * 32, threads);
+    ProfScope ps(KID_INTERP, s, (double)md.N * g.d * ((g.d == 3 ? 64 : 16) * sizeof(T) + g.d * 4 * sizeof(T) + sizeof(T)));
     if (g.d == 3)
         k_interp<3, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.base, w, v, out, (T)sign, add, (T)add_scale);
     else
@@ -450,17 +455,20 @@ void interp(const Geo& g, const MarkerData& md, const T* v, T* out, double sign,
 
 template <typename T>
 void lam_sum(int d, int N, const T* lam, double scale, double* shift, cudaStream_t s) {
+    ProfScope ps(KID_LAMSUM, s, (double)N * d * sizeof(T));
     k_lam_sum<T><<<1, 256, 0, s>>>(d, N, lam, scale, shift);
     IBR_CHECK_LAUNCH();
 }
 
 void rigid_K(int d, int N, const double* rel, const int* body, const double* UO, double* V, double sign,
              cudaStream_t s) {
+    ProfScope ps(KID_RIGID_K, s, (double)N * d * 8 * 3);
     k_rigid_K<<<grid_1d(N, 128), 128, 0, s>>>(d, N, rel, body, UO, V, sign);
     IBR_CHECK_LAUNCH();
 }
 
 void rigid_KT(int d, int B, const int* body_start, const double* rel, const double* lam, double* FT, cudaStream_t s) {
+    ProfScope ps(KID_RIGID_KT, s, 0.0);
     k_rigid_KT<<<B, 256, 0, s>>>(d, body_start, rel, lam, FT);
     IBR_CHECK_LAUNCH();
 }

@@ -23,7 +23,36 @@ struct Error {
         if (_e != cudaSuccess)                                                    \
             throw ::ibr::Error{IBR_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
     } while (0)
-#define IBR_CHECK_LAUNCH() IBR_CUDA_TRY(cudaGetLastError())
+// every kernel launch of the library goes through this check (and counter)
+void count_launch();
+#define IBR_CHECK_LAUNCH()                  \
+    do {                                    \
+        ::ibr::count_launch();              \
+        IBR_CUDA_TRY(cudaGetLastError());   \
+    } while (0)
+
+// kernel classes timed by the optional profiler (prof.cu)
+enum KernelId {
+    KID_STOKES, KID_RBGS, KID_RESTRICT, KID_PROLONG, KID_COARSE, KID_PS_DIV, KID_PS_FINISH,
+    KID_AXPBY, KID_SCALE, KID_CONVERT, KID_MDOT, KID_UPD_MDOT, KID_UPD_NORM, KID_NORM2, KID_COMBINE,
+    KID_BLOCK_MEANS, KID_SUB_MEANS, KID_SMALL, KID_SPREAD, KID_INTERP, KID_LAMSUM, KID_RIGID_K,
+    KID_RIGID_KT, KID_MARKERS, KID_MTILDE, KID_SPD_INV, KID_GEMV, KID_COUNT
+};
+// records CUDA events around the launches in its scope when profiling is on;
+// bytes = the algorithmic bytes those launches move
+class ProfScope {
+  public:
+    ProfScope(int kid, cudaStream_t s, double bytes);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    int kid_;
+    cudaStream_t s_;
+    double bytes_;
+    void* a_;
+};
 
 // ---------------------------------------------------------------------------
 // periodic cell grid (x fastest); n2 == 1 in 2-D

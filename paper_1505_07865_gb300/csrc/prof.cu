@@ -1,0 +1,118 @@
+// Launch counting and optional per-launch CUDA-event timing of every kernel
+// class of the library, with the algorithmic bytes each launch must move
+// (each array read or written once).  Process-wide; intended for one host
+// thread driving the library at a time.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ibr_internal.cuh"
+
+namespace ibr {
+
+static std::atomic<long long> g_launches{0};
+static bool g_prof = false;
+
+struct Pending {
+    int kid;
+    cudaEvent_t a, b;
+    double bytes;
+};
+struct Acc {
+    long long launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;
+};
+static std::mutex g_mu;
+static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_free;
+static Acc g_acc[KID_COUNT];
+
+static const char* kNames[KID_COUNT] = {
+    "stokes_apply", "mg_smooth_rbgs", "mg_residual_restrict", "mg_prolong_correct", "mg_coarse_solve",
+    "ps_divergence", "ps_finish", "vec_axpby", "vec_scale_copy", "vec_convert", "krylov_mdot",
+    "krylov_update_mdot", "krylov_update_norm2", "krylov_norm2", "krylov_combine", "block_means",
+    "subtract_means", "krylov_small", "spread_gather", "interp", "lam_sum", "rigid_K", "rigid_KT",
+    "markers_setup", "mtilde_build", "spd_inverse", "blockdiag_gemv",
+};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t get_event() {
+    if (!g_free.empty()) {
+        cudaEvent_t e = g_free.back();
+        g_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+ProfScope::ProfScope(int kid, cudaStream_t s, double bytes) : kid_(kid), s_(s), bytes_(bytes), a_(nullptr) {
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    a_ = get_event();
+    if (a_) cudaEventRecord((cudaEvent_t)a_, s_);
+}
+
+ProfScope::~ProfScope() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaEvent_t b = get_event();
+    if (!b) return;
+    cudaEventRecord(b, s_);
+    g_pending.push_back({kid_, (cudaEvent_t)a_, b, bytes_});
+}
+
+static void drain() {
+    for (auto& p : g_pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        Acc& a = g_acc[p.kid];
+        a.launches++;
+        a.ms += ms;
+        a.bytes += p.bytes;
+        g_free.push_back(p.a);
+        g_free.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+}  // namespace ibr
+
+extern "C" {
+
+int ibr_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(ibr::g_mu);
+    ibr::g_prof = on != 0;
+    return IBR_OK;
+}
+
+int ibr_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(ibr::g_mu);
+    ibr::drain();
+    for (auto& a : ibr::g_acc) a = ibr::Acc();
+    return IBR_OK;
+}
+
+int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes) {
+    if (idx < 0 || idx >= ibr::KID_COUNT) return IBR_EINVAL;
+    std::lock_guard<std::mutex> lk(ibr::g_mu);
+    ibr::drain();
+    const ibr::Acc& a = ibr::g_acc[idx];
+    if (name && name_len > 0) {
+        std::strncpy(name, ibr::kNames[idx], (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (launches) *launches = a.launches;
+    if (ms) *ms = a.ms;
+    if (bytes) *bytes = a.bytes;
+    return IBR_OK;
+}
+
+long long ibr_launch_count(void) { return ibr::g_launches.load(); }
+
+}  // extern "C"

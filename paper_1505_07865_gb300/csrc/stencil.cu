@@ -271,6 +271,7 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
     T kh2 = (T)(eta / (g.h * g.h));
     T ih = (T)(1.0 / g.h);
     int nb = grid_1d(g.ncell, 256);
+    ProfScope ps(KID_STOKES, s, 2.0 * (g.d + 1) * g.ncell * sizeof(T));
     if (g.d == 3)
         k_stokes<3, T><<<nb, 256, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
     else
@@ -283,6 +284,8 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa
                cudaStream_t s) {
     T kh2 = (T)(kappa / (g.h * g.h));
     dim3 grid(grid_1d(g.ncell / 2, 256), C);
+    // half sweep: read the other colour and f of this colour, write this colour
+    ProfScope ps(KID_RBGS, s, (zero_init ? 1.0 : 1.5) * C * g.ncell * sizeof(T));
     if (g.d == 3)
         k_rbgs<3, T><<<grid, 256, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
     else
@@ -295,6 +298,7 @@ void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, 
                           double kappa, cudaStream_t s) {
     T kh2 = (T)(kappa / (gf.h * gf.h));
     dim3 grid(grid_1d(gc.ncell, 256), C);
+    ProfScope ps(KID_RESTRICT, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
     if (gf.d == 3)
         k_resid_restrict<3, T><<<grid, 256, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
     else
@@ -305,6 +309,7 @@ void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, 
 template <typename T>
 void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, cudaStream_t s) {
     dim3 grid(grid_1d(gf.ncell, 256), C);
+    ProfScope ps(KID_PROLONG, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
     if (gf.d == 3)
         k_prolong<3, T><<<grid, 256, 0, s>>>(u, uc, gf, gc);
     else
@@ -318,6 +323,7 @@ void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double
     T kh2 = (T)(kappa / (g.h * g.h));
     size_t sm = 2 * (size_t)g.ncell * sizeof(T);
     int nt = g.ncell >= 1024 ? 1024 : (int)((g.ncell + 31) / 32 * 32);
+    ProfScope ps(KID_COARSE, s, 2.0 * C * g.ncell * sizeof(T));
     if (g.d == 3)
         k_coarse<3, T><<<C, nt, sm, s>>>(u, f, g, (T)sigma, kh2, sweeps);
     else
@@ -328,6 +334,7 @@ void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s) {
     int nb = grid_1d(g.ncell, 256);
+    ProfScope ps(KID_PS_DIV, s, (g.d + 3.0) * g.ncell * sizeof(T));
     if (g.d == 3)
         k_ps_div<3, T><<<nb, 256, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
     else
@@ -339,6 +346,7 @@ template <typename T>
 void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double c_q, double c_phi,
                cudaStream_t s) {
     int nb = grid_1d(g.ncell, 256);
+    ProfScope ps(KID_PS_FINISH, s, (2.0 * g.d + 3.0) * g.ncell * sizeof(T));
     if (g.d == 3)
         k_ps_finish<3, T><<<nb, 256, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
     else

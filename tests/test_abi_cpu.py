@@ -24,7 +24,7 @@ def abi():
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(ibr_\w+)\s*\(", txt, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(ibr_\w+)\s*\(", txt, flags=re.M)))
 
 
 def test_header_declares_the_abi():
