@@ -210,6 +210,26 @@ int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
  * f and returns mean-zero u. */
 int ibr_op_vcycle(ibr_grid* g, double sigma, double kappa, const double* f, double* u, int k);
 
+/* The V-cycles of ibr_op_vcycle (FP64, the grid's default 2/2 sweeps when
+ * pre = post = 2) for callers that cannot allocate device memory: code running
+ * inside an application that gives all device memory to its own pool
+ * allocator, a plug-in inside a host program that owns the CUDA context, or
+ * any caller that must not trigger the allocator's device-wide
+ * synchronisation.  The paper has no counterpart; this is an interface
+ * service.  No grid handle: dim, n[dim] (even, >= 4), L[dim] describe the
+ * periodic cell grid; f (right-hand side) and u (initial guess in, result out)
+ * are device arrays of n[0]*...*n[dim-1] doubles owned by the caller; k
+ * V-cycles of pre/post red-black sweeps are issued on cuda_stream (NULL: the
+ * legacy default stream); asynchronous.  The coarse-level buffers live in one
+ * 4 MiB file-scope device array (524288 doubles, enough for grids up to 96^3
+ * or 1024x512); a grid whose coarse levels need more returns IBR_EINVAL with
+ * a message.  Nothing is allocated or freed.  The first call on each device
+ * looks up the array's device address (make that first call before any stream
+ * capture).  Every call shares the array: calls that overlap on the GPU race,
+ * and the array keeps the last call's contents. */
+int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, double sigma, double kappa,
+                          const double* f, double* u, int k, int pre, int post, void* cuda_stream);
+
 /* ---- instrumentation (measurement support; the paper has no counterpart) ---
  * Process-wide.  ibr_launch_count: kernels launched by the library since it
  * was loaded.  ibr_profile_enable(1): from then on every launch is bracketed

@@ -98,6 +98,8 @@ _SIGS = {
     "ibr_op_vcycle": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_int]),
     "ibr_destroy_grid": (ctypes.c_int, [_P]),
     "ibr_last_error": (ctypes.c_char_p, []),
+    "ibr_op_vcycle_noalloc": (ctypes.c_int, [ctypes.c_int, _I, _D, ctypes.c_double, ctypes.c_double, _P, _P,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "ibr_launch_count": (ctypes.c_longlong, []),
     "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ibr_profile_reset": (ctypes.c_int, []),
@@ -268,6 +270,16 @@ def op_stokes_pc(grid, r, z):
 
 def op_vcycle(grid, sigma, kappa, f, u, k):
     _check(_lib.ibr_op_vcycle(grid, float(sigma), float(kappa), _dev(f), _dev(u), int(k)))
+
+
+def op_vcycle_noalloc(dim, n, L, sigma, kappa, f, u, k, pre=2, post=2, stream=None):
+    """ibr_op_vcycle_noalloc: k V-cycles with the library's static scratch
+    (no device allocation); f, u float64 CUDA tensors."""
+    n_arr = (ctypes.c_int * 3)(*(list(n) + [0] * (3 - len(n))))
+    L_arr = (ctypes.c_double * 3)(*(list(L) + [0.0] * (3 - len(L))))
+    s = None if stream is None else _P(int(stream))
+    _check(_lib.ibr_op_vcycle_noalloc(int(dim), n_arr, L_arr, float(sigma), float(kappa), _dev(f), _dev(u),
+                                      int(k), int(pre), int(post), s))
 
 
 def destroy_grid(grid):
