@@ -264,6 +264,174 @@ inline int blocks_for(long long n) {
     return (int)b;
 }
 
+// ---- classical Gram-Schmidt with reorthogonalisation only when needed ------
+// st[0] = |w|^2 before projection, st[1] = 1 if a second pass is needed,
+// st[2] = |w_perp|^2 used to normalise.
+
+// partial[blk*(k+1) + j] = V_j . w (j < k) and w . w (j == k)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_norm(long long n, const T* __restrict__ V, long long ld, int k,
+                                                           const T* __restrict__ w, double* __restrict__ partial,
+                                                           const double* __restrict__ st) {
+    if (st && st[1] == 0.0) return;
+    const int K1 = k + 1;
+    for (int j0 = 0; j0 < K1; j0 += MDOT_CHUNK) {
+        double acc[MDOT_CHUNK];
+        T tacc[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
+        int nq = min(MDOT_CHUNK, K1 - j0);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            T wi = w[i];
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q) {
+                int j = j0 + q;
+                if (q < nq) tacc[q] += (j < k ? V[(long long)j * ld + i] : wi) * wi;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q];
+        __shared__ double outv[MDOT_CHUNK];
+        block_sum<MDOT_CHUNK>(acc, outv);
+        if (threadIdx.x < nq) partial[(long long)blockIdx.x * K1 + j0 + threadIdx.x] = outv[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// after the first pass: dots hk[0..k) and |w|^2 = hk[k]; decide on a second
+// pass (|w_perp|^2 < |w|^2 / 2, the "twice is enough" test) and clear h2
+__global__ void k_cgs_state(const double* hk, int k, double* st, double* h2) {
+    double nw2 = hk[k], s = 0.0;
+    for (int j = 0; j < k; ++j) s += hk[j] * hk[j];
+    double nu2 = nw2 - s;
+    st[0] = nw2;
+    st[1] = (nu2 < 0.5 * nw2) ? 1.0 : 0.0;
+    st[2] = nu2 > 0.0 ? nu2 : 0.0;
+    for (int j = 0; j < k; ++j) h2[j] = 0.0;
+}
+
+// second pass (only when st[1] != 0): w -= V h1
+template <typename T>
+__global__ void k_cgs_sub(long long n, const T* __restrict__ V, long long ld, int k, const double* __restrict__ h,
+                          T* __restrict__ w, const double* __restrict__ st) {
+    if (st[1] == 0.0) return;
+    __shared__ double hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        w[i] -= s;
+    }
+}
+
+// after the second pass's dots: h2 and |w_perp|^2
+__global__ void k_cgs_state2(const double* hk2, int k, double* st, double* h2) {
+    if (st[1] == 0.0) return;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) {
+        h2[j] = hk2[j];
+        s += hk2[j] * hk2[j];
+    }
+    double nu2 = hk2[k] - s;
+    st[2] = nu2 > 0.0 ? nu2 : 0.0;
+}
+
+// V_{k} = (w - sum_j hsel_j V_j) / sqrt(st[2]), hsel = st[1] ? h2 : h1; also an
+// optional copy of the first n32 entries in the preconditioner precision
+template <typename T, typename T2>
+__global__ void k_cgs_normalize(long long n, const T* __restrict__ V, long long ld, int k,
+                                const double* __restrict__ h1, const double* __restrict__ h2,
+                                const double* __restrict__ st, const T* w, T* vout,  // may alias
+                                T2* __restrict__ out2, long long n2) {
+    __shared__ double hs[128];
+    const double* h = st[1] != 0.0 ? h2 : h1;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    double nu = sqrt(st[2]);
+    T inv = (T)(nu > 0.0 ? 1.0 / nu : 0.0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        T v = (w[i] - s) * inv;
+        vout[i] = v;
+        if (out2 && i < n2) out2[i] = (T2)v;
+    }
+}
+
+// y = x * inv_sqrt(*nrm2), plus an optional copy of the first n2 entries
+template <typename T, typename T2>
+__global__ void k_scale_rsqrt(long long n, const double* __restrict__ nrm2, const T* __restrict__ x, T* __restrict__ y,
+                              T2* __restrict__ out2, long long n2) {
+    double nr = sqrt(fmax(*nrm2, 0.0));
+    T a = (T)(nr > 0.0 ? 1.0 / nr : 0.0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        T v = a * x[i];
+        y[i] = v;
+        if (out2 && i < n2) out2[i] = (T2)v;
+    }
+}
+
+}  // namespace
+
+template <typename T, typename T2>
+void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* vout, T2* out2, long long n2,
+                        double* partial, double* h1, double* h2, double* hk2, double* st, cudaStream_t s) {
+    {
+        ProfScope ps(KID_MDOT, s, (k + 1.0) * n * sizeof(T));
+        k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
+        IBR_CHECK_LAUNCH();
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, h1);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        ProfScope ps(KID_SMALL, s, 0.0);
+        k_cgs_state<<<1, 1, 0, s>>>(h1, k, st, h2);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        // second pass, skipped inside the kernels unless st[1] != 0
+        ProfScope ps(KID_UPD_MDOT, s, 0.0);
+        k_cgs_sub<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, w, st);
+        IBR_CHECK_LAUNCH();
+        k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, st);
+        IBR_CHECK_LAUNCH();
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, hk2);
+        IBR_CHECK_LAUNCH();
+        k_cgs_state2<<<1, 1, 0, s>>>(hk2, k, st, h2);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        ProfScope ps(KID_UPD_NORM, s, (k + 2.0) * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
+        k_cgs_normalize<T, T2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, h2, st, w, vout, out2, n2);
+        IBR_CHECK_LAUNCH();
+    }
+}
+
+template <typename T, typename T2>
+void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s) {
+    ProfScope ps(KID_SCALE, s, 2.0 * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
+    k_scale_rsqrt<T, T2><<<blocks_for(n), 256, 0, s>>>(n, nrm2, x, y, out2, n2);
+    IBR_CHECK_LAUNCH();
+}
+
+template void cgs_orthonormalize<double, float>(long long, const double*, long long, int, double*, double*, float*,
+                                                long long, double*, double*, double*, double*, double*, cudaStream_t);
+template void cgs_orthonormalize<double, double>(long long, const double*, long long, int, double*, double*, double*,
+                                                 long long, double*, double*, double*, double*, double*, cudaStream_t);
+template void cgs_orthonormalize<float, float>(long long, const float*, long long, int, float*, float*, float*,
+                                               long long, double*, double*, double*, double*, double*, cudaStream_t);
+template void scale_rsqrt<double, float>(long long, const double*, const double*, double*, float*, long long,
+                                         cudaStream_t);
+template void scale_rsqrt<double, double>(long long, const double*, const double*, double*, double*, long long,
+                                          cudaStream_t);
+template void scale_rsqrt<float, float>(long long, const double*, const float*, float*, float*, long long,
+                                        cudaStream_t);
+
+namespace {
 }  // namespace
 
 template <typename T>

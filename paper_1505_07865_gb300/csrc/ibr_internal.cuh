@@ -145,6 +145,19 @@ void block_means(long long m, int C, const T* x, double* partial, double* out, c
 template <typename T>
 void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t s);
 
+// One Arnoldi step's orthonormalisation against V_0..V_{k-1} (classical
+// Gram-Schmidt, second pass only when |w_perp|^2 < |w|^2 / 2):
+//   h1[0..k) = V^T w, h1[k] = |w|^2; h2 = second-pass coefficients (or 0);
+//   st[2] = |w_perp|^2; vout = w_perp / |w_perp| (vout may alias w);
+//   out2[0..n2) = vout[0..n2) converted to T2 (if out2 != NULL).
+// h1, hk2 hold k+1 doubles; h2 k; st 3; partial RED_BLOCKS*(k+1).
+template <typename T, typename T2>
+void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* vout, T2* out2, long long n2,
+                        double* partial, double* h1, double* h2, double* hk2, double* st, cudaStream_t s);
+// y = x / sqrt(*nrm2) (0 if nrm2 == 0), plus optional out2[0..n2) copy
+template <typename T, typename T2>
+void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s);
+
 // small single-thread kernels for the Arnoldi/Givens bookkeeping (FP64)
 // H column j (k = j+2 entries) assembled from h1 + h2 and the norm; Givens
 // rotations applied, new rotation formed, res_out = |g[j+1]|.

@@ -1,8 +1,9 @@
 // Host orchestration and the C ABI of libibrigid.
 //
 // Outer solver: right-preconditioned flexible GMRES in FP64 on the
-// constrained system (Sec. V), CGS2 Arnoldi and Givens rotations on the
-// device, true residual recomputed at every restart and at exit.
+// constrained system (Sec. V), Arnoldi by classical Gram-Schmidt with a
+// second pass only when needed, Givens rotations on the device, true residual
+// recomputed at every restart and at exit.
 // Preconditioner: the Schur-complement preconditioner of Sec. V.A
 //   1. inner GMRES(N_s) on the unconstrained Stokes system, each step
 //      preconditioned by P_S (Sec. V.B, Eq. P1_practical) = one vector
@@ -188,6 +189,7 @@ struct ibr_grid {
     double *V = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *w = nullptr;
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
     double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr, *shift = nullptr, *means = nullptr;
+    double *hk2 = nullptr, *st = nullptr;
     double* host_sc = nullptr;  // pinned
     double* FT = nullptr;
     double* UO = nullptr;
@@ -211,7 +213,7 @@ struct PC {
     T *Vi = nullptr, *Zi = nullptr, *w = nullptr, *rs = nullptr, *rs2 = nullptr, *xs = nullptr;
     T *y = nullptr, *phi = nullptr, *q = nullptr, *qr = nullptr, *dU = nullptr, *lamT = nullptr;
     double *Hi = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr, *h1 = nullptr, *h2 = nullptr;
-    double *sc = nullptr, *partial = nullptr, *means = nullptr, *shift = nullptr;
+    double *sc = nullptr, *partial = nullptr, *means = nullptr, *shift = nullptr, *hk2 = nullptr, *st = nullptr;
     const T* Minv = nullptr;
     int pre = 2, post = 2, variant = IBR_PC_LOWER;
     long long ps_count = 0;
@@ -235,8 +237,10 @@ struct PC {
         sn = dalloc<double>(ns + 1);
         gv = dalloc<double>(ns + 2);
         yv = dalloc<double>(ns + 1);
-        h1 = dalloc<double>(ns + 1);
+        h1 = dalloc<double>(ns + 2);
         h2 = dalloc<double>(ns + 1);
+        hk2 = dalloc<double>(ns + 2);
+        st = dalloc<double>(4);
         sc = dalloc<double>(8);
         partial = dalloc<double>((size_t)RED_BLOCKS * std::max(ns + 1, 4));
         means = dalloc<double>(4);
@@ -255,7 +259,7 @@ struct PC {
         T* tp[] = {Vi, Zi, w, rs, rs2, xs, y, phi, q, qr, dU, lamT};
         for (T* p : tp)
             if (p) cudaFree(p);
-        double* dp[] = {Hi, cs, sn, gv, yv, h1, h2, sc, partial, means, shift};
+        double* dp[] = {Hi, cs, sn, gv, yv, h1, h2, sc, partial, means, shift, hk2, st};
         for (double* p : dp)
             if (p) cudaFree(p);
     }
@@ -282,24 +286,23 @@ struct PC {
         long long nS = G->nS;
         norm2<T>(nS, rhs, partial, sc + 0, s);
         givens_init(sc + 0, gv, ns + 1, sc + 1, sc + 2, s);
-        vec_scale_copy<T>(nS, sc + 2, false, rhs, Vi, s);
+        scale_rsqrt<T, T>(nS, sc + 0, rhs, Vi, nullptr, 0, s);
         for (int j = 0; j < ns; ++j) {
             T* Vj = Vi + (long long)j * nS;
             T* Zj = Zi + (long long)j * nS;
             apply_ps(Vj, Zj);
             stokes_apply<T>(g, Zj, w, G->sigma(), G->eta, nullptr, s);
-            mdot<T>(nS, Vi, nS, j + 1, w, partial, h1, s);
-            update_mdot<T>(nS, Vi, nS, j + 1, h1, w, partial, h2, s);
-            update_norm2<T>(nS, Vi, nS, j + 1, h2, w, partial, sc + 0, s);
-            arnoldi_column(Hi, ns + 1, h1, h2, sc + 0, j, cs, sn, gv, sc + 3, sc + 4, s);
-            if (j + 1 < ns) vec_scale_copy<T>(nS, sc + 4, false, w, Vi + (long long)(j + 1) * nS, s);
+            // the last step only needs its Hessenberg column: normalise in place
+            T* vnext = (j + 1 < ns) ? Vi + (long long)(j + 1) * nS : w;
+            cgs_orthonormalize<T, T>(nS, Vi, nS, j + 1, w, vnext, nullptr, 0, partial, h1, h2, hk2, st, s);
+            arnoldi_column(Hi, ns + 1, h1, h2, st + 2, j, cs, sn, gv, sc + 3, sc + 4, s);
         }
         hess_solve(Hi, ns + 1, gv, ns, yv, s);
         combine<T, T>(nS, Zi, nS, ns, yv, xout, false, s);
     }
 
     // z = P^-1 r for the constrained system (Sec. V.A), FP64 in and out
-    void apply(const double* r, double* z) {
+    void apply(const double* r, double* z, bool fluid_prepared = false) {
         cudaStream_t s = G->stream;
         const Geo& g = G->geo;
         long long n = g.ncell, nS = G->nS;
@@ -309,7 +312,7 @@ struct PC {
         if (sizeof(T) == sizeof(double)) {
             rin = reinterpret_cast<const T*>(r);
         } else {
-            vec_convert<double, T>(nS, r, rs, s);
+            if (!fluid_prepared) vec_convert<double, T>(nS, r, rs, s);
             rin = rs;
         }
         inner_gmres(rin, xs);                                                // step 1
@@ -390,7 +393,7 @@ void free_markers(ibr_grid* G) {
 
 void free_outer(ibr_grid* G) {
     double** ps[] = {&G->V, &G->Z, &G->b, &G->x, &G->w, &G->H, &G->cs, &G->sn, &G->gv, &G->yv,
-                     &G->h1, &G->h2, &G->sc, &G->partial, &G->shift, &G->means};
+                     &G->h1, &G->h2, &G->sc, &G->partial, &G->shift, &G->means, &G->hk2, &G->st};
     for (double** p : ps) dfree(*p);
     G->m_alloc = 0;
 }
@@ -599,8 +602,10 @@ void ensure_outer(ibr_grid* G, int m) {
     G->sn = dalloc<double>(m + 1);
     G->gv = dalloc<double>(m + 2);
     G->yv = dalloc<double>(m + 1);
-    G->h1 = dalloc<double>(m + 1);
+    G->h1 = dalloc<double>(m + 2);
     G->h2 = dalloc<double>(m + 1);
+    G->hk2 = dalloc<double>(m + 2);
+    G->st = dalloc<double>(4);
     G->sc = dalloc<double>(8);
     G->partial = dalloc<double>((size_t)RED_BLOCKS * std::max(m + 1, 4));
     G->shift = dalloc<double>(4);
@@ -629,11 +634,12 @@ void full_matvec(ibr_grid* G, const double* x, double* y) {
     }
 }
 
-void pc_apply(ibr_grid* G, const double* r, double* z) {
+// fluid_prepared: the FP32 copy of r's fluid part is already in pc32->rs
+void pc_apply(ibr_grid* G, const double* r, double* z, bool fluid_prepared) {
     if (G->precision == IBR_FP64)
         G->pc64->apply(r, z);
     else
-        G->pc32->apply(r, z);
+        G->pc32->apply(r, z, fluid_prepared);
 }
 
 double read_scalar(ibr_grid* G, const double* dev) {
@@ -712,28 +718,29 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
             break;
         }
         givens_init(G->sc + 0, G->gv, m + 1, G->sc + 1, G->sc + 2, s);
-        vec_scale_copy<double>(len, G->sc + 2, false, G->w, G->V, s);
+        // V_0 = r / |r|; in mixed precision the preconditioner's FP32 copy of
+        // its fluid part is written by the same pass
+        float* rs32 = G->precision == IBR_MIXED ? G->pc32->rs : nullptr;
+        scale_rsqrt<double, float>(len, G->sc + 0, G->w, G->V, rs32, G->nS, s);
         int k = 0;
         last_cycle_converged_est = false;
         for (int j = 0; j < m; ++j) {
             double* Vj = G->V + (long long)j * len;
             double* Zj = G->Z + (long long)j * len;
-            pc_apply(G, Vj, Zj);
+            pc_apply(G, Vj, Zj, true);
             full_matvec(G, Zj, G->w);
-            mdot<double>(len, G->V, len, j + 1, G->w, G->partial, G->h1, s);
-            update_mdot<double>(len, G->V, len, j + 1, G->h1, G->w, G->partial, G->h2, s);
-            update_norm2<double>(len, G->V, len, j + 1, G->h2, G->w, G->partial, G->sc + 0, s);
-            arnoldi_column(G->H, m + 1, G->h1, G->h2, G->sc + 0, j, G->cs, G->sn, G->gv, G->sc + 3, G->sc + 4, s);
-            vec_scale_copy<double>(len, G->sc + 4, false, G->w, G->V + (long long)(j + 1) * len, s);
+            cgs_orthonormalize<double, float>(len, G->V, len, j + 1, G->w, G->V + (long long)(j + 1) * len, rs32,
+                                              G->nS, G->partial, G->h1, G->h2, G->hk2, G->st, s);
+            arnoldi_column(G->H, m + 1, G->h1, G->h2, G->st + 2, j, G->cs, G->sn, G->gv, G->sc + 3, G->sc + 4, s);
             k = j + 1;
             info.iters++;
             double est = read_scalar(G, G->sc + 3);
             info.rel_res_est = est / bnorm;
             if (verbose) {
-                double hn = std::sqrt(read_scalar(G, G->sc + 0));
-                double h1j = read_scalar(G, G->h1 + j);
-                std::fprintf(stderr, "[ibr] it %d j %d est %.3e |w_perp| %.3e h1[j] %.3e\n", info.iters, j,
-                             est / bnorm, hn, h1j);
+                double hn = std::sqrt(read_scalar(G, G->st + 2));
+                double re = read_scalar(G, G->st + 1);
+                std::fprintf(stderr, "[ibr] it %d j %d est %.3e |w_perp| %.3e reorth %d\n", info.iters, j,
+                             est / bnorm, hn, (int)re);
             }
             if (std::isnan(est)) throw Error{IBR_ENUMERIC, "NaN in the FGMRES Arnoldi process"};
             if (est <= target) last_cycle_converged_est = true;
