@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None, help="steps of the all-FP64 comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--quick", action="store_true",
+                    help="mixed-precision arm only (no profile, e2e, FP64 or CPU legs); for profiler runs")
     return ap.parse_args()
 
 
@@ -274,6 +276,16 @@ def run_ours(args, world, rank, local):
     barrier()
     total_ms = max_over_ranks(total_ms)
     value = world * args.steps / (total_ms / 1000.0)
+    if args.quick:
+        abi.destroy_grid(G)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "quick": True,
+                              "iters_per_solve": float(np.mean([i.iters for i in infos])),
+                              "gpu_launches": int(launches)}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     # ---- per-kernel CUDA-event profile of the same steps (separate pass) ----
     abi.profile_reset()
