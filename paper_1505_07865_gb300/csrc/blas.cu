@@ -281,8 +281,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_norm(long long n, const T*
 #pragma unroll
         for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
         int nq = min(MDOT_CHUNK, K1 - j0);
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x) {
+        T tacc2[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) tacc2[q] = T(0);
+        // two elements per trip (i and i + stride) keep twice the loads in flight
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        for (; i + stride < n; i += 2 * stride) {
+            T wa = w[i], wb = w[i + stride];
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q) {
+                int j = j0 + q;
+                if (q < nq) {
+                    T va = j < k ? V[(long long)j * ld + i] : wa;
+                    T vb = j < k ? V[(long long)j * ld + i + stride] : wb;
+                    tacc[q] += va * wa;
+                    tacc2[q] += vb * wb;
+                }
+            }
+        }
+        if (i < n) {
             T wi = w[i];
 #pragma unroll
             for (int q = 0; q < MDOT_CHUNK; ++q) {
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_norm(long long n, const T*
             }
         }
 #pragma unroll
-        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q];
+        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q] + (double)tacc2[q];
         __shared__ double outv[MDOT_CHUNK];
         block_sum<MDOT_CHUNK>(acc, outv);
         if (threadIdx.x < nq) partial[(long long)blockIdx.x * K1 + j0 + threadIdx.x] = outv[threadIdx.x];
@@ -300,13 +318,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_norm(long long n, const T*
 }
 
 // after the first pass: dots hk[0..k) and |w|^2 = hk[k]; decide on a second
-// pass (|w_perp|^2 < |w|^2 / 2, the "twice is enough" test) and clear h2
+// pass and clear h2.  One classical Gram-Schmidt pass leaves the new vector
+// orthogonal to about eps * sqrt(k) * |w| / |w_perp|; a second pass is taken
+// when |w_perp| < 1e-3 |w|, i.e. when that loss could exceed ~1e-12.
 __global__ void k_cgs_state(const double* hk, int k, double* st, double* h2) {
     double nw2 = hk[k], s = 0.0;
     for (int j = 0; j < k; ++j) s += hk[j] * hk[j];
     double nu2 = nw2 - s;
     st[0] = nw2;
-    st[1] = (nu2 < 0.5 * nw2) ? 1.0 : 0.0;
+    st[1] = (nu2 < 1e-6 * nw2) ? 1.0 : 0.0;
     st[2] = nu2 > 0.0 ? nu2 : 0.0;
     for (int j = 0; j < k; ++j) h2[j] = 0.0;
 }
@@ -352,8 +372,25 @@ __global__ void k_cgs_normalize(long long n, const T* __restrict__ V, long long 
     __syncthreads();
     double nu = sqrt(st[2]);
     T inv = (T)(nu > 0.0 ? 1.0 / nu : 0.0);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {
+        T sa = T(0), sb = T(0);
+        for (int j = 0; j < k; ++j) {
+            T hj = (T)hs[j];
+            sa += hj * V[(long long)j * ld + i];
+            sb += hj * V[(long long)j * ld + i + stride];
+        }
+        T va = (w[i] - sa) * inv;
+        T vb = (w[i + stride] - sb) * inv;
+        vout[i] = va;
+        vout[i + stride] = vb;
+        if (out2) {
+            if (i < n2) out2[i] = (T2)va;
+            if (i + stride < n2) out2[i + stride] = (T2)vb;
+        }
+    }
+    if (i < n) {
         T s = T(0);
         for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
         T v = (w[i] - s) * inv;

@@ -92,6 +92,12 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
 template <typename T>
 void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int color, bool zero_init,
                cudaStream_t s);
+// one full red-black sweep (colour c0, then 1 - c0), out of place, for 3-D
+// levels accepted by mg_fused_ok; identical result to two mg_smooth calls
+bool mg_fused_ok(const Geo& g);
+template <typename T>
+void mg_sweep_fused(const Geo& g, const T* u_old, const T* f, T* u_new, int C, double sigma, double kappa, int c0,
+                    bool zero_init, cudaStream_t s);
 template <typename T>
 void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
                           double kappa, cudaStream_t s);

@@ -93,6 +93,99 @@ __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __rest
     uu[n.c] = (ff[n.c] + kh2 * nb) / diag;
 }
 
+// One full red-black Gauss-Seidel sweep (colour c0 first, then 1 - c0) of a
+// 3-D periodic field, out of place: u_new = sweep(u_old).  Same arithmetic and
+// summation order as two k_rbgs half sweeps, so the result is identical.
+// A CTA owns a FX x FY column of cells and marches along z over [z0, z0+FZ):
+// at plane p it loads u_old(p+1) with a 2-cell in-plane halo, updates the
+// first colour on plane p over the tile plus a 1-cell ring (recomputed by the
+// neighbouring CTAs too, so no CTA reads another's output), then updates the
+// second colour on plane p-1 from the first-colour values of planes p-2..p.
+constexpr int FX = 32, FY = 8, FZ = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(FX* FY) k_rbgs_fused3d(const T* __restrict__ uo, const T* __restrict__ f,
+                                                         T* __restrict__ un, Geo g, T sigma, T kh2, int c0,
+                                                         int zero_init) {
+    __shared__ T su[3][FY + 4][FX + 4];   // u_old planes p-1, p, p+1 (ring)
+    __shared__ T sr[3][FY + 2][FX + 2];   // first-colour values, planes p-2, p-1, p (ring)
+    __shared__ T sf[2][FY + 2][FX + 2];   // f planes p-1, p (ring)
+    const int cmp = blockIdx.z;
+    const long long off = (long long)cmp * g.ncell;
+    uo += off;
+    f += off;
+    un += off;
+    const int ntx = g.n0 / FX;
+    const int bx = (blockIdx.x % ntx) * FX, by = (blockIdx.x / ntx) * FY;
+    const int z0 = blockIdx.y * FZ;
+    const int z1 = min(z0 + FZ, g.n2);
+    const int tid = threadIdx.x;
+    const long long sy = g.n0, sz = (long long)g.n0 * g.n1;
+    const T diag = sigma + T(6) * kh2;
+    auto wrap = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+    auto load_u = [&](int p) {
+        int slot = ((p % 3) + 3) % 3, pz = wrap(p, g.n2);
+        for (int e = tid; e < (FY + 4) * (FX + 4); e += FX * FY) {
+            int ly = e / (FX + 4), lx = e % (FX + 4);
+            int gx = wrap(bx + lx - 2, g.n0), gy = wrap(by + ly - 2, g.n1);
+            su[slot][ly][lx] = zero_init ? T(0) : uo[gx + sy * gy + sz * pz];
+        }
+    };
+    auto load_f = [&](int p) {
+        int slot = ((p % 2) + 2) % 2, pz = wrap(p, g.n2);
+        for (int e = tid; e < (FY + 2) * (FX + 2); e += FX * FY) {
+            int ly = e / (FX + 2), lx = e % (FX + 2);
+            int gx = wrap(bx + lx - 1, g.n0), gy = wrap(by + ly - 1, g.n1);
+            sf[slot][ly][lx] = f[gx + sy * gy + sz * pz];
+        }
+    };
+    load_u(z0 - 2);
+    load_u(z0 - 1);
+    for (int p = z0 - 1; p <= z1; ++p) {
+        load_u(p + 1);
+        load_f(p);
+        __syncthreads();
+        // first colour on plane p, tile + 1-cell ring
+        {
+            const int s0 = ((p - 1) % 3 + 3) % 3, s1 = ((p % 3) + 3) % 3, s2 = ((p + 1) % 3 + 3) % 3;
+            const int fs = ((p % 2) + 2) % 2, rs = s1;
+            for (int e = tid; e < (FY + 2) * (FX + 2); e += FX * FY) {
+                int ly = e / (FX + 2), lx = e % (FX + 2);
+                int gx = bx + lx - 1, gy = by + ly - 1;
+                int pz = wrap(p, g.n2);
+                int colour = (wrap(gx, g.n0) + wrap(gy, g.n1) + pz) & 1;
+                if (colour != c0) continue;
+                int ux = lx + 1, uy = ly + 1;
+                // the association of nbr_sum: (x+ + x- + y+ + y-) + (z+ + z-)
+                T nb = zero_init ? T(0)
+                                 : (su[s1][uy][ux + 1] + su[s1][uy][ux - 1] + su[s1][uy + 1][ux] + su[s1][uy - 1][ux]) +
+                                       (su[s2][uy][ux] + su[s0][uy][ux]);
+                sr[rs][ly][lx] = (sf[fs][ly][lx] + kh2 * nb) / diag;
+            }
+        }
+        __syncthreads();
+        // second colour on plane p-1, tile interior; write both colours
+        const int q = p - 1;
+        if (q >= z0) {
+            const int r0 = ((q - 1) % 3 + 3) % 3, r1 = ((q % 3) + 3) % 3, r2 = ((q + 1) % 3 + 3) % 3;
+            const int fs = ((q % 2) + 2) % 2;
+            int lx = tid % FX, ly = tid / FX;
+            int gx = bx + lx, gy = by + ly, qz = wrap(q, g.n2);
+            int colour = (gx + gy + qz) & 1;
+            T val;
+            if (colour == c0) {
+                val = sr[r1][ly + 1][lx + 1];
+            } else {
+                T nb = (sr[r1][ly + 1][lx + 2] + sr[r1][ly + 1][lx] + sr[r1][ly + 2][lx + 1] + sr[r1][ly][lx + 1]) +
+                       (sr[r2][ly + 1][lx + 1] + sr[r0][ly + 1][lx + 1]);
+                val = (sf[fs][ly + 1][lx + 1] + kh2 * nb) / diag;
+            }
+            un[gx + sy * gy + sz * qz] = val;
+        }
+        __syncthreads();
+    }
+}
+
 // coarse f = average over the 2^D children of the fine residual f - (sigma u - kh2 Lap u)
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
@@ -293,6 +386,18 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa
     IBR_CHECK_LAUNCH();
 }
 
+bool mg_fused_ok(const Geo& g) { return g.d == 3 && g.n0 % FX == 0 && g.n1 % FY == 0 && g.n2 >= 4; }
+
+template <typename T>
+void mg_sweep_fused(const Geo& g, const T* u_old, const T* f, T* u_new, int C, double sigma, double kappa, int c0,
+                    bool zero_init, cudaStream_t s) {
+    T kh2 = (T)(kappa / (g.h * g.h));
+    dim3 grid((g.n0 / FX) * (g.n1 / FY), (g.n2 + FZ - 1) / FZ, C);
+    ProfScope ps(KID_RBGS, s, (zero_init ? 2.0 : 3.0) * C * g.ncell * sizeof(T));
+    k_rbgs_fused3d<T><<<grid, FX * FY, 0, s>>>(u_old, f, u_new, g, (T)sigma, kh2, c0, zero_init ? 1 : 0);
+    IBR_CHECK_LAUNCH();
+}
+
 template <typename T>
 void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
                           double kappa, cudaStream_t s) {
@@ -357,6 +462,8 @@ void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double 
 #define IBR_INST(T)                                                                                        \
     template void stokes_apply<T>(const Geo&, const T*, T*, double, double, const double*, cudaStream_t); \
     template void mg_smooth<T>(const Geo&, T*, const T*, int, double, double, int, bool, cudaStream_t);   \
+    template void mg_sweep_fused<T>(const Geo&, const T*, const T*, T*, int, double, double, int, bool,      \
+                                    cudaStream_t);                                                          \
     template void mg_residual_restrict<T>(const Geo&, const Geo&, const T*, const T*, T*, int, double,    \
                                           double, cudaStream_t);                                          \
     template void mg_prolong_correct<T>(const Geo&, const Geo&, T*, const T*, int, cudaStream_t);         \
