@@ -3,6 +3,9 @@
 // Layout: a scalar field is ncell values, x fastest; a stack of C fields is
 // C*ncell values.  A Stokes vector is [v_0 .. v_{d-1} | p].  All grids here
 // are periodic with an even number of cells per axis (red-black ordering).
+#include <cstdlib>
+#include <cstring>
+
 #include "ibr_internal.cuh"
 
 namespace ibr {
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __rest
 // first colour on plane p over the tile plus a 1-cell ring (recomputed by the
 // neighbouring CTAs too, so no CTA reads another's output), then updates the
 // second colour on plane p-1 from the first-colour values of planes p-2..p.
-constexpr int FX = 32, FY = 8, FZ = 16;
+constexpr int FX = 32, FY = 8, FZ = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(FX* FY) k_rbgs_fused3d(const T* __restrict__ uo, const T* __restrict__ f,
@@ -386,7 +389,21 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa
     IBR_CHECK_LAUNCH();
 }
 
-bool mg_fused_ok(const Geo& g) { return g.d == 3 && g.n0 % FX == 0 && g.n1 % FY == 0 && g.n2 >= 4; }
+// The fused sweep pays a serial z-march per CTA, so it is used only on levels
+// large enough to fill the GPU (>= IBR_FUSED_MIN_CELLS cells, default 64^3);
+// IBR_SMOOTHER=halfsweep selects the two-launch sweep everywhere (the two give
+// identical results).
+bool mg_fused_ok(const Geo& g) {
+    static const long long min_cells = [] {
+        const char* e = std::getenv("IBR_FUSED_MIN_CELLS");
+        return e ? std::atoll(e) : 64LL * 64 * 64;
+    }();
+    static const bool off = [] {
+        const char* e = std::getenv("IBR_SMOOTHER");
+        return e && std::strcmp(e, "halfsweep") == 0;
+    }();
+    return !off && g.d == 3 && g.n0 % FX == 0 && g.n1 % FY == 0 && g.n2 >= 4 && g.ncell >= min_cells;
+}
 
 template <typename T>
 void mg_sweep_fused(const Geo& g, const T* u_old, const T* f, T* u_new, int C, double sigma, double kappa, int c0,
