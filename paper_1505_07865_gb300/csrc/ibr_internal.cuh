@@ -92,12 +92,6 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
 template <typename T>
 void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int color, bool zero_init,
                cudaStream_t s);
-// one full red-black sweep (colour c0, then 1 - c0), out of place, for 3-D
-// levels accepted by mg_fused_ok; identical result to two mg_smooth calls
-bool mg_fused_ok(const Geo& g);
-template <typename T>
-void mg_sweep_fused(const Geo& g, const T* u_old, const T* f, T* u_new, int C, double sigma, double kappa, int c0,
-                    bool zero_init, cudaStream_t s);
 template <typename T>
 void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
                           double kappa, cudaStream_t s);
@@ -106,6 +100,17 @@ void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, 
 template <typename T>
 void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int sweeps,
                      cudaStream_t s);
+// One V-cycle for (sigma I - kappa Delta_h) U[0] = F0 on the levels lev[0..L)
+// (C stacked fields): red-black pre/post sweeps, averaging restriction into
+// Fw[l] (l >= 1), (bi/tri)linear prolongation, coarsest level by red-black
+// sweeps in one CTA; all levels with <= MG_TAIL_MAX_CELLS cells run inside one
+// shared-memory kernel.  zero_start: U[0] starts at zero (else from its value).
+constexpr int MG_TAIL_MAX_LEVELS = 8;
+constexpr long long MG_TAIL_MAX_CELLS = 4096;
+constexpr size_t MG_TAIL_MAX_SMEM = 200 * 1024;
+template <typename T>
+void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, double sigma, double kappa,
+               bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s);
 // q = -D y - hd ; (P_S middle factor, Sec. V.B)
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s);

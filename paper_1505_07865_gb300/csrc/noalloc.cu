@@ -93,49 +93,21 @@ extern "C" int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, dou
         cudaStream_t s = (cudaStream_t)cuda_stream;
         double* base = scratch_address();
         double* U[32];
-        const double* F[32];
         double* Fw[32];
         U[0] = u;
-        F[0] = f;
         Fw[0] = nullptr;
         long long off = 0;
         for (int l = 1; l < nl; ++l) {
             U[l] = base + off;
             off += lev[l].ncell;
             Fw[l] = base + off;
-            F[l] = Fw[l];
             off += lev[l].ncell;
         }
         int nmax = lev[nl - 1].n0 > lev[nl - 1].n1 ? lev[nl - 1].n0 : lev[nl - 1].n1;
         if (lev[nl - 1].n2 > nmax) nmax = lev[nl - 1].n2;
         int coarse_sweeps = 2 * nmax * nmax > 20 ? 2 * nmax * nmax : 20;
-        for (int it = 0; it < k; ++it) {
-            // one V-cycle from the current u (the sweep order of ibr_op_vcycle)
-            for (int l = 0; l + 1 < nl; ++l) {
-                bool zs = l > 0;
-                if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(double) * lev[l].ncell, s));
-                for (int q = 0; q < pre; ++q) {
-                    mg_smooth<double>(lev[l], U[l], F[l], 1, sigma, kappa, 0, zs && q == 0, s);
-                    mg_smooth<double>(lev[l], U[l], F[l], 1, sigma, kappa, 1, false, s);
-                }
-                mg_residual_restrict<double>(lev[l], lev[l + 1], U[l], F[l], Fw[l + 1], 1, sigma, kappa, s);
-            }
-            if (nl == 1) {
-                for (int q = 0; q < coarse_sweeps; ++q) {
-                    mg_smooth<double>(lev[0], U[0], F[0], 1, sigma, kappa, 0, false, s);
-                    mg_smooth<double>(lev[0], U[0], F[0], 1, sigma, kappa, 1, false, s);
-                }
-                continue;
-            }
-            mg_coarse_solve<double>(lev[nl - 1], U[nl - 1], F[nl - 1], 1, sigma, kappa, coarse_sweeps, s);
-            for (int l = nl - 2; l >= 0; --l) {
-                mg_prolong_correct<double>(lev[l], lev[l + 1], U[l], U[l + 1], 1, s);
-                for (int q = 0; q < post; ++q) {
-                    mg_smooth<double>(lev[l], U[l], F[l], 1, sigma, kappa, 1, false, s);
-                    mg_smooth<double>(lev[l], U[l], F[l], 1, sigma, kappa, 0, false, s);
-                }
-            }
-        }
+        for (int it = 0; it < k; ++it)
+            mg_vcycle<double>(lev, nl, U, Fw, f, 1, sigma, kappa, false, pre, post, coarse_sweeps, s);
         set_error("");
         return IBR_OK;
     } catch (const Error& e) {

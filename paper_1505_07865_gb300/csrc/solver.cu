@@ -65,7 +65,6 @@ template <typename T>
 struct Multigrid {
     std::vector<Geo> lev;
     std::vector<T*> u, f;  // index 0 unused (caller's buffers)
-    std::vector<T*> tmp;   // ping-pong buffer of the fused smoother (levels it accepts)
     int cmax = 0;
     int coarse_sweeps = 40;
 
@@ -98,71 +97,22 @@ struct Multigrid {
         const Geo& cg = lev.back();
         int nmax = std::max(cg.n0, std::max(cg.n1, cg.n2));
         coarse_sweeps = std::max(20, 2 * nmax * nmax);
-        for (size_t l = 0; l + 1 < lev.size(); ++l)
-            tmp.push_back(mg_fused_ok(lev[l]) ? dalloc<T>((size_t)cmax * lev[l].ncell) : nullptr);
-        tmp.push_back(nullptr);
     }
     void release() {
         for (auto& p : u) dfree(p);
         for (auto& p : f) dfree(p);
-        for (auto& p : tmp) dfree(p);
         u.clear();
         f.clear();
-        tmp.clear();
         lev.clear();
     }
     // one V-cycle for (sigma I - kappa Delta_h) u0 = f0 (C stacked fields)
     void vcycle(T* u0, const T* f0, int C, double sigma, double kappa, bool zero_start, int pre, int post,
                 cudaStream_t s) {
         int L = (int)lev.size();
-        std::vector<T*> U(L);
-        std::vector<const T*> F(L);
+        std::vector<T*> U(u);
         U[0] = u0;
-        F[0] = f0;
-        for (int l = 1; l < L; ++l) {
-            U[l] = u[l];
-            F[l] = f[l];
-        }
-        for (int l = 0; l + 1 < L; ++l) {
-            bool zs = (l > 0) || zero_start;
-            if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(T) * C * lev[l].ncell, s));
-            int it = 0;
-            if (tmp[l] && mg_fused_ok(lev[l])) {
-                // pairs of full sweeps ping-pong through tmp and end in U[l]
-                for (; it + 2 <= pre; it += 2) {
-                    mg_sweep_fused<T>(lev[l], U[l], F[l], tmp[l], C, sigma, kappa, 0, zs && it == 0, s);
-                    mg_sweep_fused<T>(lev[l], tmp[l], F[l], U[l], C, sigma, kappa, 0, false, s);
-                }
-            }
-            for (; it < pre; ++it) {
-                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 0, zs && it == 0, s);
-                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 1, false, s);
-            }
-            mg_residual_restrict<T>(lev[l], lev[l + 1], U[l], F[l], f[l + 1], C, sigma, kappa, s);
-        }
-        if (L == 1 && !zero_start) {
-            // single-level grid: smooth only
-            for (int it = 0; it < coarse_sweeps; ++it) {
-                mg_smooth<T>(lev[0], U[0], F[0], C, sigma, kappa, 0, false, s);
-                mg_smooth<T>(lev[0], U[0], F[0], C, sigma, kappa, 1, false, s);
-            }
-            return;
-        }
-        mg_coarse_solve<T>(lev[L - 1], U[L - 1], F[L - 1], C, sigma, kappa, coarse_sweeps, s);
-        for (int l = L - 2; l >= 0; --l) {
-            mg_prolong_correct<T>(lev[l], lev[l + 1], U[l], U[l + 1], C, s);
-            int it = 0;
-            if (tmp[l] && mg_fused_ok(lev[l])) {
-                for (; it + 2 <= post; it += 2) {
-                    mg_sweep_fused<T>(lev[l], U[l], F[l], tmp[l], C, sigma, kappa, 1, false, s);
-                    mg_sweep_fused<T>(lev[l], tmp[l], F[l], U[l], C, sigma, kappa, 1, false, s);
-                }
-            }
-            for (; it < post; ++it) {
-                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 1, false, s);
-                mg_smooth<T>(lev[l], U[l], F[l], C, sigma, kappa, 0, false, s);
-            }
-        }
+        mg_vcycle<T>(lev.data(), L, U.data(), f.data(), f0, C, sigma, kappa, zero_start, pre, post, coarse_sweeps,
+                     s);
     }
 };
 

@@ -3,9 +3,6 @@
 // Layout: a scalar field is ncell values, x fastest; a stack of C fields is
 // C*ncell values.  A Stokes vector is [v_0 .. v_{d-1} | p].  All grids here
 // are periodic with an even number of cells per axis (red-black ordering).
-#include <cstdlib>
-#include <cstring>
-
 #include "ibr_internal.cuh"
 
 namespace ibr {
@@ -74,16 +71,13 @@ __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __re
     y[D * g.ncell + n.c] = -div * ih;
 }
 
-// red-black Gauss-Seidel half sweep on C stacked fields (component = blockIdx.y)
+// ---- point operators shared by the per-level kernels and the one-CTA tail ----
+// (same arithmetic, so a level gives the same result on either path)
+
+// red-black Gauss-Seidel update of the t-th cell of the given colour
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
-                                              int color, int zero_init) {
-    long long half = g.ncell >> 1;
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= half) return;
-    int cmp = blockIdx.y;
-    T* uu = u + cmp * g.ncell;
-    const T* ff = f + cmp * g.ncell;
+__device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, T sigma, T kh2, int color, int zero_init,
+                                           long long t) {
     int hn0 = g.n0 >> 1;
     int ih = (int)(t % hn0);
     long long r = t / hn0;
@@ -91,113 +85,15 @@ __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __rest
     int k = (int)(r / g.n1);
     int i = 2 * ih + ((j + k + color) & 1);
     Nbr n = neighbours<D>(g, i, j, k);
-    T nb = zero_init ? T(0) : nbr_sum<D, T>(uu, n);
+    T nb = zero_init ? T(0) : nbr_sum<D, T>(u, n);
     T diag = sigma + T(2 * D) * kh2;
-    uu[n.c] = (ff[n.c] + kh2 * nb) / diag;
+    u[n.c] = (f[n.c] + kh2 * nb) / diag;
 }
 
-// One full red-black Gauss-Seidel sweep (colour c0 first, then 1 - c0) of a
-// 3-D periodic field, out of place: u_new = sweep(u_old).  Same arithmetic and
-// summation order as two k_rbgs half sweeps, so the result is identical.
-// A CTA owns a FX x FY column of cells and marches along z over [z0, z0+FZ):
-// at plane p it loads u_old(p+1) with a 2-cell in-plane halo, updates the
-// first colour on plane p over the tile plus a 1-cell ring (recomputed by the
-// neighbouring CTAs too, so no CTA reads another's output), then updates the
-// second colour on plane p-1 from the first-colour values of planes p-2..p.
-constexpr int FX = 32, FY = 8, FZ = 8;
-
-template <typename T>
-__global__ void __launch_bounds__(FX* FY) k_rbgs_fused3d(const T* __restrict__ uo, const T* __restrict__ f,
-                                                         T* __restrict__ un, Geo g, T sigma, T kh2, int c0,
-                                                         int zero_init) {
-    __shared__ T su[3][FY + 4][FX + 4];   // u_old planes p-1, p, p+1 (ring)
-    __shared__ T sr[3][FY + 2][FX + 2];   // first-colour values, planes p-2, p-1, p (ring)
-    __shared__ T sf[2][FY + 2][FX + 2];   // f planes p-1, p (ring)
-    const int cmp = blockIdx.z;
-    const long long off = (long long)cmp * g.ncell;
-    uo += off;
-    f += off;
-    un += off;
-    const int ntx = g.n0 / FX;
-    const int bx = (blockIdx.x % ntx) * FX, by = (blockIdx.x / ntx) * FY;
-    const int z0 = blockIdx.y * FZ;
-    const int z1 = min(z0 + FZ, g.n2);
-    const int tid = threadIdx.x;
-    const long long sy = g.n0, sz = (long long)g.n0 * g.n1;
-    const T diag = sigma + T(6) * kh2;
-    auto wrap = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
-    auto load_u = [&](int p) {
-        int slot = ((p % 3) + 3) % 3, pz = wrap(p, g.n2);
-        for (int e = tid; e < (FY + 4) * (FX + 4); e += FX * FY) {
-            int ly = e / (FX + 4), lx = e % (FX + 4);
-            int gx = wrap(bx + lx - 2, g.n0), gy = wrap(by + ly - 2, g.n1);
-            su[slot][ly][lx] = zero_init ? T(0) : uo[gx + sy * gy + sz * pz];
-        }
-    };
-    auto load_f = [&](int p) {
-        int slot = ((p % 2) + 2) % 2, pz = wrap(p, g.n2);
-        for (int e = tid; e < (FY + 2) * (FX + 2); e += FX * FY) {
-            int ly = e / (FX + 2), lx = e % (FX + 2);
-            int gx = wrap(bx + lx - 1, g.n0), gy = wrap(by + ly - 1, g.n1);
-            sf[slot][ly][lx] = f[gx + sy * gy + sz * pz];
-        }
-    };
-    load_u(z0 - 2);
-    load_u(z0 - 1);
-    for (int p = z0 - 1; p <= z1; ++p) {
-        load_u(p + 1);
-        load_f(p);
-        __syncthreads();
-        // first colour on plane p, tile + 1-cell ring
-        {
-            const int s0 = ((p - 1) % 3 + 3) % 3, s1 = ((p % 3) + 3) % 3, s2 = ((p + 1) % 3 + 3) % 3;
-            const int fs = ((p % 2) + 2) % 2, rs = s1;
-            for (int e = tid; e < (FY + 2) * (FX + 2); e += FX * FY) {
-                int ly = e / (FX + 2), lx = e % (FX + 2);
-                int gx = bx + lx - 1, gy = by + ly - 1;
-                int pz = wrap(p, g.n2);
-                int colour = (wrap(gx, g.n0) + wrap(gy, g.n1) + pz) & 1;
-                if (colour != c0) continue;
-                int ux = lx + 1, uy = ly + 1;
-                // the association of nbr_sum: (x+ + x- + y+ + y-) + (z+ + z-)
-                T nb = zero_init ? T(0)
-                                 : (su[s1][uy][ux + 1] + su[s1][uy][ux - 1] + su[s1][uy + 1][ux] + su[s1][uy - 1][ux]) +
-                                       (su[s2][uy][ux] + su[s0][uy][ux]);
-                sr[rs][ly][lx] = (sf[fs][ly][lx] + kh2 * nb) / diag;
-            }
-        }
-        __syncthreads();
-        // second colour on plane p-1, tile interior; write both colours
-        const int q = p - 1;
-        if (q >= z0) {
-            const int r0 = ((q - 1) % 3 + 3) % 3, r1 = ((q % 3) + 3) % 3, r2 = ((q + 1) % 3 + 3) % 3;
-            const int fs = ((q % 2) + 2) % 2;
-            int lx = tid % FX, ly = tid / FX;
-            int gx = bx + lx, gy = by + ly, qz = wrap(q, g.n2);
-            int colour = (gx + gy + qz) & 1;
-            T val;
-            if (colour == c0) {
-                val = sr[r1][ly + 1][lx + 1];
-            } else {
-                T nb = (sr[r1][ly + 1][lx + 2] + sr[r1][ly + 1][lx] + sr[r1][ly + 2][lx + 1] + sr[r1][ly][lx + 1]) +
-                       (sr[r2][ly + 1][lx + 1] + sr[r0][ly + 1][lx + 1]);
-                val = (sf[fs][ly + 1][lx + 1] + kh2 * nb) / diag;
-            }
-            un[gx + sy * gy + sz * qz] = val;
-        }
-        __syncthreads();
-    }
-}
-
-// coarse f = average over the 2^D children of the fine residual f - (sigma u - kh2 Lap u)
+// coarse cell t: average over its 2^D children of f - (sigma u - kh2 Lap u)
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
-                                                        T* __restrict__ fc, Geo gf, Geo gc, T sigma, T kh2) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= gc.ncell) return;
-    int cmp = blockIdx.y;
-    const T* uu = u + cmp * gf.ncell;
-    const T* ff = f + cmp * gf.ncell;
+__device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& gf, const Geo& gc, T sigma, T kh2,
+                                            long long t) {
     int I = (int)(t % gc.n0);
     long long r = t / gc.n0;
     int J = (int)(r % gc.n1);
@@ -209,21 +105,17 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u,
         int j = 2 * J + ((c >> 1) & 1);
         int k = D == 3 ? 2 * K + ((c >> 2) & 1) : 0;
         Nbr n = neighbours<D>(gf, i, j, k);
-        T uc = uu[n.c];
-        T res = ff[n.c] - (sigma * uc - kh2 * (nbr_sum<D, T>(uu, n) - T(2 * D) * uc));
+        T uc = u[n.c];
+        T res = f[n.c] - (sigma * uc - kh2 * (nbr_sum<D, T>(u, n) - T(2 * D) * uc));
         acc += res;
     }
-    fc[cmp * gc.ncell + t] = acc * (T(1) / T(1 << D));
+    return acc * (T(1) / T(1 << D));
 }
 
-// cell-centred (bi/tri)linear prolongation: weights 3/4 (parent), 1/4 (the
-// neighbour on the side of the child) per axis; u += P uc
+// fine cell t: cell-centred (bi/tri)linear interpolation of the coarse
+// correction, weights 3/4 (parent) and 1/4 (the neighbour on the child's side)
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __restrict__ uc, Geo gf, Geo gc) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= gf.ncell) return;
-    int cmp = blockIdx.y;
-    const T* cc = uc + cmp * gc.ncell;
+__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, long long t) {
     int i = (int)(t % gf.n0);
     long long r = t / gf.n0;
     int j = (int)(r % gf.n1);
@@ -248,32 +140,17 @@ __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __r
         long long idx = I[a] + (long long)gc.n0 * (Jc[b] + (long long)gc.n1 * Kc[e]);
         acc += ww * cc[idx];
     }
-    u[cmp * gf.ncell + t] += acc;
+    return acc;
 }
 
-// single-CTA coarse solve: zero start, (mean-removed f if sigma == 0), red-black
-// sweeps in shared memory, mean-removed result if sigma == 0.  One CTA per field.
-template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
-                                                 int sweeps) {
-    extern __shared__ unsigned char smem_raw[];
-    T* su = reinterpret_cast<T*>(smem_raw);
-    T* sf = su + g.ncell;
-    __shared__ double red[32];
-    int cmp = blockIdx.x;
-    const T* ff = f + cmp * g.ncell;
-    T* uu = u + cmp * g.ncell;
-    int tid = threadIdx.x;
-    int nt = blockDim.x;
-    // mean of f
+// block-wide mean of a[0..n) (all threads get it); red: 32 doubles of shared memory
+template <typename T>
+__device__ double block_mean(const T* a, long long n, double* red) {
+    int tid = threadIdx.x, nt = blockDim.x;
     double part = 0.0;
-    for (long long c = tid; c < g.ncell; c += nt) {
-        T v = ff[c];
-        sf[c] = v;
-        su[c] = T(0);
-        part += (double)v;
-    }
+    for (long long c = tid; c < n; c += nt) part += (double)a[c];
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = part;
     __syncthreads();
     if (tid < 32) {
@@ -282,9 +159,22 @@ __global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __r
         if (tid == 0) red[0] = v;
     }
     __syncthreads();
-    T fmean = sigma == T(0) ? (T)(red[0] / (double)g.ncell) : T(0);
+    double m = red[0] / (double)n;
     __syncthreads();
-    for (long long c = tid; c < g.ncell; c += nt) sf[c] -= fmean;
+    return m;
+}
+
+// coarsest-level solve in shared memory: f (in sf, modified) made mean-free if
+// sigma == 0, u (su) from zero by red-black sweeps, then made mean-free if
+// sigma == 0
+template <int D, typename T>
+__device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int sweeps, double* red) {
+    int tid = threadIdx.x, nt = blockDim.x;
+    T fmean = sigma == T(0) ? (T)block_mean(sf, g.ncell, red) : T(0);
+    for (long long c = tid; c < g.ncell; c += nt) {
+        sf[c] -= fmean;
+        su[c] = T(0);
+    }
     __syncthreads();
     T diag = sigma + T(2 * D) * kh2;
     for (int s = 0; s < sweeps; ++s) {
@@ -301,20 +191,149 @@ __global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __r
             __syncthreads();
         }
     }
-    part = 0.0;
-    for (long long c = tid; c < g.ncell; c += nt) part += (double)su[c];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    T umean = sigma == T(0) ? (T)block_mean(su, g.ncell, red) : T(0);
+    for (long long c = tid; c < g.ncell; c += nt) su[c] -= umean;
     __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = part;
+}
+
+// red-black Gauss-Seidel half sweep on C stacked fields (component = blockIdx.y)
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
+                                              int color, int zero_init) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (g.ncell >> 1)) return;
+    int cmp = blockIdx.y;
+    rbgs_point<D, T>(u + cmp * g.ncell, f + cmp * g.ncell, g, sigma, kh2, color, zero_init, t);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
+                                                        T* __restrict__ fc, Geo gf, Geo gc, T sigma, T kh2) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= gc.ncell) return;
+    int cmp = blockIdx.y;
+    fc[cmp * gc.ncell + t] = restrict_point<D, T>(u + cmp * gf.ncell, f + cmp * gf.ncell, gf, gc, sigma, kh2, t);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __restrict__ uc, Geo gf, Geo gc) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= gf.ncell) return;
+    int cmp = blockIdx.y;
+    u[cmp * gf.ncell + t] += prolong_point<D, T>(uc + cmp * gc.ncell, gf, gc, t);
+}
+
+// single-CTA coarse solve of the coarsest level (one CTA per field)
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
+                                                 int sweeps) {
+    extern __shared__ unsigned char smem_raw[];
+    T* su = reinterpret_cast<T*>(smem_raw);
+    T* sf = su + g.ncell;
+    __shared__ double red[32];
+    int cmp = blockIdx.x;
+    const T* ff = f + cmp * g.ncell;
+    T* uu = u + cmp * g.ncell;
+    for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) sf[c] = ff[c];
     __syncthreads();
-    if (tid < 32) {
-        double v = tid < (nt >> 5) ? red[tid] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (tid == 0) red[0] = v;
+    coarse_block<D, T>(su, sf, g, sigma, kh2, sweeps, red);
+    for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) uu[c] = su[c];
+}
+
+// The small levels of a V-cycle, all in one CTA's shared memory (one CTA per
+// field): levels tl.g[0] (finest of the tail) .. tl.g[nl-1] (coarsest), the
+// same sweeps, restriction, coarse solve and prolongation as the per-level
+// kernels, with __syncthreads between them instead of kernel launches.
+struct TailLevels {
+    int nl;
+    Geo g[MG_TAIL_MAX_LEVELS];
+    int uoff[MG_TAIL_MAX_LEVELS];
+    int foff[MG_TAIL_MAX_LEVELS];
+};
+
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__ ug, const T* __restrict__ fg,
+                                                  T sigma, double kappa, int zero_start, int pre, int post,
+                                                  int sweeps) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    __shared__ double red[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int cmp = blockIdx.x;
+    const Geo g0 = tl.g[0];
+    ug += cmp * g0.ncell;
+    fg += cmp * g0.ncell;
+    {
+        T* u0 = sm + tl.uoff[0];
+        T* f0 = sm + tl.foff[0];
+        for (long long c = tid; c < g0.ncell; c += nt) {
+            f0[c] = fg[c];
+            u0[c] = zero_start ? T(0) : ug[c];
+        }
     }
     __syncthreads();
-    T umean = sigma == T(0) ? (T)(red[0] / (double)g.ncell) : T(0);
-    for (long long c = tid; c < g.ncell; c += nt) uu[c] = su[c] - umean;
+    auto half = [&](int l, int color, int zero) {
+        const Geo& g = tl.g[l];
+        T kh2 = (T)(kappa / (g.h * g.h));
+        T* u = sm + tl.uoff[l];
+        const T* f = sm + tl.foff[l];
+        for (long long t = tid; t < (g.ncell >> 1); t += nt) rbgs_point<D, T>(u, f, g, sigma, kh2, color, zero, t);
+        __syncthreads();
+    };
+    const int L = tl.nl;
+    if (L == 1) {
+        const Geo& g = tl.g[0];
+        if (zero_start) {
+            coarse_block<D, T>(sm + tl.uoff[0], sm + tl.foff[0], g, sigma, (T)(kappa / (g.h * g.h)), sweeps, red);
+        } else {
+            for (int s = 0; s < sweeps; ++s) {
+                half(0, 0, 0);
+                half(0, 1, 0);
+            }
+        }
+    } else {
+        for (int l = 0; l + 1 < L; ++l) {
+            int zs = (l > 0) || zero_start;
+            if (pre == 0 && zs) {
+                T* u = sm + tl.uoff[l];
+                for (long long c = tid; c < tl.g[l].ncell; c += nt) u[c] = T(0);
+                __syncthreads();
+            }
+            for (int it = 0; it < pre; ++it) {
+                half(l, 0, zs && it == 0);
+                half(l, 1, 0);
+            }
+            const Geo& gf = tl.g[l];
+            const Geo& gc = tl.g[l + 1];
+            T kh2 = (T)(kappa / (gf.h * gf.h));
+            const T* u = sm + tl.uoff[l];
+            const T* f = sm + tl.foff[l];
+            T* fc = sm + tl.foff[l + 1];
+            for (long long t = tid; t < gc.ncell; t += nt) fc[t] = restrict_point<D, T>(u, f, gf, gc, sigma, kh2, t);
+            __syncthreads();
+        }
+        {
+            const Geo& g = tl.g[L - 1];
+            coarse_block<D, T>(sm + tl.uoff[L - 1], sm + tl.foff[L - 1], g, sigma, (T)(kappa / (g.h * g.h)), sweeps,
+                               red);
+        }
+        for (int l = L - 2; l >= 0; --l) {
+            const Geo& gf = tl.g[l];
+            const Geo& gc = tl.g[l + 1];
+            T* u = sm + tl.uoff[l];
+            const T* uc = sm + tl.uoff[l + 1];
+            for (long long t = tid; t < gf.ncell; t += nt) u[t] += prolong_point<D, T>(uc, gf, gc, t);
+            __syncthreads();
+            for (int it = 0; it < post; ++it) {
+                half(l, 1, 0);
+                half(l, 0, 0);
+            }
+        }
+    }
+    {
+        const T* u0 = sm + tl.uoff[0];
+        for (long long c = tid; c < g0.ncell; c += nt) ug[c] = u0[c];
+    }
 }
 
 // q = -D y - hd ; qr = rhs_scale * q
@@ -389,32 +408,6 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa
     IBR_CHECK_LAUNCH();
 }
 
-// The fused sweep pays a serial z-march per CTA, so it is used only on levels
-// large enough to fill the GPU (>= IBR_FUSED_MIN_CELLS cells, default 64^3);
-// IBR_SMOOTHER=halfsweep selects the two-launch sweep everywhere (the two give
-// identical results).
-bool mg_fused_ok(const Geo& g) {
-    static const long long min_cells = [] {
-        const char* e = std::getenv("IBR_FUSED_MIN_CELLS");
-        return e ? std::atoll(e) : 64LL * 64 * 64;
-    }();
-    static const bool off = [] {
-        const char* e = std::getenv("IBR_SMOOTHER");
-        return e && std::strcmp(e, "halfsweep") == 0;
-    }();
-    return !off && g.d == 3 && g.n0 % FX == 0 && g.n1 % FY == 0 && g.n2 >= 4 && g.ncell >= min_cells;
-}
-
-template <typename T>
-void mg_sweep_fused(const Geo& g, const T* u_old, const T* f, T* u_new, int C, double sigma, double kappa, int c0,
-                    bool zero_init, cudaStream_t s) {
-    T kh2 = (T)(kappa / (g.h * g.h));
-    dim3 grid((g.n0 / FX) * (g.n1 / FY), (g.n2 + FZ - 1) / FZ, C);
-    ProfScope ps(KID_RBGS, s, (zero_init ? 2.0 : 3.0) * C * g.ncell * sizeof(T));
-    k_rbgs_fused3d<T><<<grid, FX * FY, 0, s>>>(u_old, f, u_new, g, (T)sigma, kh2, c0, zero_init ? 1 : 0);
-    IBR_CHECK_LAUNCH();
-}
-
 template <typename T>
 void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
                           double kappa, cudaStream_t s) {
@@ -453,6 +446,81 @@ void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double
     IBR_CHECK_LAUNCH();
 }
 
+
+// shared memory of the tail kernel for levels [l0, L)
+template <typename T>
+static size_t tail_smem(const Geo* lev, int l0, int L) {
+    size_t n = 0;
+    for (int l = l0; l < L; ++l) n += 2 * (size_t)lev[l].ncell;
+    return n * sizeof(T);
+}
+
+template <typename T>
+void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, double sigma, double kappa,
+               bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s) {
+    // the tail: the longest suffix of levels with <= MG_TAIL_MAX_CELLS cells each
+    // that fits in shared memory (the coarsest level always does)
+    int lt = L - 1;
+    while (lt - 1 >= 0 && L - (lt - 1) <= MG_TAIL_MAX_LEVELS && lev[lt - 1].ncell <= MG_TAIL_MAX_CELLS &&
+           tail_smem<T>(lev, lt - 1, L) <= MG_TAIL_MAX_SMEM)
+        --lt;
+    auto Fl = [&](int l) -> const T* { return l == 0 ? F0 : Fw[l]; };
+    for (int l = 0; l < lt; ++l) {
+        bool zs = (l > 0) || zero_start;
+        if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(T) * C * lev[l].ncell, s));
+        for (int it = 0; it < pre; ++it) {
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 0, zs && it == 0, s);
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 1, false, s);
+        }
+        mg_residual_restrict<T>(lev[l], lev[l + 1], U[l], Fl(l), Fw[l + 1], C, sigma, kappa, s);
+    }
+    {
+        TailLevels tl;
+        tl.nl = L - lt;
+        int off = 0;
+        for (int q = 0; q < tl.nl; ++q) {
+            tl.g[q] = lev[lt + q];
+            tl.uoff[q] = off;
+            off += (int)lev[lt + q].ncell;
+            tl.foff[q] = off;
+            off += (int)lev[lt + q].ncell;
+        }
+        size_t sm = tail_smem<T>(lev, lt, L);
+        long long n0 = lev[lt].ncell;
+        int nt = n0 >= 2048 ? 1024 : (int)(((n0 + 1) / 2 + 31) / 32 * 32);
+        if (nt < 32) nt = 32;
+        bool zs = (lt > 0) || zero_start;
+        ProfScope ps(KID_COARSE, s, 2.0 * C * n0 * sizeof(T));
+        if (lev[0].d == 3) {
+            static bool attr = false;
+            if (!attr) {
+                IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)MG_TAIL_MAX_SMEM));
+                attr = true;
+            }
+            k_mg_tail<3, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), (T)sigma, kappa, zs ? 1 : 0, pre, post,
+                                              coarse_sweeps);
+        } else {
+            static bool attr = false;
+            if (!attr) {
+                IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)MG_TAIL_MAX_SMEM));
+                attr = true;
+            }
+            k_mg_tail<2, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), (T)sigma, kappa, zs ? 1 : 0, pre, post,
+                                              coarse_sweeps);
+        }
+        IBR_CHECK_LAUNCH();
+    }
+    for (int l = lt - 1; l >= 0; --l) {
+        mg_prolong_correct<T>(lev[l], lev[l + 1], U[l], U[l + 1], C, s);
+        for (int it = 0; it < post; ++it) {
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 1, false, s);
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 0, false, s);
+        }
+    }
+}
+
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s) {
     int nb = grid_1d(g.ncell, 256);
@@ -479,12 +547,12 @@ void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double 
 #define IBR_INST(T)                                                                                        \
     template void stokes_apply<T>(const Geo&, const T*, T*, double, double, const double*, cudaStream_t); \
     template void mg_smooth<T>(const Geo&, T*, const T*, int, double, double, int, bool, cudaStream_t);   \
-    template void mg_sweep_fused<T>(const Geo&, const T*, const T*, T*, int, double, double, int, bool,      \
-                                    cudaStream_t);                                                          \
     template void mg_residual_restrict<T>(const Geo&, const Geo&, const T*, const T*, T*, int, double,    \
                                           double, cudaStream_t);                                          \
     template void mg_prolong_correct<T>(const Geo&, const Geo&, T*, const T*, int, cudaStream_t);         \
     template void mg_coarse_solve<T>(const Geo&, T*, const T*, int, double, double, int, cudaStream_t);   \
+    template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, double, double, bool, int,   \
+                               int, int, cudaStream_t);                                                      \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \
     template void ps_finish<T>(const Geo&, const T*, const T*, const T*, T*, double, double, cudaStream_t);
 IBR_INST(double)
