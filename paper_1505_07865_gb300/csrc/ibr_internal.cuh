@@ -23,8 +23,11 @@ struct Error {
         if (_e != cudaSuccess)                                                    \
             throw ::ibr::Error{IBR_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
     } while (0)
-// every kernel launch of the library goes through this check (and counter)
+// every kernel launch of the library goes through this check (and counter);
+// add_launches accounts for the kernels of a replayed CUDA graph
 void count_launch();
+void add_launches(long long n);
+bool profiling_enabled();
 #define IBR_CHECK_LAUNCH()                  \
     do {                                    \
         ::ibr::count_launch();              \
@@ -111,6 +114,16 @@ constexpr size_t MG_TAIL_MAX_SMEM = 200 * 1024;
 template <typename T>
 void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, double sigma, double kappa,
                bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s);
+// red-black sweeps of the coarsest-level solve: enough for a preconditioner
+// (the coarsest grid has at most a few hundred cells)
+inline int mg_coarse_sweeps(const Geo& g) {
+    int nmax = g.n0 > g.n1 ? g.n0 : g.n1;
+    if (g.n2 > nmax) nmax = g.n2;
+    return 2 * nmax > 8 ? 2 * nmax : 8;
+}
+// raises the shared-memory limit of the tail kernel (call outside stream capture)
+template <typename T>
+void mg_set_attributes();
 // q = -D y - hd ; (P_S middle factor, Sec. V.B)
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s);

@@ -103,9 +103,7 @@ extern "C" int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, dou
             Fw[l] = base + off;
             off += lev[l].ncell;
         }
-        int nmax = lev[nl - 1].n0 > lev[nl - 1].n1 ? lev[nl - 1].n0 : lev[nl - 1].n1;
-        if (lev[nl - 1].n2 > nmax) nmax = lev[nl - 1].n2;
-        int coarse_sweeps = 2 * nmax * nmax > 20 ? 2 * nmax * nmax : 20;
+        int coarse_sweeps = mg_coarse_sweeps(lev[nl - 1]);
         for (int it = 0; it < k; ++it)
             mg_vcycle<double>(lev, nl, U, Fw, f, 1, sigma, kappa, false, pre, post, coarse_sweeps, s);
         set_error("");

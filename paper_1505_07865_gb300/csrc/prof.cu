@@ -38,6 +38,8 @@ static const char* kNames[KID_COUNT] = {
 };
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool profiling_enabled() { return g_prof; }
 
 static cudaEvent_t get_event() {
     if (!g_free.empty()) {

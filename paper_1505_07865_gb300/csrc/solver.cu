@@ -94,9 +94,7 @@ struct Multigrid {
             f.push_back(dalloc<T>((size_t)cmax * c.ncell));
             g = c;
         }
-        const Geo& cg = lev.back();
-        int nmax = std::max(cg.n0, std::max(cg.n1, cg.n2));
-        coarse_sweeps = std::max(20, 2 * nmax * nmax);
+        coarse_sweeps = mg_coarse_sweeps(lev.back());
     }
     void release() {
         for (auto& p : u) dfree(p);
@@ -188,11 +186,23 @@ struct PC {
     const T* Minv = nullptr;
     int pre = 2, post = 2, variant = IBR_PC_LOWER;
     long long ps_count = 0;
+    // the preconditioner body (from rs and rL to xs and lamT) captured once as a
+    // CUDA graph and replayed; invalidated by a new geometry or new options
+    double* rL = nullptr;  // FP64 copy of the constraint part of the input
+    cudaGraphExec_t gexec = nullptr;
+    int g_ns = -1, g_pre = -1, g_post = -1, g_variant = -1;
+    long long g_launches = 0;
+
+    void invalidate_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    }
 
     PC(ibr_grid* g, int ns_) : G(g), ns(ns_) {
         long long n = G->geo.ncell;
         long long nS = G->nS;
         mg.init(G->geo, G->d);
+        mg_set_attributes<T>();
         Vi = dalloc<T>((size_t)(ns + 1) * nS);
         Zi = dalloc<T>((size_t)ns * nS);
         w = dalloc<T>(nS);
@@ -219,13 +229,18 @@ struct PC {
         alloc_markers();
     }
     void alloc_markers() {
+        invalidate_graph();
         dfree(dU);
         dfree(lamT);
+        dfree(rL);
         long long dN = (long long)G->N * G->d;
         dU = dalloc<T>(std::max(dN, 1LL));
         lamT = dalloc<T>(std::max(dN, 1LL));
+        rL = dalloc<double>(std::max(dN, 1LL));
     }
     ~PC() {
+        invalidate_graph();
+        dfree(rL);
         mg.release();
         T* tp[] = {Vi, Zi, w, rs, rs2, xs, y, phi, q, qr, dU, lamT};
         for (T* p : tp)
@@ -273,26 +288,22 @@ struct PC {
     }
 
     // z = P^-1 r for the constrained system (Sec. V.A), FP64 in and out
-    void apply(const double* r, double* z, bool fluid_prepared = false) {
+    // steps 1-4 of Sec. V.A from rs (fluid part, precision T) and rL (the
+    // constraint part, FP64) into xs (v, pi) and lamT (Lambda); fixed buffers
+    // only, so the whole sequence can be captured as one CUDA graph
+    void body() {
         cudaStream_t s = G->stream;
         const Geo& g = G->geo;
         long long n = g.ncell, nS = G->nS;
         int d = G->d, N = G->N;
         long long dN = (long long)N * d;
-        const T* rin;
-        if (sizeof(T) == sizeof(double)) {
-            rin = reinterpret_cast<const T*>(r);
-        } else {
-            if (!fluid_prepared) vec_convert<double, T>(nS, r, rs, s);
-            rin = rs;
-        }
-        inner_gmres(rin, xs);                                                // step 1
+        inner_gmres(rs, xs);                                                 // step 1
         if (N > 0) {
-            interp<T, double>(g, G->md, xs, dU, -1.0, r + nS, s, -1.0);      // step 2: dU = -(J v + W)
+            interp<T, double>(g, G->md, xs, dU, -1.0, rL, s, -1.0);          // step 2: dU = -(J v + W)
             blockdiag_gemv<T, T>((int)G->bodies.size(), G->moff_dev, G->roff_dev, (int)dN, Minv, dU, lamT,
                                  s);                                        // step 3
             if (variant == IBR_PC_FULL) {                                   // step 4
-                IBR_CUDA_TRY(cudaMemcpyAsync(rs2, rin, sizeof(T) * nS, cudaMemcpyDeviceToDevice, s));
+                IBR_CUDA_TRY(cudaMemcpyAsync(rs2, rs, sizeof(T) * nS, cudaMemcpyDeviceToDevice, s));
                 spread_gather<T>(G->md, lamT, rs2, 1.0 / std::pow(g.h, d), s);
                 if (G->steady()) {
                     lam_sum<T>(d, N, lamT, 1.0 / G->vol, shift, s);
@@ -308,6 +319,58 @@ struct PC {
             subtract_means<T>(n, d + 1, xs, means, s);
         else
             subtract_means<T>(n, 1, xs + (long long)d * n, means + d, s);
+    }
+
+    static bool use_graphs() {
+        static const bool off = [] {
+            const char* e = std::getenv("IBR_GRAPHS");
+            return e && e[0] == '0';
+        }();
+        return !off && !profiling_enabled();
+    }
+
+    // z = P^-1 r for the constrained system (Sec. V.A), FP64 in and out.
+    // fluid_prepared: rs already holds r's fluid part in precision T.
+    void apply(const double* r, double* z, bool fluid_prepared = false) {
+        cudaStream_t s = G->stream;
+        long long nS = G->nS;
+        int N = G->N;
+        long long dN = (long long)N * G->d;
+        if (!fluid_prepared) vec_convert<double, T>(nS, r, rs, s);
+        if (N > 0) IBR_CUDA_TRY(cudaMemcpyAsync(rL, r + nS, sizeof(double) * dN, cudaMemcpyDeviceToDevice, s));
+        long long ps_per = (long long)ns * (variant == IBR_PC_FULL && N > 0 ? 2 : 1);
+        if (use_graphs()) {
+            if (gexec && (g_ns != ns || g_pre != pre || g_post != post || g_variant != variant)) invalidate_graph();
+            if (!gexec) {
+                long long l0 = ibr_launch_count();
+                long long psc = ps_count;
+                cudaGraph_t graph = nullptr;
+                IBR_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                try {
+                    body();
+                } catch (...) {
+                    cudaStreamEndCapture(s, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw;
+                }
+                IBR_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+                cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                IBR_CUDA_TRY(e);
+                g_ns = ns;
+                g_pre = pre;
+                g_post = post;
+                g_variant = variant;
+                g_launches = ibr_launch_count() - l0;
+                add_launches(-g_launches);  // counted again on every replay below
+                ps_count = psc;
+            }
+            IBR_CUDA_TRY(cudaGraphLaunch(gexec, s));
+            add_launches(g_launches);
+            ps_count += ps_per;
+        } else {
+            body();
+        }
         vec_convert<T, double>(nS, xs, z, s);
         if (N > 0) vec_convert<T, double>(dN, lamT, z + nS, s);
     }

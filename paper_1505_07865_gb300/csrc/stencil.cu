@@ -447,6 +447,17 @@ void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double
 }
 
 
+template <typename T>
+void mg_set_attributes() {
+    static bool done = false;
+    if (done) return;
+    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)MG_TAIL_MAX_SMEM));
+    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)MG_TAIL_MAX_SMEM));
+    done = true;
+}
+
 // shared memory of the tail kernel for levels [l0, L)
 template <typename T>
 static size_t tail_smem(const Geo* lev, int l0, int L) {
@@ -491,22 +502,11 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         if (nt < 32) nt = 32;
         bool zs = (lt > 0) || zero_start;
         ProfScope ps(KID_COARSE, s, 2.0 * C * n0 * sizeof(T));
+        mg_set_attributes<T>();
         if (lev[0].d == 3) {
-            static bool attr = false;
-            if (!attr) {
-                IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)MG_TAIL_MAX_SMEM));
-                attr = true;
-            }
             k_mg_tail<3, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), (T)sigma, kappa, zs ? 1 : 0, pre, post,
                                               coarse_sweeps);
         } else {
-            static bool attr = false;
-            if (!attr) {
-                IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)MG_TAIL_MAX_SMEM));
-                attr = true;
-            }
             k_mg_tail<2, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), (T)sigma, kappa, zs ? 1 : 0, pre, post,
                                               coarse_sweeps);
         }
@@ -551,6 +551,7 @@ void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double 
                                           double, cudaStream_t);                                          \
     template void mg_prolong_correct<T>(const Geo&, const Geo&, T*, const T*, int, cudaStream_t);         \
     template void mg_coarse_solve<T>(const Geo&, T*, const T*, int, double, double, int, cudaStream_t);   \
+    template void mg_set_attributes<T>();                                                                   \
     template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, double, double, bool, int,   \
                                int, int, cudaStream_t);                                                      \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \
