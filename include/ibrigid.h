@@ -234,10 +234,12 @@ int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, double sigma, 
  * Process-wide.  ibr_launch_count: kernels launched by the library since it
  * was loaded.  ibr_profile_enable(1): from then on every launch is bracketed
  * by CUDA events on its own stream; ibr_profile_read(idx, ...) returns, for
- * kernel class idx (0..count-1; IBR_EINVAL past the end), its name, launches,
- * summed event time in ms and summed algorithmic bytes (each array read or
- * written once); it synchronises on the recorded events.  ibr_profile_reset
- * clears the sums. */
+ * entry idx (IBR_EINVAL past the end), a kernel-class name, launches, summed
+ * event time in ms and summed algorithmic bytes (each array read or written
+ * once); the first half of the entries count every launch of a class, the
+ * second half ("<name>@large") only its launches that move >= 32 MiB.  It
+ * synchronises on the recorded events.  ibr_profile_reset clears the sums.
+ * While profiling is on the preconditioner runs without CUDA graphs. */
 long long ibr_launch_count(void);
 int ibr_profile_enable(int on);
 int ibr_profile_reset(void);

@@ -4,6 +4,7 @@
 // thread driving the library at a time.
 #include <atomic>
 #include <cstring>
+#include <string>
 #include <mutex>
 #include <vector>
 
@@ -27,7 +28,10 @@ struct Acc {
 static std::mutex g_mu;
 static std::vector<Pending> g_pending;
 static std::vector<cudaEvent_t> g_free;
-static Acc g_acc[KID_COUNT];
+// [0, KID_COUNT): all launches of a class; [KID_COUNT, 2 KID_COUNT): only its
+// launches that move >= kLargeBytes (the HBM-bound ones)
+constexpr double kLargeBytes = 32.0 * 1024 * 1024;
+static Acc g_acc[2 * KID_COUNT];
 
 static const char* kNames[KID_COUNT] = {
     "stokes_apply", "mg_smooth_rbgs", "mg_residual_restrict", "mg_prolong_correct", "mg_coarse_solve",
@@ -73,10 +77,13 @@ static void drain() {
         cudaEventSynchronize(p.b);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p.a, p.b);
-        Acc& a = g_acc[p.kid];
-        a.launches++;
-        a.ms += ms;
-        a.bytes += p.bytes;
+        for (int q = 0; q < 2; ++q) {
+            if (q == 1 && p.bytes < kLargeBytes) break;
+            Acc& a = g_acc[p.kid + q * KID_COUNT];
+            a.launches++;
+            a.ms += ms;
+            a.bytes += p.bytes;
+        }
         g_free.push_back(p.a);
         g_free.push_back(p.b);
     }
@@ -101,12 +108,14 @@ int ibr_profile_reset(void) {
 }
 
 int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes) {
-    if (idx < 0 || idx >= ibr::KID_COUNT) return IBR_EINVAL;
+    if (idx < 0 || idx >= 2 * ibr::KID_COUNT) return IBR_EINVAL;
     std::lock_guard<std::mutex> lk(ibr::g_mu);
     ibr::drain();
     const ibr::Acc& a = ibr::g_acc[idx];
     if (name && name_len > 0) {
-        std::strncpy(name, ibr::kNames[idx], (size_t)name_len - 1);
+        std::string nm = ibr::kNames[idx % ibr::KID_COUNT];
+        if (idx >= ibr::KID_COUNT) nm += "@large";
+        std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
         name[name_len - 1] = 0;
     }
     if (launches) *launches = a.launches;
