@@ -43,15 +43,15 @@ __device__ __forceinline__ T nbr_sum(const T* __restrict__ u, const Nbr& n) {
 
 // y_v^a = sigma v^a - kh2 (nbrsum - 2D v^a) + (p_c - p_{c-e_a}) ih + shift_a ;
 // y_p = -ih sum_a (v^a_{c+e_a} - v^a_c)
+// Launch shape of the grid kernels: blocks of 32 x 8 threads over (x, y),
+// gridDim.z = n2 * (number of stacked fields); no 64-bit index division.
+constexpr int BX = 32, BY = 8;
+
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __restrict__ y, Geo g, T sigma, T kh2,
                                                 T ih, const double* __restrict__ shift) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= g.ncell) return;
-    int i = (int)(t % g.n0);
-    long long r = t / g.n0;
-    int j = (int)(r % g.n1);
-    int k = (int)(r / g.n1);
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
     const T* p = x + D * g.ncell;
     T pc = p[n.c];
@@ -74,7 +74,17 @@ __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __re
 // ---- point operators shared by the per-level kernels and the one-CTA tail ----
 // (same arithmetic, so a level gives the same result on either path)
 
-// red-black Gauss-Seidel update of the t-th cell of the given colour
+// red-black Gauss-Seidel update of cell (i, j, k)
+template <int D, typename T>
+__device__ __forceinline__ void rbgs_cell(T* u, const T* f, const Geo& g, T sigma, T kh2, int zero_init, int i, int j,
+                                          int k) {
+    Nbr n = neighbours<D>(g, i, j, k);
+    T nb = zero_init ? T(0) : nbr_sum<D, T>(u, n);
+    T diag = sigma + T(2 * D) * kh2;
+    u[n.c] = (f[n.c] + kh2 * nb) / diag;
+}
+
+// the same for the t-th cell of the given colour (x index ih = t mod n0/2)
 template <int D, typename T>
 __device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, T sigma, T kh2, int color, int zero_init,
                                            long long t) {
@@ -83,21 +93,12 @@ __device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, T sig
     long long r = t / hn0;
     int j = (int)(r % g.n1);
     int k = (int)(r / g.n1);
-    int i = 2 * ih + ((j + k + color) & 1);
-    Nbr n = neighbours<D>(g, i, j, k);
-    T nb = zero_init ? T(0) : nbr_sum<D, T>(u, n);
-    T diag = sigma + T(2 * D) * kh2;
-    u[n.c] = (f[n.c] + kh2 * nb) / diag;
+    rbgs_cell<D, T>(u, f, g, sigma, kh2, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
 }
 
-// coarse cell t: average over its 2^D children of f - (sigma u - kh2 Lap u)
+// coarse cell (I, J, K): average over its 2^D children of f - (sigma u - kh2 Lap u)
 template <int D, typename T>
-__device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& gf, const Geo& gc, T sigma, T kh2,
-                                            long long t) {
-    int I = (int)(t % gc.n0);
-    long long r = t / gc.n0;
-    int J = (int)(r % gc.n1);
-    int K = (int)(r / gc.n1);
+__device__ __forceinline__ T restrict_cell(const T* u, const T* f, const Geo& gf, T sigma, T kh2, int I, int J, int K) {
     T acc = T(0);
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
@@ -112,14 +113,20 @@ __device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& g
     return acc * (T(1) / T(1 << D));
 }
 
-// fine cell t: cell-centred (bi/tri)linear interpolation of the coarse
+template <int D, typename T>
+__device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& gf, const Geo& gc, T sigma, T kh2,
+                                            long long t) {
+    int I = (int)(t % gc.n0);
+    long long r = t / gc.n0;
+    int J = (int)(r % gc.n1);
+    int K = (int)(r / gc.n1);
+    return restrict_cell<D, T>(u, f, gf, sigma, kh2, I, J, K);
+}
+
+// fine cell (i, j, k): cell-centred (bi/tri)linear interpolation of the coarse
 // correction, weights 3/4 (parent) and 1/4 (the neighbour on the child's side)
 template <int D, typename T>
-__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, long long t) {
-    int i = (int)(t % gf.n0);
-    long long r = t / gf.n0;
-    int j = (int)(r % gf.n1);
-    int k = (int)(r / gf.n1);
+__device__ __forceinline__ T prolong_cell(const T* cc, const Geo& gc, int i, int j, int k) {
     int I[2], Jc[2], Kc[2];
     I[0] = i >> 1;
     I[1] = (i & 1) ? (I[0] + 1 == gc.n0 ? 0 : I[0] + 1) : (I[0] == 0 ? gc.n0 - 1 : I[0] - 1);
@@ -141,6 +148,15 @@ __device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo
         acc += ww * cc[idx];
     }
     return acc;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, long long t) {
+    int i = (int)(t % gf.n0);
+    long long r = t / gf.n0;
+    int j = (int)(r % gf.n1);
+    int k = (int)(r / gf.n1);
+    return prolong_cell<D, T>(cc, gc, i, j, k);
 }
 
 // block-wide mean of a[0..n) (all threads get it); red: 32 doubles of shared memory
@@ -200,27 +216,30 @@ __device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int swe
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
                                               int color, int zero_init) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (g.ncell >> 1)) return;
-    int cmp = blockIdx.y;
-    rbgs_point<D, T>(u + cmp * g.ncell, f + cmp * g.ncell, g, sigma, kh2, color, zero_init, t);
+    int ih = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    int k = blockIdx.z % g.n2, cmp = blockIdx.z / g.n2;
+    if (ih >= (g.n0 >> 1) || j >= g.n1) return;
+    long long off = (long long)cmp * g.ncell;
+    rbgs_cell<D, T>(u + off, f + off, g, sigma, kh2, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
                                                         T* __restrict__ fc, Geo gf, Geo gc, T sigma, T kh2) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= gc.ncell) return;
-    int cmp = blockIdx.y;
-    fc[cmp * gc.ncell + t] = restrict_point<D, T>(u + cmp * gf.ncell, f + cmp * gf.ncell, gf, gc, sigma, kh2, t);
+    int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+    int K = blockIdx.z % gc.n2, cmp = blockIdx.z / gc.n2;
+    if (I >= gc.n0 || J >= gc.n1) return;
+    long long t = I + (long long)gc.n0 * (J + (long long)gc.n1 * K);
+    fc[cmp * gc.ncell + t] = restrict_cell<D, T>(u + cmp * gf.ncell, f + cmp * gf.ncell, gf, sigma, kh2, I, J, K);
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __restrict__ uc, Geo gf, Geo gc) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= gf.ncell) return;
-    int cmp = blockIdx.y;
-    u[cmp * gf.ncell + t] += prolong_point<D, T>(uc + cmp * gc.ncell, gf, gc, t);
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    int k = blockIdx.z % gf.n2, cmp = blockIdx.z / gf.n2;
+    if (i >= gf.n0 || j >= gf.n1) return;
+    long long t = i + (long long)gf.n0 * (j + (long long)gf.n1 * k);
+    u[cmp * gf.ncell + t] += prolong_cell<D, T>(uc + cmp * gc.ncell, gc, i, j, k);
 }
 
 // single-CTA coarse solve of the coarsest level (one CTA per field)
@@ -340,12 +359,8 @@ __global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_ps_div(const T* __restrict__ y, const T* __restrict__ hd,
                                                 T* __restrict__ qr, T rhs_scale, T* __restrict__ q, Geo g, T ih) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= g.ncell) return;
-    int i = (int)(t % g.n0);
-    long long r = t / g.n0;
-    int j = (int)(r % g.n1);
-    int k = (int)(r / g.n1);
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
     const long long pp[3] = {n.xp, n.yp, n.zp};
     T div = T(0);
@@ -364,12 +379,8 @@ template <int D, typename T>
 __global__ void __launch_bounds__(256) k_ps_finish(const T* __restrict__ y, const T* __restrict__ phi,
                                                    const T* __restrict__ q, T* __restrict__ z, Geo g, T h, T c_q,
                                                    T c_phi) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= g.ncell) return;
-    int i = (int)(t % g.n0);
-    long long r = t / g.n0;
-    int j = (int)(r % g.n1);
-    int k = (int)(r / g.n1);
+    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
     const long long pm[3] = {n.xm, n.ym, n.zm};
     T pc = phi[n.c];
@@ -385,12 +396,12 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
                   cudaStream_t s) {
     T kh2 = (T)(eta / (g.h * g.h));
     T ih = (T)(1.0 / g.h);
-    int nb = grid_1d(g.ncell, 256);
+    dim3 grid((g.n0 + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2), blk(BX, BY);
     ProfScope ps(KID_STOKES, s, 2.0 * (g.d + 1) * g.ncell * sizeof(T));
     if (g.d == 3)
-        k_stokes<3, T><<<nb, 256, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+        k_stokes<3, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
     else
-        k_stokes<2, T><<<nb, 256, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+        k_stokes<2, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
     IBR_CHECK_LAUNCH();
 }
 
@@ -398,13 +409,13 @@ template <typename T>
 void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int color, bool zero_init,
                cudaStream_t s) {
     T kh2 = (T)(kappa / (g.h * g.h));
-    dim3 grid(grid_1d(g.ncell / 2, 256), C);
+    dim3 grid(((g.n0 >> 1) + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2 * C), blk(BX, BY);
     // half sweep: read the other colour and f of this colour, write this colour
     ProfScope ps(KID_RBGS, s, (zero_init ? 1.0 : 1.5) * C * g.ncell * sizeof(T));
     if (g.d == 3)
-        k_rbgs<3, T><<<grid, 256, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
+        k_rbgs<3, T><<<grid, blk, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
     else
-        k_rbgs<2, T><<<grid, 256, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
+        k_rbgs<2, T><<<grid, blk, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
     IBR_CHECK_LAUNCH();
 }
 
@@ -412,23 +423,23 @@ template <typename T>
 void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
                           double kappa, cudaStream_t s) {
     T kh2 = (T)(kappa / (gf.h * gf.h));
-    dim3 grid(grid_1d(gc.ncell, 256), C);
+    dim3 grid((gc.n0 + BX - 1) / BX, (gc.n1 + BY - 1) / BY, gc.n2 * C), blk(BX, BY);
     ProfScope ps(KID_RESTRICT, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
     if (gf.d == 3)
-        k_resid_restrict<3, T><<<grid, 256, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
+        k_resid_restrict<3, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
     else
-        k_resid_restrict<2, T><<<grid, 256, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
+        k_resid_restrict<2, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
     IBR_CHECK_LAUNCH();
 }
 
 template <typename T>
 void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, cudaStream_t s) {
-    dim3 grid(grid_1d(gf.ncell, 256), C);
+    dim3 grid((gf.n0 + BX - 1) / BX, (gf.n1 + BY - 1) / BY, gf.n2 * C), blk(BX, BY);
     ProfScope ps(KID_PROLONG, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
     if (gf.d == 3)
-        k_prolong<3, T><<<grid, 256, 0, s>>>(u, uc, gf, gc);
+        k_prolong<3, T><<<grid, blk, 0, s>>>(u, uc, gf, gc);
     else
-        k_prolong<2, T><<<grid, 256, 0, s>>>(u, uc, gf, gc);
+        k_prolong<2, T><<<grid, blk, 0, s>>>(u, uc, gf, gc);
     IBR_CHECK_LAUNCH();
 }
 
@@ -523,24 +534,24 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
 
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s) {
-    int nb = grid_1d(g.ncell, 256);
+    dim3 grid((g.n0 + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2), blk(BX, BY);
     ProfScope ps(KID_PS_DIV, s, (g.d + 3.0) * g.ncell * sizeof(T));
     if (g.d == 3)
-        k_ps_div<3, T><<<nb, 256, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
+        k_ps_div<3, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
     else
-        k_ps_div<2, T><<<nb, 256, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
+        k_ps_div<2, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
     IBR_CHECK_LAUNCH();
 }
 
 template <typename T>
 void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double c_q, double c_phi,
                cudaStream_t s) {
-    int nb = grid_1d(g.ncell, 256);
+    dim3 grid((g.n0 + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2), blk(BX, BY);
     ProfScope ps(KID_PS_FINISH, s, (2.0 * g.d + 3.0) * g.ncell * sizeof(T));
     if (g.d == 3)
-        k_ps_finish<3, T><<<nb, 256, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
+        k_ps_finish<3, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
     else
-        k_ps_finish<2, T><<<nb, 256, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
+        k_ps_finish<2, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
     IBR_CHECK_LAUNCH();
 }
 
