@@ -858,6 +858,7 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
         for (int a = 0; a < dim; ++a) G->vol *= L[a];
         G->precision = precision;
         G->geo = make_geo(dim, n, h);
+        require(G->geo.ncell < (1LL << 31), "a field must have fewer than 2^31 cells");
         G->nS = (long long)(dim + 1) * G->geo.ncell;
         G->len = G->nS;
         // the coarsest multigrid level must fit one CTA's shared memory

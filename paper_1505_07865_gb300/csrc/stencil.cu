@@ -8,26 +8,28 @@
 namespace ibr {
 namespace {
 
+// flat index and wrapped neighbour offsets of a cell; 32-bit (a field has
+// fewer than 2^31 cells, checked when the grid is created)
 struct Nbr {
-    long long c;          // flat index
-    long long xp, xm;     // offsets to i+1, i-1 (wrapped)
-    long long yp, ym;
-    long long zp, zm;
+    int c;
+    int xp, xm;
+    int yp, ym;
+    int zp, zm;
 };
 
 template <int D>
 __device__ __forceinline__ Nbr neighbours(const Geo& g, int i, int j, int k) {
     Nbr n;
-    long long sy = g.n0;
-    long long sz = (long long)g.n0 * g.n1;
+    const int sy = g.n0;
+    const int sz = g.n0 * g.n1;
     n.c = i + sy * j + sz * k;
-    n.xp = (i == g.n0 - 1) ? -(long long)(g.n0 - 1) : 1;
-    n.xm = (i == 0) ? (long long)(g.n0 - 1) : -1;
-    n.yp = (j == g.n1 - 1) ? -(long long)(g.n1 - 1) * sy : sy;
-    n.ym = (j == 0) ? (long long)(g.n1 - 1) * sy : -sy;
+    n.xp = (i == g.n0 - 1) ? 1 - g.n0 : 1;
+    n.xm = (i == 0) ? g.n0 - 1 : -1;
+    n.yp = (j == g.n1 - 1) ? (1 - g.n1) * sy : sy;
+    n.ym = (j == 0) ? (g.n1 - 1) * sy : -sy;
     if (D == 3) {
-        n.zp = (k == g.n2 - 1) ? -(long long)(g.n2 - 1) * sz : sz;
-        n.zm = (k == 0) ? (long long)(g.n2 - 1) * sz : -sz;
+        n.zp = (k == g.n2 - 1) ? (1 - g.n2) * sz : sz;
+        n.zm = (k == 0) ? (g.n2 - 1) * sz : -sz;
     } else {
         n.zp = n.zm = 0;
     }
@@ -56,8 +58,8 @@ __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __re
     const T* p = x + D * g.ncell;
     T pc = p[n.c];
     T div = T(0);
-    const long long pm[3] = {n.xm, n.ym, n.zm};
-    const long long pp[3] = {n.xp, n.yp, n.zp};
+    const int pm[3] = {n.xm, n.ym, n.zm};
+    const int pp[3] = {n.xp, n.yp, n.zp};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T* u = x + a * g.ncell;
@@ -75,13 +77,19 @@ __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __re
 // (same arithmetic, so a level gives the same result on either path)
 
 // red-black Gauss-Seidel update of cell (i, j, k)
+// inv_diag = 1 / (sigma + 2D kh2), formed by rbgs_inv_diag on host or device
 template <int D, typename T>
-__device__ __forceinline__ void rbgs_cell(T* u, const T* f, const Geo& g, T sigma, T kh2, int zero_init, int i, int j,
-                                          int k) {
+__host__ __device__ __forceinline__ T rbgs_inv_diag(T sigma, T kh2) {
+    T diag = sigma + T(2 * D) * kh2;
+    return T(1) / diag;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void rbgs_cell(T* u, const T* f, const Geo& g, T kh2, T inv_diag, int zero_init, int i,
+                                          int j, int k) {
     Nbr n = neighbours<D>(g, i, j, k);
     T nb = zero_init ? T(0) : nbr_sum<D, T>(u, n);
-    T diag = sigma + T(2 * D) * kh2;
-    u[n.c] = (f[n.c] + kh2 * nb) / diag;
+    u[n.c] = (f[n.c] + kh2 * nb) * inv_diag;
 }
 
 // the same for the t-th cell of the given colour (x index ih = t mod n0/2)
@@ -93,7 +101,7 @@ __device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, T sig
     long long r = t / hn0;
     int j = (int)(r % g.n1);
     int k = (int)(r / g.n1);
-    rbgs_cell<D, T>(u, f, g, sigma, kh2, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
+    rbgs_cell<D, T>(u, f, g, kh2, rbgs_inv_diag<D, T>(sigma, kh2), zero_init, 2 * ih + ((j + k + color) & 1), j, k);
 }
 
 // coarse cell (I, J, K): average over its 2^D children of f - (sigma u - kh2 Lap u)
@@ -144,7 +152,7 @@ __device__ __forceinline__ T prolong_cell(const T* cc, const Geo& gc, int i, int
     for (int c = 0; c < (1 << D); ++c) {
         int a = c & 1, b = (c >> 1) & 1, e = D == 3 ? (c >> 2) & 1 : 0;
         T ww = w[a] * w[b] * (D == 3 ? w[e] : T(1));
-        long long idx = I[a] + (long long)gc.n0 * (Jc[b] + (long long)gc.n1 * Kc[e]);
+        int idx = I[a] + gc.n0 * (Jc[b] + gc.n1 * Kc[e]);
         acc += ww * cc[idx];
     }
     return acc;
@@ -192,7 +200,7 @@ __device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int swe
         su[c] = T(0);
     }
     __syncthreads();
-    T diag = sigma + T(2 * D) * kh2;
+    T inv = rbgs_inv_diag<D, T>(sigma, kh2);
     for (int s = 0; s < sweeps; ++s) {
         for (int color = 0; color < 2; ++color) {
             for (long long c = tid; c < g.ncell; c += nt) {
@@ -202,7 +210,7 @@ __device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int swe
                 int k = (int)(r / g.n1);
                 if (((i + j + k) & 1) != color) continue;
                 Nbr n = neighbours<D>(g, i, j, k);
-                su[c] = (sf[c] + kh2 * nbr_sum<D, T>(su, n)) / diag;
+                su[c] = (sf[c] + kh2 * nbr_sum<D, T>(su, n)) * inv;
             }
             __syncthreads();
         }
@@ -214,13 +222,13 @@ __device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int swe
 
 // red-black Gauss-Seidel half sweep on C stacked fields (component = blockIdx.y)
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
+__global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, T kh2, T inv_diag,
                                               int color, int zero_init) {
     int ih = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     int k = blockIdx.z % g.n2, cmp = blockIdx.z / g.n2;
     if (ih >= (g.n0 >> 1) || j >= g.n1) return;
     long long off = (long long)cmp * g.ncell;
-    rbgs_cell<D, T>(u + off, f + off, g, sigma, kh2, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
+    rbgs_cell<D, T>(u + off, f + off, g, kh2, inv_diag, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
 }
 
 template <int D, typename T>
@@ -413,9 +421,9 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa
     // half sweep: read the other colour and f of this colour, write this colour
     ProfScope ps(KID_RBGS, s, (zero_init ? 1.0 : 1.5) * C * g.ncell * sizeof(T));
     if (g.d == 3)
-        k_rbgs<3, T><<<grid, blk, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
+        k_rbgs<3, T><<<grid, blk, 0, s>>>(u, f, g, kh2, rbgs_inv_diag<3, T>((T)sigma, kh2), color, zero_init ? 1 : 0);
     else
-        k_rbgs<2, T><<<grid, blk, 0, s>>>(u, f, g, (T)sigma, kh2, color, zero_init ? 1 : 0);
+        k_rbgs<2, T><<<grid, blk, 0, s>>>(u, f, g, kh2, rbgs_inv_diag<2, T>((T)sigma, kh2), color, zero_init ? 1 : 0);
     IBR_CHECK_LAUNCH();
 }
 
