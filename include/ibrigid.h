@@ -73,6 +73,7 @@ extern "C" {
                                /* FP32 preconditioner (MG, P_S, inner GMRES,      */
                                /* spread/interp inside it, M~^-1)                 */
 #define IBR_PRESCRIBED 0       /* body velocity given (Sec. II)                   */
+#define IBR_FREE       1       /* body force and torque given, velocity unknown   */
 #define IBR_PC_LOWER 0         /* lower block-triangular Schur preconditioner     */
 #define IBR_PC_FULL  1         /* full Schur preconditioner (steps 1-4, Sec. V.A) */
 #define IBR_MOB_AUTO  0        /* RPY (3-D) / App. B steady form (2-D)            */
@@ -127,7 +128,11 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L,
 
 /* Adds a rigid body with reference point x_c[dim] and orientation quat[4]
  * (w,x,y,z; unit; 2-D uses the rotation about z it describes).  kinematics:
- * IBR_PRESCRIBED.  Writes the body index (0,1,...) to *body_id. */
+ * IBR_PRESCRIBED (velocity given) or IBR_FREE (force and torque given; the
+ * rigid velocity becomes an unknown: the markers satisfy J v = K U and the
+ * force balance K^T Lambda = F is added, Sec. II; the preconditioner adds the
+ * body block N = (K^T M~^-1 K)^-1 in FP64, Sec. VIII).  Writes the body index
+ * (0,1,...) to *body_id. */
 int ibr_add_body(ibr_grid* g, const double* x_c, const double* quat, int kinematics, int* body_id);
 
 /* Sets the N markers of a body from body-frame offsets r_body[N*dim] (host).
@@ -148,9 +153,9 @@ int ibr_set_boundary_velocity(ibr_grid* g, int face, const double* values);
  * mobility options of opts (NULL: defaults). */
 int ibr_prepare(ibr_grid* g, const ibr_solve_opts* opts);
 
-/* Solves the constrained system for prescribed body velocities
- * body_UO[B*(dim+rot)] (host; per body U then Omega; rot = 1 in 2-D, 3 in
- * 3-D) with momentum forcing g (NULL: zero; else dim face arrays laid out as
+/* Solves the constrained system for body_UO[B*(dim+rot)] (host; per body U
+ * then Omega for a prescribed body, applied force F then torque T for a free
+ * one; rot = 1 in 2-D, 3 in 3-D) with momentum forcing g (NULL: zero; else dim face arrays laid out as
  * above, on the device if g_on_device != 0, else on the host; for periodic
  * steady Stokes each component must have zero mean) and h = 0.  FGMRES starts
  * from x0 = 0 and stops when the true relative residual is <= opts->tol.
@@ -164,12 +169,17 @@ int ibr_solve_coupled(ibr_grid* g, const double* body_UO, const double* gforce, 
  * (may be NULL), of the last solve to host memory. */
 int ibr_get_forces(ibr_grid* g, double* Lambda, double* body_FT);
 
+/* Rigid velocities [B*(dim+rot)] after a solve: body_UO (the array given to the
+ * solve) with the rows of free bodies replaced by their computed U, Omega. */
+int ibr_get_body_velocities(ibr_grid* g, const double* body_UO, double* out);
+
 /* Copies the velocity (dim face arrays, concatenated) and pressure of the last
  * solve.  to_device != 0: v and p are device pointers; else host. */
 int ibr_get_fields(ibr_grid* g, double* v, double* p, int to_device);
 
-/* Total length of a system vector, (dim+1)*cells + dim*N, and the marker and
- * body counts (any output pointer may be NULL). */
+/* Total length of a system vector, (dim+1)*cells + dim*N + (dim+rot)*(free
+ * bodies) (the free bodies' velocities come last), and the marker and body
+ * counts (any output pointer may be NULL). */
 int ibr_sizes(const ibr_grid* g, long long* system_len, int* n_markers, int* n_bodies);
 
 /* ---- op-level entry points (device pointers, FP64, asynchronous) ----------

@@ -22,7 +22,7 @@ OK, EINVAL, ENOMEM, ENOTCONV, ETIMEOUT, ENUMERIC, ECUDA, ESTATE = 0, -1, -2, -3,
 PERIODIC, NOSLIP, VELOCITY = 0, 1, 2
 KERNEL_PESKIN4 = 4
 FP64, MIXED = 0, 1
-PRESCRIBED = 0
+PRESCRIBED, FREE = 0, 1
 PC_LOWER, PC_FULL = 0, 1
 MOB_AUTO, MOB_RPY, MOB_FIT2D = 0, 1, 2
 
@@ -86,6 +86,7 @@ _SIGS = {
                                          ctypes.POINTER(SolveInfo)]),
     "ibr_get_forces": (ctypes.c_int, [_P, _D, _D]),
     "ibr_get_fields": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "ibr_get_body_velocities": (ctypes.c_int, [_P, _D, _D]),
     "ibr_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), _I, _I]),
     "ibr_apply_system": (ctypes.c_int, [_P, _P, _P]),
     "ibr_op_spread": (ctypes.c_int, [_P, _P, _P]),
@@ -222,6 +223,14 @@ def get_forces(grid, dim):
     ft = np.zeros(B * (dim + (1 if dim == 2 else 3)))
     _check(_lib.ibr_get_forces(grid, _dptr(lam), _dptr(ft)))
     return lam.reshape(N, dim), ft.reshape(B, -1)
+
+
+def get_body_velocities(grid, body_UO):
+    """Rigid velocities after a solve: body_UO with free bodies' rows replaced."""
+    uo = _host(body_UO)
+    out = np.zeros_like(uo)
+    _check(_lib.ibr_get_body_velocities(grid, _dptr(uo), _dptr(out)))
+    return out
 
 
 def get_fields(grid, v=None, p=None):

@@ -483,3 +483,185 @@ template void lam_sum<double>(int, int, const double*, double, double*, cudaStre
 template void lam_sum<float>(int, int, const float*, double, double*, cudaStream_t);
 
 }  // namespace ibr
+
+// ---- free kinematics (bodies with unknown rigid velocity) ------------------
+namespace ibr {
+namespace {
+
+// out[i] += sign * (K U_f)_i on the markers of free bodies (bfree[b] = free
+// index or -1); U_f body-major, nr = d + rot entries per free body
+__global__ void k_rigid_K_free(int d, int N, const double* __restrict__ rel, const int* __restrict__ body,
+                               const int* __restrict__ bfree, const double* __restrict__ Uf, double* __restrict__ out,
+                               double sign) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int fb = bfree[body[i]];
+    if (fb < 0) return;
+    int nr = d == 2 ? 3 : 6;
+    const double* u = Uf + (long long)fb * nr;
+    const double* r = rel + (long long)i * d;
+    if (d == 2) {
+        out[i * 2 + 0] += sign * (u[0] - u[2] * r[1]);
+        out[i * 2 + 1] += sign * (u[1] + u[2] * r[0]);
+    } else {
+        const double* O = u + 3;
+        out[i * 3 + 0] += sign * (u[0] + O[1] * r[2] - O[2] * r[1]);
+        out[i * 3 + 1] += sign * (u[1] + O[2] * r[0] - O[0] * r[2]);
+        out[i * 3 + 2] += sign * (u[2] + O[0] * r[1] - O[1] * r[0]);
+    }
+}
+
+// one CTA per body: [sum lam; sum rel x lam] of a free body written at
+// out[fb*nr .. ) (bodies with bfree[b] < 0 are skipped)
+template <typename Tl>
+__global__ void k_rigid_KT_free(int d, const int* __restrict__ bstart, const int* __restrict__ bfree,
+                                const double* __restrict__ rel, const Tl* __restrict__ lam, double* __restrict__ out) {
+    int b = blockIdx.x;
+    int fb = bfree[b];
+    if (fb < 0) return;
+    int i0 = bstart[b], i1 = bstart[b + 1];
+    int nr = d == 2 ? 3 : 6;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double* r = rel + (long long)i * d;
+        double l0 = (double)lam[(long long)i * d], l1 = (double)lam[(long long)i * d + 1];
+        if (d == 2) {
+            acc[0] += l0;
+            acc[1] += l1;
+            acc[2] += r[0] * l1 - r[1] * l0;
+        } else {
+            double l2 = (double)lam[(long long)i * d + 2];
+            acc[0] += l0;
+            acc[1] += l1;
+            acc[2] += l2;
+            acc[3] += r[1] * l2 - r[2] * l1;
+            acc[4] += r[2] * l0 - r[0] * l2;
+            acc[5] += r[0] * l1 - r[1] * l0;
+        }
+    }
+    __shared__ double sm[6][32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < nr; ++q) {
+        double s = acc[q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sm[q][wid] = s;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        for (int q = 0; q < nr; ++q) {
+            double s = lane < (int)(blockDim.x >> 5) ? sm[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) out[(long long)fb * nr + q] = s;
+        }
+    }
+}
+
+// lam[e] += sum_c X[c*dN + e] * U_f[fb(e)*nr + c] on free bodies' markers
+template <typename T>
+__global__ void k_lam_add_XU(int d, int N, const int* __restrict__ body, const int* __restrict__ bfree,
+                             const T* __restrict__ X, const double* __restrict__ Uf, T* __restrict__ lam) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long dN = (long long)N * d;
+    if (e >= dN) return;
+    int fb = bfree[body[e / d]];
+    if (fb < 0) return;
+    int nr = d == 2 ? 3 : 6;
+    double s = 0.0;
+    for (int c = 0; c < nr; ++c) s += (double)X[c * dN + e] * Uf[(long long)fb * nr + c];
+    lam[e] = (T)((double)lam[e] + s);
+}
+
+// per free body (one thread each): U = Nb (r - s), Nb nr x nr row-major
+__global__ void k_body_solve(int nfree, int nr, const double* __restrict__ Nb, const double* __restrict__ r,
+                             const double* __restrict__ s, double* __restrict__ U) {
+    int fb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fb >= nfree) return;
+    const double* A = Nb + (long long)fb * nr * nr;
+    for (int a = 0; a < nr; ++a) {
+        double acc = 0.0;
+        for (int c = 0; c < nr; ++c) acc += A[a * nr + c] * (r[fb * nr + c] - s[fb * nr + c]);
+        U[fb * nr + a] = acc;
+    }
+}
+
+// in-place inverse of each free body's nr x nr block (Gauss-Jordan with
+// partial pivoting, FP64, one thread per body); info set if singular
+__global__ void k_small_inverse(int nfree, int nr, double* __restrict__ A, int* __restrict__ info) {
+    int fb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fb >= nfree) return;
+    double* M = A + (long long)fb * nr * nr;
+    double a[6][12];
+    for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < 2 * nr; ++j) a[i][j] = j < nr ? M[i * nr + j] : (j - nr == i ? 1.0 : 0.0);
+    for (int c = 0; c < nr; ++c) {
+        int p = c;
+        for (int i = c + 1; i < nr; ++i)
+            if (fabs(a[i][c]) > fabs(a[p][c])) p = i;
+        if (!(fabs(a[p][c]) > 0.0)) {
+            atomicExch(info, 1);
+            return;
+        }
+        if (p != c)
+            for (int j = 0; j < 2 * nr; ++j) {
+                double t = a[c][j];
+                a[c][j] = a[p][j];
+                a[p][j] = t;
+            }
+        double iv = 1.0 / a[c][c];
+        for (int j = 0; j < 2 * nr; ++j) a[c][j] *= iv;
+        for (int i = 0; i < nr; ++i) {
+            if (i == c) continue;
+            double f = a[i][c];
+            for (int j = 0; j < 2 * nr; ++j) a[i][j] -= f * a[c][j];
+        }
+    }
+    for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < nr; ++j) M[i * nr + j] = a[i][nr + j];
+}
+
+}  // namespace
+
+void rigid_K_free(int d, int N, const double* rel, const int* body, const int* bfree, const double* Uf, double* out,
+                  double sign, cudaStream_t s) {
+    ProfScope ps(KID_RIGID_K, s, 0.0);
+    k_rigid_K_free<<<grid_1d(N, 128), 128, 0, s>>>(d, N, rel, body, bfree, Uf, out, sign);
+    IBR_CHECK_LAUNCH();
+}
+
+template <typename Tl>
+void rigid_KT_free(int d, int B, const int* bstart, const int* bfree, const double* rel, const Tl* lam, double* out,
+                   cudaStream_t s) {
+    ProfScope ps(KID_RIGID_KT, s, 0.0);
+    k_rigid_KT_free<Tl><<<B, 256, 0, s>>>(d, bstart, bfree, rel, lam, out);
+    IBR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void lam_add_XU(int d, int N, const int* body, const int* bfree, const T* X, const double* Uf, T* lam,
+                cudaStream_t s) {
+    ProfScope ps(KID_RIGID_K, s, 0.0);
+    k_lam_add_XU<T><<<grid_1d((long long)N * d, 128), 128, 0, s>>>(d, N, body, bfree, X, Uf, lam);
+    IBR_CHECK_LAUNCH();
+}
+
+void body_solve(int nfree, int nr, const double* Nb, const double* r, const double* sv, double* U, cudaStream_t s) {
+    ProfScope ps(KID_SMALL, s, 0.0);
+    k_body_solve<<<grid_1d(nfree, 32), 32, 0, s>>>(nfree, nr, Nb, r, sv, U);
+    IBR_CHECK_LAUNCH();
+}
+
+void small_inverse(int nfree, int nr, double* A, int* info, cudaStream_t s) {
+    ProfScope ps(KID_SMALL, s, 0.0);
+    k_small_inverse<<<grid_1d(nfree, 32), 32, 0, s>>>(nfree, nr, A, info);
+    IBR_CHECK_LAUNCH();
+}
+
+template void rigid_KT_free<double>(int, int, const int*, const int*, const double*, const double*, double*,
+                                    cudaStream_t);
+template void rigid_KT_free<float>(int, int, const int*, const int*, const double*, const float*, double*,
+                                   cudaStream_t);
+template void lam_add_XU<double>(int, int, const int*, const int*, const double*, const double*, double*,
+                                 cudaStream_t);
+template void lam_add_XU<float>(int, int, const int*, const int*, const float*, const double*, float*, cudaStream_t);
+
+}  // namespace ibr

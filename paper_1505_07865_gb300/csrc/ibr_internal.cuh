@@ -234,6 +234,20 @@ void rigid_K(int d, int N, const double* rel, const int* body, const double* UO,
 void rigid_KT(int d, int B, const int* body_start, const double* rel, const double* lam, double* FT,
               cudaStream_t s);
 
+// free kinematics: bfree[b] = index of body b among the free bodies or -1;
+// U_f and the per-body outputs are body-major with nr = d + rot entries.
+void rigid_K_free(int d, int N, const double* rel, const int* body, const int* bfree, const double* Uf, double* out,
+                  double sign, cudaStream_t s);  // out += sign K_f U_f
+template <typename Tl>
+void rigid_KT_free(int d, int B, const int* bstart, const int* bfree, const double* rel, const Tl* lam, double* out,
+                   cudaStream_t s);  // out = K_f^T lam
+template <typename T>
+void lam_add_XU(int d, int N, const int* body, const int* bfree, const T* X, const double* Uf, T* lam,
+                cudaStream_t s);  // lam += X U_f, X = nr columns of length dN
+void body_solve(int nfree, int nr, const double* Nb, const double* r, const double* sv, double* U,
+                cudaStream_t s);  // U = Nb (r - sv)
+void small_inverse(int nfree, int nr, double* A, int* info, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // dense.cu -- approximate mobility blocks
 struct MobParams {

@@ -142,6 +142,10 @@ struct ibr_grid {
     MarkerData md;
     int N = 0;
     long long nS = 0, len = 0;
+    // free kinematics: bodies with unknown velocity under a given load
+    int nfree = 0, nU = 0;   // free bodies, their unknowns ((d + rot) each)
+    std::vector<int> bfree;  // body -> free index or -1
+    int* bfree_dev = nullptr;
     // mobility
     std::vector<long long> moff;
     std::vector<int> roff;
@@ -189,6 +193,11 @@ struct PC {
     // the preconditioner body (from rs and rL to xs and lamT) captured once as a
     // CUDA graph and replayed; invalidated by a new geometry or new options
     double* rL = nullptr;  // FP64 copy of the constraint part of the input
+    // free bodies: X = M~^-1 K_f (nr columns of length dN), the FP64 body blocks
+    // Nb = (K_f^T M~^-1 K_f)^-1, and the load / velocity vectors of the apply
+    T* Xf = nullptr;
+    double *Nb = nullptr, *rU = nullptr, *sU = nullptr, *Uo = nullptr;
+    bool free_ready = false;
     cudaGraphExec_t gexec = nullptr;
     int g_ns = -1, g_pre = -1, g_post = -1, g_variant = -1;
     long long g_launches = 0;
@@ -233,14 +242,76 @@ struct PC {
         dfree(dU);
         dfree(lamT);
         dfree(rL);
+        dfree(Xf);
+        dfree(Nb);
+        dfree(rU);
+        dfree(sU);
+        dfree(Uo);
+        free_ready = false;
         long long dN = (long long)G->N * G->d;
         dU = dalloc<T>(std::max(dN, 1LL));
         lamT = dalloc<T>(std::max(dN, 1LL));
         rL = dalloc<double>(std::max(dN, 1LL));
+        if (G->nfree > 0) {
+            int nr = G->d + G->rot();
+            Xf = dalloc<T>((size_t)nr * std::max(dN, 1LL));
+            Nb = dalloc<double>((size_t)G->nfree * nr * nr);
+            rU = dalloc<double>(G->nU);
+            sU = dalloc<double>(G->nU);
+            Uo = dalloc<double>(G->nU);
+        }
+    }
+
+    // X = M~^-1 K_f column by column, then the body blocks K_f^T X and their
+    // FP64 inverses (the free bodies' mobilities, Sec. VIII)
+    void setup_free() {
+        if (G->nfree == 0 || free_ready) return;
+        cudaStream_t s = G->stream;
+        int d = G->d, nr = d + G->rot(), N = G->N, B = (int)G->bodies.size();
+        long long dN = (long long)N * d;
+        double* col = nullptr;
+        double* unit = nullptr;
+        T* colT = nullptr;
+        IBR_CUDA_TRY(cudaMallocAsync(&col, sizeof(double) * dN, s));
+        IBR_CUDA_TRY(cudaMallocAsync(&unit, sizeof(double) * G->nU, s));
+        IBR_CUDA_TRY(cudaMallocAsync(&colT, sizeof(T) * dN, s));
+        std::vector<double> hu(G->nU);
+        std::vector<double> hN((size_t)G->nfree * nr * nr);
+        std::vector<double> kt(G->nU);
+        for (int c = 0; c < nr; ++c) {
+            for (int fb = 0; fb < G->nfree; ++fb)
+                for (int q = 0; q < nr; ++q) hu[fb * nr + q] = q == c ? 1.0 : 0.0;
+            IBR_CUDA_TRY(cudaMemcpyAsync(unit, hu.data(), sizeof(double) * G->nU, cudaMemcpyHostToDevice, s));
+            IBR_CUDA_TRY(cudaMemsetAsync(col, 0, sizeof(double) * dN, s));
+            rigid_K_free(d, N, G->md.rel, G->md.body, G->bfree_dev, unit, col, 1.0, s);
+            vec_convert<double, T>(dN, col, colT, s);
+            blockdiag_gemv<T, T>(B, G->moff_dev, G->roff_dev, (int)dN, Minv, colT, Xf + (long long)c * dN, s);
+            rigid_KT_free<T>(d, B, G->md.body_start, G->bfree_dev, G->md.rel, Xf + (long long)c * dN, sU, s);
+            IBR_CUDA_TRY(cudaMemcpyAsync(kt.data(), sU, sizeof(double) * G->nU, cudaMemcpyDeviceToHost, s));
+            IBR_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int fb = 0; fb < G->nfree; ++fb)
+                for (int q = 0; q < nr; ++q) hN[((size_t)fb * nr + q) * nr + c] = kt[fb * nr + q];
+        }
+        IBR_CUDA_TRY(cudaMemcpyAsync(Nb, hN.data(), sizeof(double) * hN.size(), cudaMemcpyHostToDevice, s));
+        IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, sizeof(int), s));
+        small_inverse(G->nfree, nr, Nb, G->info_dev, s);
+        int info = 0;
+        IBR_CUDA_TRY(cudaMemcpyAsync(&info, G->info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(col);
+        cudaFree(unit);
+        cudaFree(colT);
+        if (info) throw Error{IBR_ENUMERIC, "a free body's resistance block K^T M~^-1 K is singular"};
+        free_ready = true;
     }
     ~PC() {
         invalidate_graph();
         dfree(rL);
+        dfree(Xf);
+        dfree(Nb);
+        dfree(rU);
+        dfree(sU);
+        dfree(Uo);
         mg.release();
         T* tp[] = {Vi, Zi, w, rs, rs2, xs, y, phi, q, qr, dU, lamT};
         for (T* p : tp)
@@ -302,6 +373,13 @@ struct PC {
             interp<T, double>(g, G->md, xs, dU, -1.0, rL, s, -1.0);          // step 2: dU = -(J v + W)
             blockdiag_gemv<T, T>((int)G->bodies.size(), G->moff_dev, G->roff_dev, (int)dN, Minv, dU, lamT,
                                  s);                                        // step 3
+            if (G->nfree > 0) {
+                // free bodies: [M~ -K_f; K_f^T 0][Lambda; U] = [dU; F]  ->
+                // U = N (F - K_f^T M~^-1 dU), Lambda = M~^-1 dU + X U
+                rigid_KT_free<T>(d, (int)G->bodies.size(), G->md.body_start, G->bfree_dev, G->md.rel, lamT, sU, s);
+                body_solve(G->nfree, d + G->rot(), Nb, rU, sU, Uo, s);
+                lam_add_XU<T>(d, N, G->md.body, G->bfree_dev, Xf, Uo, lamT, s);
+            }
             if (variant == IBR_PC_FULL) {                                   // step 4
                 IBR_CUDA_TRY(cudaMemcpyAsync(rs2, rs, sizeof(T) * nS, cudaMemcpyDeviceToDevice, s));
                 spread_gather<T>(G->md, lamT, rs2, 1.0 / std::pow(g.h, d), s);
@@ -338,6 +416,8 @@ struct PC {
         long long dN = (long long)N * G->d;
         if (!fluid_prepared) vec_convert<double, T>(nS, r, rs, s);
         if (N > 0) IBR_CUDA_TRY(cudaMemcpyAsync(rL, r + nS, sizeof(double) * dN, cudaMemcpyDeviceToDevice, s));
+        if (G->nfree > 0)
+            IBR_CUDA_TRY(cudaMemcpyAsync(rU, r + nS + dN, sizeof(double) * G->nU, cudaMemcpyDeviceToDevice, s));
         long long ps_per = (long long)ns * (variant == IBR_PC_FULL && N > 0 ? 2 : 1);
         if (use_graphs()) {
             if (gexec && (g_ns != ns || g_pre != pre || g_post != post || g_variant != variant)) invalidate_graph();
@@ -373,6 +453,8 @@ struct PC {
         }
         vec_convert<T, double>(nS, xs, z, s);
         if (N > 0) vec_convert<T, double>(dN, lamT, z + nS, s);
+        if (G->nfree > 0)
+            IBR_CUDA_TRY(cudaMemcpyAsync(z + nS + dN, Uo, sizeof(double) * G->nU, cudaMemcpyDeviceToDevice, s));
     }
 };
 
@@ -423,6 +505,7 @@ void free_markers(ibr_grid* G) {
     dfree(G->Minv32);
     dfree(G->FT);
     dfree(G->UO);
+    dfree(G->bfree_dev);
 }
 
 void free_outer(ibr_grid* G) {
@@ -509,7 +592,12 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     G->N = N;
     G->md.N = N;
     G->md.B = B;
-    G->len = G->nS + (long long)N * d;
+    G->bfree.assign(B, -1);
+    G->nfree = 0;
+    for (int bi = 0; bi < B; ++bi)
+        if (G->bodies[bi].kin == IBR_FREE) G->bfree[bi] = G->nfree++;
+    G->nU = G->nfree * (d + G->rot());
+    G->len = G->nS + (long long)N * d + G->nU;
     std::vector<double> rb((size_t)N * d);
     std::vector<int> body(N), bstart(B + 1);
     std::vector<double> xcR((size_t)B * 12);
@@ -607,6 +695,8 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
         cudaFree(work);
     }
     G->FT = dalloc<double>((size_t)B * (d + G->rot()));
+    G->bfree_dev = dalloc<int>(B);
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->bfree_dev, G->bfree.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
     G->UO = dalloc<double>((size_t)B * (d + G->rot()));
     cudaFree(rb_dev);
     cudaFree(xcR_dev);
@@ -665,6 +755,13 @@ void full_matvec(ibr_grid* G, const double* x, double* y) {
     if (G->N > 0) {
         spread_gather<double>(G->md, lam, y, -1.0 / std::pow(g.h, d), s);
         interp<double, double>(g, G->md, x, y + nS, -1.0, nullptr, s, 0.0);
+    }
+    if (G->nfree > 0) {
+        // free bodies: -J v + K_f U_f on their markers, and K_f^T Lambda
+        long long dN = (long long)G->N * d;
+        rigid_K_free(d, G->N, G->md.rel, G->md.body, G->bfree_dev, x + nS + dN, y + nS, 1.0, s);
+        rigid_KT_free<double>(d, (int)G->bodies.size(), G->md.body_start, G->bfree_dev, G->md.rel, lam,
+                              y + nS + dN, s);
     }
 }
 
@@ -887,7 +984,7 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
 int ibr_add_body(ibr_grid* G, const double* x_c, const double* quat, int kinematics, int* body_id) {
     return run_guarded("ibr_add_body", [&] {
         require(G && x_c, "grid and x_c must be non-NULL");
-        require(kinematics == IBR_PRESCRIBED, "only IBR_PRESCRIBED kinematics are supported");
+        require(kinematics == IBR_PRESCRIBED || kinematics == IBR_FREE, "kinematics must be IBR_PRESCRIBED or IBR_FREE");
         Body b;
         for (int a = 0; a < G->d; ++a) b.xc[a] = x_c[a];
         if (quat) quat_to_R(quat, b.R);
@@ -963,8 +1060,17 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
         int nuo = B * (G->d + G->rot());
         for (int i = 0; i < nuo; ++i)
             if (!std::isfinite(body_UO[i])) throw Error{IBR_ENUMERIC, "body_UO contains NaN/Inf"};
-        IBR_CUDA_TRY(cudaMemcpyAsync(G->UO, body_UO, nuo * sizeof(double), cudaMemcpyHostToDevice, s));
-        // b = [g; 0; W = -K U]
+        // prescribed bodies' velocities (free bodies' rows zeroed: their markers
+        // have W = 0) and free bodies' loads
+        std::vector<double> uo(body_UO, body_UO + nuo), load;
+        int nr = G->d + G->rot();
+        for (int bi = 0; bi < B; ++bi)
+            if (G->bfree[bi] >= 0) {
+                load.insert(load.end(), uo.begin() + bi * nr, uo.begin() + (bi + 1) * nr);
+                std::fill(uo.begin() + bi * nr, uo.begin() + (bi + 1) * nr, 0.0);
+            }
+        IBR_CUDA_TRY(cudaMemcpyAsync(G->UO, uo.data(), nuo * sizeof(double), cudaMemcpyHostToDevice, s));
+        // b = [g; 0; W = -K U; F]
         long long nS = G->nS;
         IBR_CUDA_TRY(cudaMemsetAsync(G->b, 0, nS * sizeof(double), s));
         if (gforce) {
@@ -973,6 +1079,9 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
                                          g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         }
         rigid_K(G->d, G->N, G->md.rel, G->md.body, G->UO, G->b + nS, -1.0, s);
+        if (G->nfree > 0)
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->b + nS + (long long)G->N * G->d, load.data(),
+                                         load.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         auto setup_pc = [&](auto* pc) {
             pc->ns = o.n_s;
             pc->pre = o.mg_pre;
@@ -983,9 +1092,11 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
         if (G->precision == IBR_FP64) {
             setup_pc(G->pc64);
             G->pc64->Minv = G->Minv64;
+            G->pc64->setup_free();
         } else {
             setup_pc(G->pc32);
             G->pc32->Minv = G->Minv32;
+            G->pc32->setup_free();
         }
         status = fgmres(G, o, info);
         IBR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1023,6 +1134,24 @@ int ibr_get_forces(ibr_grid* G, double* Lambda, double* body_FT) {
     });
 }
 
+int ibr_get_body_velocities(ibr_grid* G, const double* body_UO, double* out) {
+    return run_guarded("ibr_get_body_velocities", [&] {
+        require(G && body_UO && out, "grid, body_UO, out must be non-NULL");
+        if (!G->have_solution) throw Error{IBR_ESTATE, "no solution (call ibr_solve_coupled first)"};
+        int B = (int)G->bodies.size(), nr = G->d + G->rot();
+        std::copy(body_UO, body_UO + (size_t)B * nr, out);
+        if (G->nfree > 0) {
+            std::vector<double> U(G->nU);
+            IBR_CUDA_TRY(cudaMemcpyAsync(U.data(), G->x + G->nS + (long long)G->N * G->d, G->nU * sizeof(double),
+                                         cudaMemcpyDeviceToHost, G->stream));
+            IBR_CUDA_TRY(cudaStreamSynchronize(G->stream));
+            for (int bi = 0; bi < B; ++bi)
+                if (G->bfree[bi] >= 0) std::copy(U.begin() + G->bfree[bi] * nr, U.begin() + (G->bfree[bi] + 1) * nr,
+                                                 out + (size_t)bi * nr);
+        }
+    });
+}
+
 int ibr_get_fields(ibr_grid* G, double* v, double* p, int to_device) {
     return run_guarded("ibr_get_fields", [&] {
         require(G, "grid is NULL");
@@ -1041,7 +1170,9 @@ int ibr_sizes(const ibr_grid* G, long long* system_len, int* n_markers, int* n_b
         require(G, "grid is NULL");
         int N = 0;
         for (auto& b : G->bodies) N += b.N;
-        if (system_len) *system_len = G->nS + (long long)N * G->d;
+        int nfree = 0;
+        for (auto& b : G->bodies) nfree += b.kin == IBR_FREE;
+        if (system_len) *system_len = G->nS + (long long)N * G->d + (long long)nfree * (G->d + G->rot());
         if (n_markers) *n_markers = N;
         if (n_bodies) *n_bodies = (int)G->bodies.size();
     });

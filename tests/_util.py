@@ -14,10 +14,12 @@ def oracle_problem(wl):
     return Problem(g, q, rel, body, len(wl.bodies))
 
 
-def gpu_grid(abi, wl, precision):
+def gpu_grid(abi, wl, precision, free=None):
+    """free: optional list of flags, True for a body under given force/torque."""
     g = abi.create_grid(wl.d, wl.n, wl.L, eta=wl.eta, rho=wl.rho, dt=wl.dt, precision=precision)
-    for b in wl.bodies:
-        bid = abi.add_body(g, b.center)
+    for i, b in enumerate(wl.bodies):
+        kin = abi.FREE if (free is not None and free[i]) else abi.PRESCRIBED
+        bid = abi.add_body(g, b.center, kinematics=kin)
         abi.set_markers(g, bid, b.rel)
     return g
 
