@@ -79,6 +79,10 @@ extern "C" {
 #define IBR_MOB_AUTO  0        /* RPY (3-D) / App. B steady form (2-D)            */
 #define IBR_MOB_RPY   1        /* Eq. RPYTensor (+ periodic correction, App. A)   */
 #define IBR_MOB_FIT2D 2        /* App. B Eq. fg_steady_2d                          */
+#define IBR_MOB_TRUE  3        /* the true mobility M0 = J L^-1 S of all markers,
+                                  one dense block, built in the set-up from
+                                  N*dim Stokes solves (Sec. V.C, VII.F: for
+                                  fixed geometries)                             */
 
 typedef struct ibr_grid ibr_grid;   /* opaque */
 
@@ -86,7 +90,8 @@ typedef struct ibr_solve_opts {
     double tol;            /* relative residual ||b - A x||_2 / ||b||_2 (true)   */
     int    restart;        /* FGMRES restart length m                           */
     int    max_iters;      /* cap on outer iterations (all restarts)            */
-    int    n_s;            /* inner Stokes GMRES iterations N_s (Sec. V.A)      */
+    int    n_s;            /* inner Stokes GMRES iterations N_s (Sec. V.A);
+                              0: 2 on periodic grids, 4 with walls             */
     int    variant;        /* IBR_PC_LOWER or IBR_PC_FULL                       */
     int    mg_pre;         /* pre-smoothing sweeps per V-cycle level            */
     int    mg_post;        /* post-smoothing sweeps per V-cycle level           */
@@ -109,7 +114,7 @@ typedef struct ibr_solve_info {
     double ms_solve;       /* FGMRES, wall ms                                    */
 } ibr_solve_info;
 
-/* Fills opts with the defaults: tol 1e-8, restart 50, max_iters 1000, N_s 2,
+/* Fills opts with the defaults: tol 1e-8, restart 50, max_iters 1000, N_s 0 (automatic),
  * IBR_PC_LOWER, mg 2/2, IBR_MOB_AUTO, a/h 0 (=1.25 in 3-D, see ibr_solve_coupled),
  * the library's 2-D coefficient set, no time cap. */
 int ibr_solve_opts_default(ibr_solve_opts* opts);
@@ -202,8 +207,9 @@ int ibr_op_interp(ibr_grid* g, const double* v, double* U);
 int ibr_op_rigid(ibr_grid* g, const double* UO, double* V);
 int ibr_op_rigid_T(ibr_grid* g, const double* lam, double* FT);
 
-/* Copies the dense M~ block of body b (row-major, (dim N_b)^2 doubles,
- * Eq. M_tilde_ij) into out. */
+/* Copies dense mobility block b into out (row-major): the M~ block of body b
+ * ((dim N_b)^2 doubles, Eq. M_tilde_ij), or with IBR_MOB_TRUE the single
+ * block M0 of all markers ((dim N)^2 doubles, b = 0). */
 int ibr_op_mtilde(ibr_grid* g, int body, double* out);
 
 /* out = M~^-1 rhs (block diagonal over bodies, [N*dim]) with the factorised
@@ -216,8 +222,9 @@ int ibr_op_mtilde_solve(ibr_grid* g, const double* rhs, double* out);
 int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
 
 /* k V-cycles of the scalar multigrid for (sigma I - kappa Delta_h) u = f on the
- * cell grid (periodic), starting from u (in/out).  sigma = 0 requires mean-zero
- * f and returns mean-zero u. */
+ * cell grid, starting from u (in/out); on wall axes the cell-centred
+ * homogeneous Neumann rule of the pressure.  sigma = 0 requires mean-zero f
+ * and returns mean-zero u. */
 int ibr_op_vcycle(ibr_grid* g, double sigma, double kappa, const double* f, double* u, int k);
 
 /* The V-cycles of ibr_op_vcycle (FP64, the grid's default 2/2 sweeps when

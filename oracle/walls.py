@@ -417,15 +417,21 @@ class WallProblem:
         return np.concatenate([np.concatenate([r.ravel() for r in rows]), hrow.ravel(),
                                np.asarray(W, dtype=np.float64).ravel()])
 
-    def solve(self, b):
-        """Sparse LU of the system bordered by <pi> = 0."""
+    def solve(self, b, refine=3):
+        """Sparse LU of the system bordered by <pi> = 0, plus a few steps of
+        iterative refinement in FP64 (removes the rounding the factorisation
+        leaves; the result is the exact solution)."""
         wg = self.g
         n, d = wg.ncell, wg.d
         M = self.matrix()
         c = np.zeros(self.size)
         c[d * n:(d + 1) * n] = 1.0 / n
         B = sp.bmat([[M, sp.csr_matrix(c).T], [sp.csr_matrix(c), None]], format="csc")
-        sol = spla.spsolve(B, np.concatenate([b, [0.0]]))
+        lu = spla.splu(B)
+        rhs = np.concatenate([b, [0.0]])
+        sol = lu.solve(rhs)
+        for _ in range(refine):
+            sol = sol + lu.solve(rhs - B @ sol)
         return sol[: self.size]
 
     def residual(self, x, b):

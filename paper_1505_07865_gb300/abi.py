@@ -24,7 +24,7 @@ KERNEL_PESKIN4 = 4
 FP64, MIXED = 0, 1
 PRESCRIBED, FREE = 0, 1
 PC_LOWER, PC_FULL = 0, 1
-MOB_AUTO, MOB_RPY, MOB_FIT2D = 0, 1, 2
+MOB_AUTO, MOB_RPY, MOB_FIT2D, MOB_TRUE = 0, 1, 2, 3
 
 
 class SolveOpts(ctypes.Structure):

@@ -42,8 +42,15 @@ __global__ void k_positions(int d, int N, const double* __restrict__ rb, const i
     }
 }
 
-// base[(i*d + a)*d + b], w[((i*d + a)*d + b)*4 + m] for component a, axis b
-__global__ void k_weights(Geo g, int N, const double* __restrict__ q, int* __restrict__ base, double* __restrict__ w64,
+// For component a, axis b and window node m (t = (i*d + a)*d + b):
+// idx[t*4 + m] = the stored node the window node maps to and w[t*4 + m] its
+// signed weight.  Periodic axes wrap.  On a wall axis the field is extended
+// beyond the walls by its mirror image with a sign (App. D): the component
+// tangential to the wall (cell-centred along b) by ghost = -mirror, the
+// normal component (faces 0..n on b, face 0 and face n on the walls) by
+// u(-k) = -u(k), u(n+k) = -u(n-k), and the wall faces themselves carry
+// boundary data, not unknowns: weight 0.
+__global__ void k_weights(Geo g, int N, const double* __restrict__ q, int* __restrict__ idx, double* __restrict__ w64,
                           float* __restrict__ w32) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int d = g.d;
@@ -56,18 +63,46 @@ __global__ void k_weights(Geo g, int N, const double* __restrict__ q, int* __res
     double fl = floor(s);
     int j0 = (int)fl - 1;
     int nb = b == 0 ? g.n0 : (b == 1 ? g.n1 : g.n2);
-    int jw = j0 % nb;
-    if (jw < 0) jw += nb;
-    base[t] = jw;
+    bool wall = (g.wall >> b) & 1;
     for (int m = 0; m < 4; ++m) {
         double ww = peskin4(s - (double)(j0 + m));
+        int j = j0 + m;
+        int st;
+        if (!wall) {
+            st = j % nb;
+            if (st < 0) st += nb;
+        } else if (a == b) {
+            if (j == 0 || j == nb) {
+                st = 0;
+                ww = 0.0;
+            } else if (j < 0) {
+                st = -j;
+                ww = -ww;
+            } else if (j > nb) {
+                st = 2 * nb - j;
+                ww = -ww;
+            } else {
+                st = j;
+            }
+        } else {
+            if (j < 0) {
+                st = -j - 1;
+                ww = -ww;
+            } else if (j >= nb) {
+                st = 2 * nb - 1 - j;
+                ww = -ww;
+            } else {
+                st = j;
+            }
+        }
+        idx[t * 4 + m] = st;
         w64[t * 4 + m] = ww;
         w32[t * 4 + m] = (float)ww;
     }
 }
 
 template <int D>
-__device__ __forceinline__ void entry_face(const Geo& g, const int* __restrict__ base, const double* __restrict__ w64,
+__device__ __forceinline__ void entry_face(const Geo& g, const int* __restrict__ idx, const double* __restrict__ w64,
                                            long long e, long long& key, double& wt, int& mcomp) {
     const int S = D == 3 ? 64 : 16;
     int c = (int)(e % S);
@@ -81,8 +116,7 @@ __device__ __forceinline__ void entry_face(const Geo& g, const int* __restrict__
     for (int b = 0; b < D; ++b) {
         int m = (c >> (2 * b)) & 3;
         long long t = ia * D + b;
-        int j = base[t] + m;
-        if (j >= ns[b]) j -= ns[b];
+        int j = idx[t * 4 + m];
         cell += j * stride;
         stride *= ns[b];
         wt *= w64[t * 4 + m];
@@ -91,7 +125,7 @@ __device__ __forceinline__ void entry_face(const Geo& g, const int* __restrict__
 }
 
 template <int D>
-__global__ void k_keys(Geo g, long long E, long long P, const int* __restrict__ base, const double* __restrict__ w64,
+__global__ void k_keys(Geo g, long long E, long long P, const int* __restrict__ idx, const double* __restrict__ w64,
                        unsigned long long* __restrict__ keys) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= P) return;
@@ -102,7 +136,7 @@ __global__ void k_keys(Geo g, long long E, long long P, const int* __restrict__ 
     long long key;
     double wt;
     int mc;
-    entry_face<D>(g, base, w64, e, key, wt, mc);
+    entry_face<D>(g, idx, w64, e, key, wt, mc);
     keys[e] = ((unsigned long long)key << 32) | (unsigned long long)e;
 }
 
@@ -202,7 +236,7 @@ __global__ void __launch_bounds__(1024) k_scan_single(long long E, const int* __
 
 template <int D>
 __global__ void k_seg_build(Geo g, long long E, const unsigned long long* __restrict__ keys,
-                            const int* __restrict__ flag, const int* __restrict__ pos, const int* __restrict__ base,
+                            const int* __restrict__ flag, const int* __restrict__ pos, const int* __restrict__ idx,
                             const double* __restrict__ w64, long long* __restrict__ face, int* __restrict__ off,
                             int* __restrict__ ent_m, double* __restrict__ ew64, float* __restrict__ ew32) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -211,7 +245,7 @@ __global__ void k_seg_build(Geo g, long long E, const unsigned long long* __rest
     long long key;
     double wt;
     int mc;
-    entry_face<D>(g, base, w64, e, key, wt, mc);
+    entry_face<D>(g, idx, w64, e, key, wt, mc);
     ent_m[t] = mc;
     ew64[t] = wt;
     ew32[t] = (float)wt;
@@ -238,7 +272,7 @@ __global__ void k_spread_gather(long long F, const long long* __restrict__ face,
 
 // one warp per marker; lanes stride the 4^D support of each component
 template <int D, typename T, typename Tadd>
-__global__ void k_interp(Geo g, int N, const int* __restrict__ base, const T* __restrict__ w, const T* __restrict__ v,
+__global__ void k_interp(Geo g, int N, const int* __restrict__ idx, const T* __restrict__ w, const T* __restrict__ v,
                          T* __restrict__ out, T sign, const Tadd* __restrict__ add, T add_scale) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -257,8 +291,7 @@ __global__ void k_interp(Geo g, int N, const int* __restrict__ base, const T* __
             for (int b = 0; b < D; ++b) {
                 int m = (c >> (2 * b)) & 3;
                 long long t = ia * D + b;
-                int j = base[t] + m;
-                if (j >= ns[b]) j -= ns[b];
+                int j = idx[t * 4 + m];
                 cell += j * stride;
                 stride *= ns[b];
                 wt *= w[t * 4 + m];
@@ -363,10 +396,10 @@ void markers_positions(int d, int N, const double* rbody, const int* body, const
     IBR_CHECK_LAUNCH();
 }
 
-void markers_weights(const Geo& g, int N, const double* q, int* base, double* w64, float* w32, cudaStream_t s) {
+void markers_weights(const Geo& g, int N, const double* q, int* idx, double* w64, float* w32, cudaStream_t s) {
     int n = N * g.d * g.d;
     ProfScope ps(KID_MARKERS, s, 0.0);
-    k_weights<<<grid_1d(n, 128), 128, 0, s>>>(g, N, q, base, w64, w32);
+    k_weights<<<grid_1d(n, 128), 128, 0, s>>>(g, N, q, idx, w64, w32);
     IBR_CHECK_LAUNCH();
 }
 
@@ -383,9 +416,9 @@ void markers_build_gather(const Geo& g, MarkerData& md, cudaStream_t s) {
     IBR_CUDA_TRY(cudaMallocAsync(&flag, E * sizeof(int), s));
     IBR_CUDA_TRY(cudaMallocAsync(&pos, (E + 1) * sizeof(int), s));
     if (g.d == 3)
-        k_keys<3><<<grid_1d(P, 256), 256, 0, s>>>(g, E, P, md.base, md.w64, keys);
+        k_keys<3><<<grid_1d(P, 256), 256, 0, s>>>(g, E, P, md.idx, md.w64, keys);
     else
-        k_keys<2><<<grid_1d(P, 256), 256, 0, s>>>(g, E, P, md.base, md.w64, keys);
+        k_keys<2><<<grid_1d(P, 256), 256, 0, s>>>(g, E, P, md.idx, md.w64, keys);
     IBR_CHECK_LAUNCH();
     int nchunks = (int)(P / BS_ELEMS);
     k_bitonic_local<<<nchunks, 1024, 0, s>>>(keys);
@@ -413,10 +446,10 @@ void markers_build_gather(const Geo& g, MarkerData& md, cudaStream_t s) {
     IBR_CUDA_TRY(cudaMalloc(&md.ent_w64, (size_t)E * sizeof(double)));
     IBR_CUDA_TRY(cudaMalloc(&md.ent_w32, (size_t)E * sizeof(float)));
     if (g.d == 3)
-        k_seg_build<3><<<grid_1d(E, 256), 256, 0, s>>>(g, E, keys, flag, pos, md.base, md.w64, md.face, md.off,
+        k_seg_build<3><<<grid_1d(E, 256), 256, 0, s>>>(g, E, keys, flag, pos, md.idx, md.w64, md.face, md.off,
                                                       md.ent_m, md.ent_w64, md.ent_w32);
     else
-        k_seg_build<2><<<grid_1d(E, 256), 256, 0, s>>>(g, E, keys, flag, pos, md.base, md.w64, md.face, md.off,
+        k_seg_build<2><<<grid_1d(E, 256), 256, 0, s>>>(g, E, keys, flag, pos, md.idx, md.w64, md.face, md.off,
                                                       md.ent_m, md.ent_w64, md.ent_w32);
     IBR_CHECK_LAUNCH();
     k_set_int<<<1, 1, 0, s>>>(md.off + F, (int)E);
@@ -447,9 +480,9 @@ void interp(const Geo& g, const MarkerData& md, const T* v, T* out, double sign,
     int blocks = grid_1d((long long)md.N * 32, threads);
     ProfScope ps(KID_INTERP, s, (double)md.N * g.d * ((g.d == 3 ? 64 : 16) * sizeof(T) + g.d * 4 * sizeof(T) + sizeof(T)));
     if (g.d == 3)
-        k_interp<3, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.base, w, v, out, (T)sign, add, (T)add_scale);
+        k_interp<3, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
     else
-        k_interp<2, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.base, w, v, out, (T)sign, add, (T)add_scale);
+        k_interp<2, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
     IBR_CHECK_LAUNCH();
 }
 

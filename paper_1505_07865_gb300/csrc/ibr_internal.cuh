@@ -58,13 +58,23 @@ class ProfScope {
 };
 
 // ---------------------------------------------------------------------------
-// periodic cell grid (x fastest); n2 == 1 in 2-D
+// cell grid (x fastest); n2 == 1 in 2-D.  wall: bit a set when axis a is
+// bounded by walls at both ends (else periodic).  Along a wall axis the
+// cell-centred fields and the tangential velocity components hold the n cell
+// centres; the normal component holds faces 0..n-1, face 0 on the low wall (a
+// boundary entry whose equation is `value = wall data`), face n (high wall)
+// not stored.
 struct Geo {
     int d;
     int n0, n1, n2;
     long long ncell;
     double h;
+    int wall;
 };
+
+// field codes of the stencil and multigrid kernels: velocity components
+// 0..d-1, the pressure (cell-centred, homogeneous Neumann on walls) FLD_P
+constexpr int FLD_P = 3;
 
 inline Geo make_geo(int d, const int* n, double h) {
     Geo g;
@@ -74,6 +84,7 @@ inline Geo make_geo(int d, const int* n, double h) {
     g.n2 = d == 3 ? n[2] : 1;
     g.ncell = (long long)g.n0 * g.n1 * g.n2;
     g.h = h;
+    g.wall = 0;
     return g;
 }
 
@@ -86,22 +97,25 @@ inline int grid_1d(long long work, int block) {
 
 // ---------------------------------------------------------------------------
 // stencil.cu -- MAC operators and multigrid (templated on scalar T)
-// y = [A v + G p + shift ; -D v] for the unconstrained Stokes operator.
+// y = [A v + G p + shift ; -D v] for the unconstrained Stokes operator
+// (walls: homogeneous boundary conditions; wall-face rows are the identity).
 template <typename T>
 void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, const double* shift_dev,
                   cudaStream_t s);
-// red-black Gauss-Seidel half sweep on C stacked scalar fields:
-// (sigma u - kappa Delta_h u) = f
+// The multigrid pieces act on C stacked fields with field codes fld0,
+// fld0 + 1, ... (fld0 == FLD_P: one pressure field), which fix the boundary
+// rule of each field on wall axes.
+// red-black Gauss-Seidel half sweep: (sigma u - kappa Delta_h u) = f
 template <typename T>
-void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int color, bool zero_init,
-               cudaStream_t s);
+void mg_smooth(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, double kappa, int color,
+               bool zero_init, cudaStream_t s);
 template <typename T>
-void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
-                          double kappa, cudaStream_t s);
+void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, int fld0,
+                          double sigma, double kappa, cudaStream_t s);
 template <typename T>
-void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, cudaStream_t s);
+void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, int fld0, cudaStream_t s);
 template <typename T>
-void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int sweeps,
+void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, double kappa, int sweeps,
                      cudaStream_t s);
 // One V-cycle for (sigma I - kappa Delta_h) U[0] = F0 on the levels lev[0..L)
 // (C stacked fields): red-black pre/post sweeps, averaging restriction into
@@ -112,8 +126,8 @@ constexpr int MG_TAIL_MAX_LEVELS = 8;
 constexpr long long MG_TAIL_MAX_CELLS = 4096;
 constexpr size_t MG_TAIL_MAX_SMEM = 200 * 1024;
 template <typename T>
-void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, double sigma, double kappa,
-               bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s);
+void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
+               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s);
 // red-black sweeps of the coarsest-level solve: enough for a preconditioner
 // (the coarsest grid has at most a few hundred cells)
 inline int mg_coarse_sweeps(const Geo& g) {
@@ -131,6 +145,15 @@ void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_s
 template <typename T>
 void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double c_q, double c_phi,
                cudaStream_t s);
+// Boundary data of wall `side` (0 low, 1 high) of wall axis a moved into the
+// right-hand side b = [g_0 .. g_{d-1} | h] (FP64): wall-face rows of the
+// normal component set to the wall value, data terms of the neighbouring
+// rows added (App. D extension with data).  data: [d][face points], the
+// face points ordered over the other axes, lower axis fastest.
+void wall_lift(const Geo& g, int a, int side, const double* data, double* b, double eta, cudaStream_t s);
+// x's stored low-wall faces of component a set to the wall value (their rows
+// are the identity and nothing else couples to them)
+void wall_set_faces(const Geo& g, int a, const double* data, double* x, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // blas.cu -- vector kernels; dots reduce deterministically (fixed blocks)
@@ -202,8 +225,8 @@ struct MarkerData {
     double* rel = nullptr;      // [N][d] q - X_body (unwrapped lever arm)
     int* body = nullptr;        // [N]
     int* body_start = nullptr;  // [B+1]
-    int* base = nullptr;        // [N][d][d] first node of the 4-wide window, comp alpha, axis beta
-    double* w64 = nullptr;      // [N][d][d][4]
+    int* idx = nullptr;         // [N][d][d][4] stored node of window node m, comp alpha, axis beta
+    double* w64 = nullptr;      // [N][d][d][4] signed weights (mirror images carry -1)
     float* w32 = nullptr;       // [N][d][d][4]
     // face-major gather lists of S: faces F, entries E
     long long F = 0, E = 0;
@@ -215,7 +238,7 @@ struct MarkerData {
 };
 void markers_positions(int d, int N, const double* rbody, const int* body, const double* xc_R /*[B][12]*/,
                        const double* Lbox, double* q, double* rel, cudaStream_t s);
-void markers_weights(const Geo& g, int N, const double* q, int* base, double* w64, float* w32,
+void markers_weights(const Geo& g, int N, const double* q, int* idx, double* w64, float* w32,
                      cudaStream_t s);
 // builds the face-major gather lists (allocates md.face/off/ent_* on device)
 void markers_build_gather(const Geo& g, MarkerData& md, cudaStream_t s);

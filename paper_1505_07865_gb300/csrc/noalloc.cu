@@ -105,7 +105,7 @@ extern "C" int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, dou
         }
         int coarse_sweeps = mg_coarse_sweeps(lev[nl - 1]);
         for (int it = 0; it < k; ++it)
-            mg_vcycle<double>(lev, nl, U, Fw, f, 1, sigma, kappa, false, pre, post, coarse_sweeps, s);
+            mg_vcycle<double>(lev, nl, U, Fw, f, 1, 0, sigma, kappa, false, pre, post, coarse_sweeps, s);
         set_error("");
         return IBR_OK;
     } catch (const Error& e) {

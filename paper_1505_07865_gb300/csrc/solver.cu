@@ -60,7 +60,7 @@ double now_ms() {
 }
 
 // ---------------------------------------------------------------------------
-// geometric multigrid on periodic cell grids (scalar fields, C stacked)
+// geometric multigrid on cell grids (C stacked fields, periodic or wall axes)
 template <typename T>
 struct Multigrid {
     std::vector<Geo> lev;
@@ -104,13 +104,14 @@ struct Multigrid {
         lev.clear();
     }
     // one V-cycle for (sigma I - kappa Delta_h) u0 = f0 (C stacked fields)
-    void vcycle(T* u0, const T* f0, int C, double sigma, double kappa, bool zero_start, int pre, int post,
+    // fld0: field code of the first stacked field (velocity component, or FLD_P)
+    void vcycle(T* u0, const T* f0, int C, int fld0, double sigma, double kappa, bool zero_start, int pre, int post,
                 cudaStream_t s) {
         int L = (int)lev.size();
         std::vector<T*> U(u);
         U[0] = u0;
-        mg_vcycle<T>(lev.data(), L, U.data(), f.data(), f0, C, sigma, kappa, zero_start, pre, post, coarse_sweeps,
-                     s);
+        mg_vcycle<T>(lev.data(), L, U.data(), f.data(), f0, C, fld0, sigma, kappa, zero_start, pre, post,
+                     coarse_sweeps, s);
     }
 };
 
@@ -151,7 +152,8 @@ struct ibr_grid {
     std::vector<int> roff;
     long long* moff_dev = nullptr;
     int* roff_dev = nullptr;
-    double* Mbuild = nullptr;  // M~ as built (FP64)
+    int nblk = 0;              // dense mobility blocks (one per body, or one for all with IBR_MOB_TRUE)
+    double* Mbuild = nullptr;  // M~ (or M0) as built (FP64)
     double* Minv64 = nullptr;
     float* Minv32 = nullptr;
     int* info_dev = nullptr;
@@ -173,6 +175,16 @@ struct ibr_grid {
 
     bool steady() const { return rho == 0.0 || dt == 0.0; }
     double sigma() const { return steady() ? 0.0 : rho / dt; }
+    // walls on some axis (geo.wall != 0), and their boundary data: bc[2a + s]
+    // per side, wdata[2a + s] the velocity on that wall ([d][face points],
+    // device; zero for no-slip), wdata_host the same on the host
+    int bc[6] = {IBR_PERIODIC, IBR_PERIODIC, IBR_PERIODIC, IBR_PERIODIC, IBR_PERIODIC, IBR_PERIODIC};
+    double* wdata[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<double> wdata_host[6];
+    bool walls() const { return geo.wall != 0; }
+    // periodic steady Stokes: <v> = 0 is part of the problem and S~ = S - vol^-1 1^T
+    bool null_v() const { return steady() && !walls(); }
+    long long face_points(int a) const { return geo.ncell / n[a]; }
     int rot() const { return d == 2 ? 1 : 3; }
 };
 
@@ -285,7 +297,7 @@ struct PC {
             IBR_CUDA_TRY(cudaMemsetAsync(col, 0, sizeof(double) * dN, s));
             rigid_K_free(d, N, G->md.rel, G->md.body, G->bfree_dev, unit, col, 1.0, s);
             vec_convert<double, T>(dN, col, colT, s);
-            blockdiag_gemv<T, T>(B, G->moff_dev, G->roff_dev, (int)dN, Minv, colT, Xf + (long long)c * dN, s);
+            blockdiag_gemv<T, T>(G->nblk, G->moff_dev, G->roff_dev, (int)dN, Minv, colT, Xf + (long long)c * dN, s);
             rigid_KT_free<T>(d, B, G->md.body_start, G->bfree_dev, G->md.rel, Xf + (long long)c * dN, sU, s);
             IBR_CUDA_TRY(cudaMemcpyAsync(kt.data(), sU, sizeof(double) * G->nU, cudaMemcpyDeviceToHost, s));
             IBR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -328,9 +340,9 @@ struct PC {
         long long n = g.ncell;
         int d = G->d;
         double sigma = G->sigma();
-        mg.vcycle(y, in, d, sigma, G->eta, true, pre, post, s);                 // y = A~^-1 g
+        mg.vcycle(y, in, d, 0, sigma, G->eta, true, pre, post, s);              // y = A~^-1 g
         ps_divergence<T>(g, y, in + d * n, qr, -1.0 / (g.h * g.h), q, s);      // q = -D y - h
-        mg.vcycle(phi, qr, 1, 0.0, 1.0, true, pre, post, s);                    // phi = L~p^-1 q
+        mg.vcycle(phi, qr, 1, FLD_P, 0.0, 1.0, true, pre, post, s);             // phi = L~p^-1 q
         double cphi = G->steady() ? 0.0 : -G->rho * g.h * g.h / G->dt;
         ps_finish<T>(g, y, phi, q, out, G->eta, cphi, s);                       // v, pi
         ++ps_count;
@@ -371,7 +383,7 @@ struct PC {
         inner_gmres(rs, xs);                                                 // step 1
         if (N > 0) {
             interp<T, double>(g, G->md, xs, dU, -1.0, rL, s, -1.0);          // step 2: dU = -(J v + W)
-            blockdiag_gemv<T, T>((int)G->bodies.size(), G->moff_dev, G->roff_dev, (int)dN, Minv, dU, lamT,
+            blockdiag_gemv<T, T>(G->nblk, G->moff_dev, G->roff_dev, (int)dN, Minv, dU, lamT,
                                  s);                                        // step 3
             if (G->nfree > 0) {
                 // free bodies: [M~ -K_f; K_f^T 0][Lambda; U] = [dU; F]  ->
@@ -383,7 +395,7 @@ struct PC {
             if (variant == IBR_PC_FULL) {                                   // step 4
                 IBR_CUDA_TRY(cudaMemcpyAsync(rs2, rs, sizeof(T) * nS, cudaMemcpyDeviceToDevice, s));
                 spread_gather<T>(G->md, lamT, rs2, 1.0 / std::pow(g.h, d), s);
-                if (G->steady()) {
+                if (G->null_v()) {
                     lam_sum<T>(d, N, lamT, 1.0 / G->vol, shift, s);
                     subtract_means<T>(n, d, rs2, shift, s);
                 }
@@ -393,7 +405,7 @@ struct PC {
         // keep the Krylov vectors in the space of the constrained problem:
         // <v> = 0 (periodic steady Stokes) and <pi> = 0
         block_means<T>(n, d + 1, xs, partial, means, s);
-        if (G->steady())
+        if (G->null_v())
             subtract_means<T>(n, d + 1, xs, means, s);
         else
             subtract_means<T>(n, 1, xs + (long long)d * n, means + d, s);
@@ -489,7 +501,7 @@ void free_markers(ibr_grid* G) {
     dfree(md.rel);
     dfree(md.body);
     dfree(md.body_start);
-    dfree(md.base);
+    dfree(md.idx);
     dfree(md.w64);
     dfree(md.w32);
     dfree(md.face);
@@ -521,7 +533,7 @@ void opts_default(ibr_solve_opts* o) {
     o->tol = 1e-8;
     o->restart = 50;
     o->max_iters = 1000;
-    o->n_s = 2;
+    o->n_s = 0;  // automatic: 2 on periodic grids, 4 with walls
     o->variant = IBR_PC_LOWER;
     o->mg_pre = 2;
     o->mg_post = 2;
@@ -556,9 +568,17 @@ MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
     p.model = model;
     p.eta = G->eta;
     p.h = G->h;
+    // the length in the 2-D self-mobility: the box (periodic), or the
+    // narrowest wall-bounded extent (walls screen the logarithmic growth)
     p.l = G->L[0];
+    if (G->walls()) {
+        p.l = 1e300;
+        for (int a = 0; a < G->d; ++a)
+            if ((G->geo.wall >> a) & 1) p.l = std::min(p.l, G->L[a]);
+    }
     p.a = aoh * G->h;
-    p.corr = (model == IBR_MOB_RPY) ? 2.84 / (6.0 * M_PI * G->eta * G->L[0]) : 0.0;
+    // periodic-image correction of App. A (fully periodic boxes only)
+    p.corr = (model == IBR_MOB_RPY && !G->walls()) ? 2.84 / (6.0 * M_PI * G->eta * G->L[0]) : 0.0;
     std::memcpy(p.coef, o.mob_coef, sizeof(p.coef));
     return p;
 }
@@ -576,6 +596,79 @@ void ensure_pc(ibr_grid* G, int ns) {
         G->pc32 = new PC<float>(G, ns);
     }
     G->pc_ns = ns;
+}
+
+// The true mobility M0 = J L^-1 S (Sec. III.C: the Schur complement of the
+// constrained system) into M0 (dN x dN, row-major, symmetrised), one column
+// per marker force component: spread the unit force, solve the unconstrained
+// Stokes problem by restarted GMRES(30) with P_S in FP64 to a relative
+// residual of 1e-8, interpolate.  Returns the mean diagonal entry (the
+// self-mobility scale used by the factorisation's pivot test).
+double build_true_mobility(ibr_grid* G, double* M0) {
+    cudaStream_t s = G->stream;
+    const Geo& g = G->geo;
+    const int d = G->d, N = G->N;
+    const long long n = g.ncell, nS = G->nS, dN = (long long)N * d;
+    PC<double> pc(G, 30);
+    double* ek = dalloc<double>(dN);
+    double* rhs = dalloc<double>(nS);
+    double* x = dalloc<double>(nS);
+    double* w = dalloc<double>(nS);
+    double* dx = dalloc<double>(nS);
+    double* hs = nullptr;
+    IBR_CUDA_TRY(cudaMallocHost(&hs, 2 * sizeof(double)));
+    auto norm_sq = [&](const double* v) {
+        norm2<double>(nS, v, pc.partial, pc.sc, s);
+        IBR_CUDA_TRY(cudaMemcpyAsync(hs, pc.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        return hs[0];
+    };
+    hs[1] = 1.0;
+    const double sc = 1.0 / std::pow(g.h, d);
+    for (long long k = 0; k < dN; ++k) {
+        IBR_CUDA_TRY(cudaMemsetAsync(ek, 0, sizeof(double) * dN, s));
+        IBR_CUDA_TRY(cudaMemcpyAsync(ek + k, hs + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+        IBR_CUDA_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * nS, s));
+        spread_gather<double>(G->md, ek, rhs, sc, s);
+        if (G->null_v()) {
+            lam_sum<double>(d, N, ek, 1.0 / G->vol, pc.shift, s);
+            subtract_means<double>(n, d, rhs, pc.shift, s);
+        }
+        const double b2 = norm_sq(rhs);
+        pc.inner_gmres(rhs, x);
+        for (int pass = 1; pass < 8 && b2 > 0.0; ++pass) {
+            stokes_apply<double>(g, x, w, G->sigma(), G->eta, nullptr, s);
+            vec_axpby<double>(nS, 1.0, rhs, -1.0, w, s);  // w = rhs - L x
+            if (norm_sq(w) <= 1e-16 * b2) break;
+            pc.inner_gmres(w, dx);
+            vec_axpby<double>(nS, 1.0, dx, 1.0, x, s);
+        }
+        if (G->null_v()) {
+            block_means<double>(n, d, x, pc.partial, pc.means, s);
+            subtract_means<double>(n, d, x, pc.means, s);
+        }
+        interp<double, double>(g, G->md, x, M0 + k * dN, 1.0, nullptr, s, 0.0);
+    }
+    std::vector<double> hM((size_t)dN * dN);
+    IBR_CUDA_TRY(cudaMemcpyAsync(hM.data(), M0, hM.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    IBR_CUDA_TRY(cudaStreamSynchronize(s));
+    double diag = 0.0;
+    for (long long i = 0; i < dN; ++i) {
+        diag += hM[(size_t)i * dN + i];
+        for (long long j = i + 1; j < dN; ++j) {
+            double a = 0.5 * (hM[(size_t)i * dN + j] + hM[(size_t)j * dN + i]);
+            hM[(size_t)i * dN + j] = hM[(size_t)j * dN + i] = a;
+        }
+    }
+    IBR_CUDA_TRY(cudaMemcpyAsync(M0, hM.data(), hM.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    IBR_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFreeHost(hs);
+    dfree(ek);
+    dfree(rhs);
+    dfree(x);
+    dfree(w);
+    dfree(dx);
+    return diag / (double)dN;
 }
 
 void prepare(ibr_grid* G, const ibr_solve_opts& o) {
@@ -612,6 +705,28 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
         for (int a = 0; a < 9; ++a) xcR[bi * 12 + 3 + a] = b.R[a];
     }
     bstart[B] = N;
+    // markers on wall axes: inside the box, and outside the kernel support
+    // (2h) of walls that carry nonzero boundary data (J_0 c is not formed)
+    if (G->walls()) {
+        bool data[6];
+        for (int f = 0; f < 2 * d; ++f) {
+            data[f] = false;
+            for (double v : G->wdata_host[f]) data[f] = data[f] || v != 0.0;
+        }
+        const double tol = 1e-12 * G->h;
+        for (int i = 0; i < N; ++i) {
+            const double* P = &xcR[(size_t)body[i] * 12];
+            const double* r = &rb[(size_t)i * d];
+            for (int a = 0; a < d; ++a) {
+                if (!((G->geo.wall >> a) & 1)) continue;
+                double q = P[a];
+                for (int e = 0; e < d; ++e) q += P[3 + 3 * a + e] * r[e];
+                require(q >= -tol && q <= G->L[a] + tol, "a marker lies outside the walls");
+                require(!(data[2 * a] && q < 2.0 * G->h - tol) && !(data[2 * a + 1] && q > G->L[a] - 2.0 * G->h + tol),
+                        "a marker lies within the kernel support (2h) of a wall with nonzero boundary velocity");
+            }
+        }
+    }
     MarkerData& md = G->md;
     double* rb_dev = dalloc<double>(rb.size());
     double* xcR_dev = dalloc<double>(xcR.size());
@@ -619,52 +734,66 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     md.rel = dalloc<double>((size_t)N * d);
     md.body = dalloc<int>(N);
     md.body_start = dalloc<int>(B + 1);
-    md.base = dalloc<int>((size_t)N * d * d);
+    md.idx = dalloc<int>((size_t)N * d * d * 4);
     md.w64 = dalloc<double>((size_t)N * d * d * 4);
     md.w32 = dalloc<float>((size_t)N * d * d * 4);
     IBR_CUDA_TRY(cudaMemcpyAsync(rb_dev, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     IBR_CUDA_TRY(cudaMemcpyAsync(xcR_dev, xcR.data(), xcR.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     IBR_CUDA_TRY(cudaMemcpyAsync(md.body, body.data(), body.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     IBR_CUDA_TRY(cudaMemcpyAsync(md.body_start, bstart.data(), bstart.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    markers_positions(d, N, rb_dev, md.body, xcR_dev, G->L, md.q, md.rel, s);
-    markers_weights(G->geo, N, md.q, md.base, md.w64, md.w32, s);
+    double Lwrap[3] = {0.0, 0.0, 0.0};  // periodic axes wrap, wall axes do not
+    for (int a = 0; a < d; ++a) Lwrap[a] = ((G->geo.wall >> a) & 1) ? 0.0 : G->L[a];
+    markers_positions(d, N, rb_dev, md.body, xcR_dev, Lwrap, md.q, md.rel, s);
+    markers_weights(G->geo, N, md.q, md.idx, md.w64, md.w32, s);
     markers_build_gather(G->geo, md, s);
-    // approximate mobility, one dense block per body
-    G->moff.assign(B + 1, 0);
-    G->roff.assign(B + 1, 0);
-    for (int bi = 0; bi < B; ++bi) {
-        long long nb = (long long)G->bodies[bi].N * d;
+    // the Schur-complement approximation: the analytic M~, one dense block per
+    // body (Sec. IV, VIII), or the true mobility M0 = J L^-1 S of all markers
+    // as one block, computed from the library's own Stokes solves (Sec. V.C:
+    // worth it for fixed geometries, e.g. the steady nozzle of Sec. VII.F)
+    const bool true_mob = o.mob_model == IBR_MOB_TRUE;
+    G->nblk = true_mob ? 1 : B;
+    const int nblk = G->nblk;
+    G->moff.assign(nblk + 1, 0);
+    G->roff.assign(nblk + 1, 0);
+    for (int bi = 0; bi < nblk; ++bi) {
+        long long nb = true_mob ? (long long)N * d : (long long)G->bodies[bi].N * d;
         G->moff[bi + 1] = G->moff[bi] + nb * nb;
         G->roff[bi + 1] = G->roff[bi] + (int)nb;
     }
-    G->moff_dev = dalloc<long long>(B + 1);
-    G->roff_dev = dalloc<int>(B + 1);
-    IBR_CUDA_TRY(cudaMemcpyAsync(G->moff_dev, G->moff.data(), (B + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
-    IBR_CUDA_TRY(cudaMemcpyAsync(G->roff_dev, G->roff.data(), (B + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-    long long mtot = G->moff[B];
+    G->moff_dev = dalloc<long long>(nblk + 1);
+    G->roff_dev = dalloc<int>(nblk + 1);
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->moff_dev, G->moff.data(), (nblk + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                                 s));
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->roff_dev, G->roff.data(), (nblk + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    long long mtot = G->moff[nblk];
     G->Mbuild = dalloc<double>(mtot);
-    MobParams mp = mob_params(G, o);
-    for (int bi = 0; bi < B; ++bi)
-        mtilde_build(d, G->bodies[bi].N, md.rel + (long long)bstart[bi] * d, mp, G->Mbuild + G->moff[bi], s);
+    double fself = 0.0;
+    if (true_mob) {
+        fself = build_true_mobility(G, G->Mbuild);
+    } else {
+        MobParams mp = mob_params(G, o);
+        for (int bi = 0; bi < B; ++bi)
+            mtilde_build(d, G->bodies[bi].N, md.rel + (long long)bstart[bi] * d, mp, G->Mbuild + G->moff[bi], s);
+        fself = mob_self(mp);
+    }
     if (!G->info_dev) G->info_dev = dalloc<int>(1);
     IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, sizeof(int), s));
     // a pivot below this fraction of the self-mobility means M~ is singular
     // to working precision (e.g. coincident markers)
-    double fself = mob_self(mp);
     if (!(fself > 0.0))
         throw Error{IBR_ENUMERIC, "self-mobility f(0) of M~ is not positive (check mob_a_over_h, box size)"};
     double min_piv64 = 1e-10 * fself, min_piv32 = 1e-5 * fself;
     long long maxblk = 0;
-    for (int bi = 0; bi < B; ++bi) maxblk = std::max(maxblk, G->moff[bi + 1] - G->moff[bi]);
+    for (int bi = 0; bi < nblk; ++bi) maxblk = std::max(maxblk, G->moff[bi + 1] - G->moff[bi]);
     // Factor each block; if M~ is not positive definite (the analytic M~ need
     // not be, Sec. V.C) retry with M~ + delta I, delta growing geometrically
     // from 1e-3 f(0): the shift damps the spurious small/negative modes the way
     // the paper's eigenvalue filtering drops them.
-    G->mob_shift.assign(B, 0.0);
+    G->mob_shift.assign(nblk, 0.0);
     auto factor_all = [&](auto* Minv, auto* work, double min_piv) {
         using TT = std::remove_pointer_t<decltype(Minv)>;
-        for (int bi = 0; bi < B; ++bi) {
-            int nb = G->bodies[bi].N * d;
+        for (int bi = 0; bi < nblk; ++bi) {
+            int nb = G->roff[bi + 1] - G->roff[bi];
             double delta = 0.0;
             for (int attempt = 0;; ++attempt) {
                 mat_convert<double, TT>(G->moff[bi + 1] - G->moff[bi], G->Mbuild + G->moff[bi], Minv + G->moff[bi], s);
@@ -676,7 +805,7 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
                 IBR_CUDA_TRY(cudaStreamSynchronize(s));
                 if (info == 0) break;
                 if (attempt >= 40)
-                    throw Error{IBR_ENUMERIC, "approximate mobility M~ of body " + std::to_string(bi) +
+                    throw Error{IBR_ENUMERIC, "mobility block " + std::to_string(bi) +
                                                   " could not be made positive definite"};
                 delta = delta == 0.0 ? 1e-3 * fself : 2.0 * delta;
             }
@@ -747,7 +876,7 @@ void full_matvec(ibr_grid* G, const double* x, double* y) {
     long long nS = G->nS;
     const double* lam = x + nS;
     const double* shift = nullptr;
-    if (G->steady() && G->N > 0) {
+    if (G->null_v() && G->N > 0) {
         lam_sum<double>(d, G->N, lam, 1.0 / G->vol, G->shift, s);  // -S~ = -S + vol^-1 1^T
         shift = G->shift;
     }
@@ -784,7 +913,7 @@ void project_solution(ibr_grid* G, double* x) {
     long long n = G->geo.ncell;
     int d = G->d;
     block_means<double>(n, d + 1, x, G->partial, G->means, s);
-    if (G->steady())
+    if (G->null_v())
         subtract_means<double>(n, d + 1, x, G->means, s);
     else
         subtract_means<double>(n, 1, x + (long long)d * n, G->means + d, s);
@@ -928,11 +1057,17 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
         *out = nullptr;
         require(dim == 2 || dim == 3, "dim must be 2 or 3");
         require(n && L && bc, "n, L, bc must be non-NULL");
+        int wall = 0;
         for (int a = 0; a < dim; ++a) {
             require(n[a] >= 4 && n[a] % 2 == 0, "each n[a] must be even and >= 4");
             require(L[a] > 0, "L[a] must be positive");
-            require(bc[2 * a] == IBR_PERIODIC && bc[2 * a + 1] == IBR_PERIODIC,
-                    "this build supports periodic boundaries only");
+            auto is_wall = [](int b) { return b == IBR_NOSLIP || b == IBR_VELOCITY; };
+            const bool per = bc[2 * a] == IBR_PERIODIC && bc[2 * a + 1] == IBR_PERIODIC;
+            const bool wl = is_wall(bc[2 * a]) && is_wall(bc[2 * a + 1]);
+            require(per || wl,
+                    "each axis must be periodic at both ends or bounded by walls (IBR_NOSLIP / IBR_VELOCITY) at both "
+                    "ends");
+            if (wl) wall |= 1 << a;
         }
         double h = L[0] / n[0];
         for (int a = 1; a < dim; ++a)
@@ -955,6 +1090,7 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
         for (int a = 0; a < dim; ++a) G->vol *= L[a];
         G->precision = precision;
         G->geo = make_geo(dim, n, h);
+        G->geo.wall = wall;
         require(G->geo.ncell < (1LL << 31), "a field must have fewer than 2^31 cells");
         G->nS = (long long)(dim + 1) * G->geo.ncell;
         G->len = G->nS;
@@ -975,6 +1111,18 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
             // a blocking stream: ordered with work on the legacy default stream
             IBR_CUDA_TRY(cudaStreamCreateWithFlags(&G->stream, cudaStreamDefault));
             G->own_stream = true;
+        }
+        // wall data, zero until ibr_set_boundary_velocity
+        for (int a = 0; a < dim; ++a) {
+            if (!((wall >> a) & 1)) continue;
+            for (int sd = 0; sd < 2; ++sd) {
+                const int f = 2 * a + sd;
+                G->bc[f] = bc[f];
+                const size_t cnt = (size_t)dim * G->face_points(a);
+                G->wdata_host[f].assign(cnt, 0.0);
+                G->wdata[f] = dalloc<double>(cnt);
+                IBR_CUDA_TRY(cudaMemsetAsync(G->wdata[f], 0, cnt * sizeof(double), G->stream));
+            }
         }
         opts_default(&G->prepared_opts);
         *out = G.release();
@@ -1012,11 +1160,18 @@ int ibr_set_markers(ibr_grid* G, int body_id, const double* r_body, int N) {
 }
 
 int ibr_set_boundary_velocity(ibr_grid* G, int face, const double* values) {
-    (void)face;
-    (void)values;
     return run_guarded("ibr_set_boundary_velocity", [&] {
-        require(G != nullptr, "grid is NULL");
-        throw Error{IBR_EINVAL, "this build supports periodic boundaries only"};
+        require(G != nullptr && values != nullptr, "grid and values must be non-NULL");
+        require(face >= 0 && face < 2 * G->d, "face must be in [0, 2*dim)");
+        require(G->bc[face] == IBR_VELOCITY, "face is not an IBR_VELOCITY wall");
+        const size_t cnt = (size_t)G->d * G->face_points(face / 2);
+        for (size_t i = 0; i < cnt; ++i)
+            if (!std::isfinite(values[i])) throw Error{IBR_ENUMERIC, "boundary values contain NaN/Inf"};
+        G->wdata_host[face].assign(values, values + cnt);
+        IBR_CUDA_TRY(cudaMemcpyAsync(G->wdata[face], G->wdata_host[face].data(), cnt * sizeof(double),
+                                     cudaMemcpyHostToDevice, G->stream));
+        G->dirty = true;  // the marker check against walls with data runs in the set-up
+        G->have_solution = false;
     });
 }
 
@@ -1046,7 +1201,11 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
             opts_default(&o);
         require(o.tol > 0 && o.tol < 1, "tol must be in (0,1)");
         require(o.restart >= 1 && o.restart <= 120, "restart must be in [1,120]");
-        require(o.n_s >= 1 && o.n_s <= 16, "n_s must be in [1,16]");
+        require(o.n_s >= 0 && o.n_s <= 16, "n_s must be in [0,16]");
+        // N_s = 2 for periodic problems (Sec. VII.A); near no-slip walls the
+        // projection preconditioner is further from the Stokes inverse and
+        // N_s = 4 is the robust choice (Sec. VII.A)
+        if (o.n_s == 0) o.n_s = G->walls() ? 4 : 2;
         require(o.max_iters >= 1, "max_iters must be >= 1");
         require(o.variant == IBR_PC_LOWER || o.variant == IBR_PC_FULL, "bad variant");
         require(o.mg_pre >= 0 && o.mg_post >= 0 && o.mg_pre + o.mg_post >= 1, "bad mg sweeps");
@@ -1079,6 +1238,24 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
                                          g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         }
         rigid_K(G->d, G->N, G->md.rel, G->md.body, G->UO, G->b + nS, -1.0, s);
+        if (G->walls()) {
+            // no net flux through the walls (solvability of the divergence rows)
+            double flux = 0.0, scale = 0.0;
+            for (int a = 0; a < G->d; ++a) {
+                if (!((G->geo.wall >> a) & 1)) continue;
+                const long long nf = G->face_points(a);
+                const double* lo = G->wdata_host[2 * a].data() + (size_t)a * nf;
+                const double* hi = G->wdata_host[2 * a + 1].data() + (size_t)a * nf;
+                for (long long t = 0; t < nf; ++t) {
+                    flux += hi[t] - lo[t];
+                    scale += std::fabs(hi[t]) + std::fabs(lo[t]);
+                }
+            }
+            require(std::fabs(flux) <= 1e-10 * scale, "the wall velocities have a net flux (inflow != outflow)");
+            for (int a = 0; a < G->d; ++a)
+                if ((G->geo.wall >> a) & 1)
+                    for (int sd = 0; sd < 2; ++sd) wall_lift(G->geo, a, sd, G->wdata[2 * a + sd], G->b, G->eta, s);
+        }
         if (G->nfree > 0)
             IBR_CUDA_TRY(cudaMemcpyAsync(G->b + nS + (long long)G->N * G->d, load.data(),
                                          load.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1099,6 +1276,9 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
             G->pc32->setup_free();
         }
         status = fgmres(G, o, info);
+        if (G->walls())
+            for (int a = 0; a < G->d; ++a)
+                if ((G->geo.wall >> a) & 1) wall_set_faces(G->geo, a, G->wdata[2 * a], G->x, s);
         IBR_CUDA_TRY(cudaStreamSynchronize(s));
         double t2 = now_ms();
         info.ms_setup = t1 - t0;
@@ -1200,7 +1380,7 @@ int ibr_op_spread(ibr_grid* G, const double* lam, double* f) {
         long long n = G->geo.ncell;
         IBR_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(double) * G->d * n, s));
         spread_gather<double>(G->md, lam, f, 1.0 / std::pow(G->h, G->d), s);
-        if (G->steady()) {
+        if (G->null_v()) {
             if (!G->shift) G->shift = dalloc<double>(4);
             lam_sum<double>(G->d, G->N, lam, 1.0 / G->vol, G->shift, s);
             subtract_means<double>(n, G->d, f, G->shift, s);
@@ -1235,7 +1415,7 @@ int ibr_op_rigid_T(ibr_grid* G, const double* lam, double* FT) {
 int ibr_op_mtilde(ibr_grid* G, int body, double* out) {
     return run_guarded("ibr_op_mtilde", [&] {
         need_prepared(G);
-        require(body >= 0 && body < (int)G->bodies.size(), "bad body");
+        require(body >= 0 && body < G->nblk, "bad mobility block");
         require(out, "out must be non-NULL");
         long long cnt = G->moff[body + 1] - G->moff[body];
         IBR_CUDA_TRY(cudaMemcpyAsync(out, G->Mbuild + G->moff[body], cnt * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1248,16 +1428,15 @@ int ibr_op_mtilde_solve(ibr_grid* G, const double* rhs, double* out) {
         need_prepared(G);
         require(rhs && out, "rhs, out must be non-NULL");
         cudaStream_t s = G->stream;
-        int B = (int)G->bodies.size();
         int dN = G->N * G->d;
         if (G->precision == IBR_FP64) {
-            blockdiag_gemv<double, double>(B, G->moff_dev, G->roff_dev, dN, G->Minv64, rhs, out, s);
+            blockdiag_gemv<double, double>(G->nblk, G->moff_dev, G->roff_dev, dN, G->Minv64, rhs, out, s);
         } else {
             ensure_pc(G, std::max(G->pc_ns, 1));
             float* tin = G->pc32->dU;
             float* tout = G->pc32->lamT;
             vec_convert<double, float>(dN, rhs, tin, s);
-            blockdiag_gemv<float, float>(B, G->moff_dev, G->roff_dev, dN, G->Minv32, tin, tout, s);
+            blockdiag_gemv<float, float>(G->nblk, G->moff_dev, G->roff_dev, dN, G->Minv32, tin, tout, s);
             vec_convert<float, double>(dN, tout, out, s);
         }
     });
@@ -1288,12 +1467,12 @@ int ibr_op_vcycle(ibr_grid* G, double sigma, double kappa, const double* f, doub
         ensure_pc(G, std::max(G->pc_ns, 1));
         if (G->precision == IBR_FP64) {
             auto* pc = G->pc64;
-            for (int i = 0; i < k; ++i) pc->mg.vcycle(u, f, 1, sigma, kappa, false, pc->pre, pc->post, s);
+            for (int i = 0; i < k; ++i) pc->mg.vcycle(u, f, 1, FLD_P, sigma, kappa, false, pc->pre, pc->post, s);
         } else {
             auto* pc = G->pc32;
             vec_convert<double, float>(n, f, pc->rs, s);
             vec_convert<double, float>(n, u, pc->xs, s);
-            for (int i = 0; i < k; ++i) pc->mg.vcycle(pc->xs, pc->rs, 1, sigma, kappa, false, pc->pre, pc->post, s);
+            for (int i = 0; i < k; ++i) pc->mg.vcycle(pc->xs, pc->rs, 1, FLD_P, sigma, kappa, false, pc->pre, pc->post, s);
             vec_convert<float, double>(n, pc->xs, u, s);
         }
     });
@@ -1309,6 +1488,7 @@ int ibr_destroy_grid(ibr_grid* G) {
         free_outer(G);
         dfree(G->info_dev);
         if (G->host_sc) cudaFreeHost(G->host_sc);
+        for (double* p : G->wdata) dfree(p);
         if (G->own_stream) cudaStreamDestroy(G->stream);
         delete G;
     });

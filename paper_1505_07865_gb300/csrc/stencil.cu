@@ -1,8 +1,17 @@
 // MAC-grid operators and the geometric multigrid pieces of P_S (Sec. V.B).
 //
 // Layout: a scalar field is ncell values, x fastest; a stack of C fields is
-// C*ncell values.  A Stokes vector is [v_0 .. v_{d-1} | p].  All grids here
-// are periodic with an even number of cells per axis (red-black ordering).
+// C*ncell values.  A Stokes vector is [v_0 .. v_{d-1} | p].  Every axis has an
+// even number of cells (red-black ordering).  An axis is periodic, or bounded
+// by walls (App. D).  Beyond a wall a field is extended by linear
+// extrapolation through the wall value; for the homogeneous operators here:
+//   velocity tangential to the wall (cell-centred along the axis): ghost = -u
+//   pressure: ghost = +u (homogeneous Neumann)
+//   normal velocity: faces 0..n, face 0 stored as a boundary entry (identity
+//   row), face n not stored; both wall faces add nothing to their neighbours.
+// The kernels are templated on W (some axis has walls); the W = false
+// instances are the plain wrapped stencils.  Boundary data enters only the
+// right-hand side (wall_lift).
 #include "ibr_internal.cuh"
 
 namespace ibr {
@@ -43,13 +52,78 @@ __device__ __forceinline__ T nbr_sum(const T* __restrict__ u, const Nbr& n) {
     return s;
 }
 
-// y_v^a = sigma v^a - kh2 (nbrsum - 2D v^a) + (p_c - p_{c-e_a}) ih + shift_a ;
-// y_p = -ih sum_a (v^a_{c+e_a} - v^a_c)
+// Boundary rule of field fld at cell (i, j, k) on the wall axes.
+// ok bit 2a (2a+1): the low (high) neighbour along a is an unknown of the
+// stencil; adj: change of the Laplacian's diagonal from mirror ghosts (-1 per
+// Dirichlet side, +1 per Neumann side); ident: a stored wall face.
+struct WInfo {
+    unsigned ok;
+    int adj;
+    bool ident;
+};
+
+template <int D>
+__device__ __forceinline__ WInfo wall_info(const Geo& g, int fld, int i, int j, int k) {
+    WInfo w;
+    w.ok = 0x3Fu;
+    w.adj = 0;
+    w.ident = false;
+    const int id[3] = {i, j, k};
+    const int ns[3] = {g.n0, g.n1, g.n2};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (!((g.wall >> a) & 1)) continue;
+        const int x = id[a], n = ns[a];
+        if (fld == a) {
+            if (x == 0) w.ident = true;
+            if (x <= 1) w.ok &= ~(1u << (2 * a));
+            if (x == n - 1) w.ok &= ~(2u << (2 * a));
+        } else {
+            const int sgn = fld == FLD_P ? 1 : -1;
+            if (x == 0) {
+                w.ok &= ~(1u << (2 * a));
+                w.adj += sgn;
+            }
+            if (x == n - 1) {
+                w.ok &= ~(2u << (2 * a));
+                w.adj += sgn;
+            }
+        }
+    }
+    return w;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T nbr_sum_w(const T* __restrict__ u, const Nbr& n, unsigned ok) {
+    T s = T(0);
+    if (ok & 1u) s += u[n.c + n.xm];
+    if (ok & 2u) s += u[n.c + n.xp];
+    if (ok & 4u) s += u[n.c + n.ym];
+    if (ok & 8u) s += u[n.c + n.yp];
+    if (D == 3) {
+        if (ok & 16u) s += u[n.c + n.zm];
+        if (ok & 32u) s += u[n.c + n.zp];
+    }
+    return s;
+}
+
+// field code of the cmp-th stacked field
+__device__ __forceinline__ int field_of(int fld0, int cmp) { return fld0 == FLD_P ? FLD_P : fld0 + cmp; }
+
+// the operator of field fld has the constants as null space: sigma == 0 and
+// no Dirichlet rule on any axis (the pressure, or a fully periodic grid)
+__device__ __forceinline__ bool singular_field(const Geo& g, int fld, double sigma) {
+    return sigma == 0.0 && (g.wall == 0 || fld == FLD_P);
+}
+
+// y_v^a = sigma v^a - kh2 Lap v^a + (p_c - p_{c-e_a}) ih + shift_a ;
+// y_p = -ih sum_a (v^a_{c+e_a} - v^a_c)   (walls: wall faces add nothing,
+// wall-face rows are the identity)
 // Launch shape of the grid kernels: blocks of 32 x 8 threads over (x, y),
 // gridDim.z = n2 * (number of stacked fields); no 64-bit index division.
 constexpr int BX = 32, BY = 8;
 
-template <int D, typename T>
+template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __restrict__ y, Geo g, T sigma, T kh2,
                                                 T ih, const double* __restrict__ shift) {
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
@@ -60,15 +134,32 @@ __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __re
     T div = T(0);
     const int pm[3] = {n.xm, n.ym, n.zm};
     const int pp[3] = {n.xp, n.yp, n.zp};
+    const int id[3] = {i, j, k};
+    const int ns[3] = {g.n0, g.n1, g.n2};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T* u = x + a * g.ncell;
         T uc = u[n.c];
-        T lap = nbr_sum<D, T>(u, n) - T(2 * D) * uc;
-        T val = sigma * uc - kh2 * lap + (pc - p[n.c + pm[a]]) * ih;
+        T val;
+        if (!W) {
+            T lap = nbr_sum<D, T>(u, n) - T(2 * D) * uc;
+            val = sigma * uc - kh2 * lap + (pc - p[n.c + pm[a]]) * ih;
+            div += u[n.c + pp[a]] - uc;
+        } else {
+            WInfo wi = wall_info<D>(g, a, i, j, k);
+            if (wi.ident) {
+                val = uc;
+            } else {
+                T lap = nbr_sum_w<D, T>(u, n, wi.ok) + T(wi.adj - 2 * D) * uc;
+                val = sigma * uc - kh2 * lap + (pc - p[n.c + pm[a]]) * ih;
+            }
+            const bool wa = (g.wall >> a) & 1;
+            T hi = (wa && id[a] == ns[a] - 1) ? T(0) : u[n.c + pp[a]];
+            T lo = (wa && id[a] == 0) ? T(0) : uc;
+            div += hi - lo;
+        }
         if (shift) val += (T)shift[a];
         y[a * g.ncell + n.c] = val;
-        div += u[n.c + pp[a]] - uc;
     }
     y[D * g.ncell + n.c] = -div * ih;
 }
@@ -76,7 +167,6 @@ __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __re
 // ---- point operators shared by the per-level kernels and the one-CTA tail ----
 // (same arithmetic, so a level gives the same result on either path)
 
-// red-black Gauss-Seidel update of cell (i, j, k)
 // inv_diag = 1 / (sigma + 2D kh2), formed by rbgs_inv_diag on host or device
 template <int D, typename T>
 __host__ __device__ __forceinline__ T rbgs_inv_diag(T sigma, T kh2) {
@@ -84,87 +174,206 @@ __host__ __device__ __forceinline__ T rbgs_inv_diag(T sigma, T kh2) {
     return T(1) / diag;
 }
 
-template <int D, typename T>
-__device__ __forceinline__ void rbgs_cell(T* u, const T* f, const Geo& g, T kh2, T inv_diag, int zero_init, int i,
-                                          int j, int k) {
+// red-black Gauss-Seidel update of cell (i, j, k) of field fld
+template <int D, bool W, typename T>
+__device__ __forceinline__ void rbgs_cell(T* u, const T* f, const Geo& g, int fld, T sigma, T kh2, T inv_diag,
+                                          int zero_init, int i, int j, int k) {
     Nbr n = neighbours<D>(g, i, j, k);
-    T nb = zero_init ? T(0) : nbr_sum<D, T>(u, n);
-    u[n.c] = (f[n.c] + kh2 * nb) * inv_diag;
+    if (!W) {
+        T nb = zero_init ? T(0) : nbr_sum<D, T>(u, n);
+        u[n.c] = (f[n.c] + kh2 * nb) * inv_diag;
+    } else {
+        WInfo wi = wall_info<D>(g, fld, i, j, k);
+        if (wi.ident) {
+            u[n.c] = f[n.c];
+            return;
+        }
+        T nb = zero_init ? T(0) : nbr_sum_w<D, T>(u, n, wi.ok);
+        T dinv = wi.adj == 0 ? inv_diag : T(1) / (sigma + kh2 * T(2 * D - wi.adj));
+        u[n.c] = (f[n.c] + kh2 * nb) * dinv;
+    }
 }
 
 // the same for the t-th cell of the given colour (x index ih = t mod n0/2)
-template <int D, typename T>
-__device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, T sigma, T kh2, int color, int zero_init,
-                                           long long t) {
+template <int D, bool W, typename T>
+__device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, int fld, T sigma, T kh2, int color,
+                                           int zero_init, long long t) {
     int hn0 = g.n0 >> 1;
     int ih = (int)(t % hn0);
     long long r = t / hn0;
     int j = (int)(r % g.n1);
     int k = (int)(r / g.n1);
-    rbgs_cell<D, T>(u, f, g, kh2, rbgs_inv_diag<D, T>(sigma, kh2), zero_init, 2 * ih + ((j + k + color) & 1), j, k);
+    rbgs_cell<D, W, T>(u, f, g, fld, sigma, kh2, rbgs_inv_diag<D, T>(sigma, kh2), zero_init,
+                       2 * ih + ((j + k + color) & 1), j, k);
 }
 
-// coarse cell (I, J, K): average over its 2^D children of f - (sigma u - kh2 Lap u)
-template <int D, typename T>
-__device__ __forceinline__ T restrict_cell(const T* u, const T* f, const Geo& gf, T sigma, T kh2, int I, int J, int K) {
-    T acc = T(0);
+// residual f - (sigma u - kh2 Lap u) at fine cell (i, j, k)
+template <int D, bool W, typename T>
+__device__ __forceinline__ T resid_cell(const T* u, const T* f, const Geo& g, int fld, T sigma, T kh2, int i, int j,
+                                        int k) {
+    Nbr n = neighbours<D>(g, i, j, k);
+    T uc = u[n.c];
+    if (!W) return f[n.c] - (sigma * uc - kh2 * (nbr_sum<D, T>(u, n) - T(2 * D) * uc));
+    WInfo wi = wall_info<D>(g, fld, i, j, k);
+    if (wi.ident) return f[n.c] - uc;
+    return f[n.c] - (sigma * uc - kh2 * (nbr_sum_w<D, T>(u, n, wi.ok) + T(wi.adj - 2 * D) * uc));
+}
+
+// coarse cell (I, J, K): average over its 2^D children of the residual; the
+// normal component on its own wall axis is vertex-centred there: full
+// weighting (1/4, 1/2, 1/4) of the fine faces 2I-1, 2I, 2I+1, and zero on the
+// coarse wall face I = 0
+template <int D, bool W, typename T>
+__device__ __forceinline__ T restrict_cell(const T* u, const T* f, const Geo& gf, int fld, T sigma, T kh2, int I,
+                                           int J, int K) {
+    if (!W) {
+        T acc = T(0);
 #pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-        int i = 2 * I + (c & 1);
-        int j = 2 * J + ((c >> 1) & 1);
-        int k = D == 3 ? 2 * K + ((c >> 2) & 1) : 0;
-        Nbr n = neighbours<D>(gf, i, j, k);
-        T uc = u[n.c];
-        T res = f[n.c] - (sigma * uc - kh2 * (nbr_sum<D, T>(u, n) - T(2 * D) * uc));
-        acc += res;
+        for (int c = 0; c < (1 << D); ++c) {
+            int i = 2 * I + (c & 1);
+            int j = 2 * J + ((c >> 1) & 1);
+            int k = D == 3 ? 2 * K + ((c >> 2) & 1) : 0;
+            acc += resid_cell<D, false, T>(u, f, gf, fld, sigma, kh2, i, j, k);
+        }
+        return acc * (T(1) / T(1 << D));
     }
-    return acc * (T(1) / T(1 << D));
+    const int Xc[3] = {I, J, K};
+    int fi[3][3];
+    T fw[3][3];
+    int cnt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= D) {
+            cnt[a] = 1;
+            fi[a][0] = 0;
+            fw[a][0] = T(1);
+        } else if (((gf.wall >> a) & 1) && fld == a) {
+            if (Xc[a] == 0) return T(0);
+            cnt[a] = 3;
+            fi[a][0] = 2 * Xc[a] - 1;
+            fi[a][1] = 2 * Xc[a];
+            fi[a][2] = 2 * Xc[a] + 1;
+            fw[a][0] = T(0.25);
+            fw[a][1] = T(0.5);
+            fw[a][2] = T(0.25);
+        } else {
+            cnt[a] = 2;
+            fi[a][0] = 2 * Xc[a];
+            fi[a][1] = 2 * Xc[a] + 1;
+            fw[a][0] = fw[a][1] = T(0.5);
+        }
+    }
+    T acc = T(0);
+    for (int p = 0; p < cnt[0]; ++p)
+        for (int q = 0; q < cnt[1]; ++q)
+            for (int r = 0; r < cnt[2]; ++r)
+                acc += fw[0][p] * fw[1][q] * fw[2][r] *
+                       resid_cell<D, true, T>(u, f, gf, fld, sigma, kh2, fi[0][p], fi[1][q], fi[2][r]);
+    return acc;
 }
 
-template <int D, typename T>
-__device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& gf, const Geo& gc, T sigma, T kh2,
-                                            long long t) {
+template <int D, bool W, typename T>
+__device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& gf, const Geo& gc, int fld, T sigma,
+                                            T kh2, long long t) {
     int I = (int)(t % gc.n0);
     long long r = t / gc.n0;
     int J = (int)(r % gc.n1);
     int K = (int)(r / gc.n1);
-    return restrict_cell<D, T>(u, f, gf, sigma, kh2, I, J, K);
+    return restrict_cell<D, W, T>(u, f, gf, fld, sigma, kh2, I, J, K);
 }
 
 // fine cell (i, j, k): cell-centred (bi/tri)linear interpolation of the coarse
-// correction, weights 3/4 (parent) and 1/4 (the neighbour on the child's side)
-template <int D, typename T>
-__device__ __forceinline__ T prolong_cell(const T* cc, const Geo& gc, int i, int j, int k) {
-    int I[2], Jc[2], Kc[2];
-    I[0] = i >> 1;
-    I[1] = (i & 1) ? (I[0] + 1 == gc.n0 ? 0 : I[0] + 1) : (I[0] == 0 ? gc.n0 - 1 : I[0] - 1);
-    Jc[0] = j >> 1;
-    Jc[1] = (j & 1) ? (Jc[0] + 1 == gc.n1 ? 0 : Jc[0] + 1) : (Jc[0] == 0 ? gc.n1 - 1 : Jc[0] - 1);
-    if (D == 3) {
-        Kc[0] = k >> 1;
-        Kc[1] = (k & 1) ? (Kc[0] + 1 == gc.n2 ? 0 : Kc[0] + 1) : (Kc[0] == 0 ? gc.n2 - 1 : Kc[0] - 1);
-    } else {
-        Kc[0] = Kc[1] = 0;
-    }
-    const T w[2] = {T(0.75), T(0.25)};
-    T acc = T(0);
+// correction, weights 3/4 (parent) and 1/4 (the neighbour on the child's
+// side; beyond a wall the mirror ghost of the parent, -/+ for Dirichlet /
+// Neumann).  The normal component on its own wall axis: injection at even
+// faces, the mean of the two coarse faces at odd ones, wall faces zero.
+template <int D, bool W, typename T>
+__device__ __forceinline__ T prolong_cell(const T* cc, const Geo& gc, int fld, int i, int j, int k) {
+    if (!W) {
+        int I[2], Jc[2], Kc[2];
+        I[0] = i >> 1;
+        I[1] = (i & 1) ? (I[0] + 1 == gc.n0 ? 0 : I[0] + 1) : (I[0] == 0 ? gc.n0 - 1 : I[0] - 1);
+        Jc[0] = j >> 1;
+        Jc[1] = (j & 1) ? (Jc[0] + 1 == gc.n1 ? 0 : Jc[0] + 1) : (Jc[0] == 0 ? gc.n1 - 1 : Jc[0] - 1);
+        if (D == 3) {
+            Kc[0] = k >> 1;
+            Kc[1] = (k & 1) ? (Kc[0] + 1 == gc.n2 ? 0 : Kc[0] + 1) : (Kc[0] == 0 ? gc.n2 - 1 : Kc[0] - 1);
+        } else {
+            Kc[0] = Kc[1] = 0;
+        }
+        const T w[2] = {T(0.75), T(0.25)};
+        T acc = T(0);
 #pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-        int a = c & 1, b = (c >> 1) & 1, e = D == 3 ? (c >> 2) & 1 : 0;
-        T ww = w[a] * w[b] * (D == 3 ? w[e] : T(1));
-        int idx = I[a] + gc.n0 * (Jc[b] + gc.n1 * Kc[e]);
-        acc += ww * cc[idx];
+        for (int c = 0; c < (1 << D); ++c) {
+            int a = c & 1, b = (c >> 1) & 1, e = D == 3 ? (c >> 2) & 1 : 0;
+            T ww = w[a] * w[b] * (D == 3 ? w[e] : T(1));
+            int idx = I[a] + gc.n0 * (Jc[b] + gc.n1 * Kc[e]);
+            acc += ww * cc[idx];
+        }
+        return acc;
     }
+    const int id[3] = {i, j, k};
+    const int nc[3] = {gc.n0, gc.n1, gc.n2};
+    int ci[3][2];
+    T cw[3][2];
+    int cnt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= D) {
+            cnt[a] = 1;
+            ci[a][0] = 0;
+            cw[a][0] = T(1);
+            continue;
+        }
+        const int x = id[a], X = x >> 1;
+        const bool wa = (gc.wall >> a) & 1;
+        if (!wa) {
+            cnt[a] = 2;
+            ci[a][0] = X;
+            cw[a][0] = T(0.75);
+            ci[a][1] = (x & 1) ? (X + 1 == nc[a] ? 0 : X + 1) : (X == 0 ? nc[a] - 1 : X - 1);
+            cw[a][1] = T(0.25);
+        } else if (fld == a) {
+            if ((x & 1) == 0) {
+                cnt[a] = 1;
+                ci[a][0] = X;
+                cw[a][0] = X == 0 ? T(0) : T(1);
+            } else {
+                cnt[a] = 2;
+                ci[a][0] = X;
+                cw[a][0] = X == 0 ? T(0) : T(0.5);
+                ci[a][1] = X + 1 == nc[a] ? 0 : X + 1;
+                cw[a][1] = X + 1 == nc[a] ? T(0) : T(0.5);
+            }
+        } else {
+            cnt[a] = 2;
+            ci[a][0] = X;
+            cw[a][0] = T(0.75);
+            const int nb = (x & 1) ? X + 1 : X - 1;
+            if (nb < 0 || nb >= nc[a]) {
+                ci[a][1] = X;
+                cw[a][1] = fld == FLD_P ? T(0.25) : T(-0.25);
+            } else {
+                ci[a][1] = nb;
+                cw[a][1] = T(0.25);
+            }
+        }
+    }
+    T acc = T(0);
+    for (int p = 0; p < cnt[0]; ++p)
+        for (int q = 0; q < cnt[1]; ++q)
+            for (int r = 0; r < cnt[2]; ++r)
+                acc += cw[0][p] * cw[1][q] * cw[2][r] * cc[ci[0][p] + gc.n0 * (ci[1][q] + gc.n1 * ci[2][r])];
     return acc;
 }
 
-template <int D, typename T>
-__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, long long t) {
+template <int D, bool W, typename T>
+__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, int fld, long long t) {
     int i = (int)(t % gf.n0);
     long long r = t / gf.n0;
     int j = (int)(r % gf.n1);
     int k = (int)(r / gf.n1);
-    return prolong_cell<D, T>(cc, gc, i, j, k);
+    return prolong_cell<D, W, T>(cc, gc, fld, i, j, k);
 }
 
 // block-wide mean of a[0..n) (all threads get it); red: 32 doubles of shared memory
@@ -188,13 +397,14 @@ __device__ double block_mean(const T* a, long long n, double* red) {
     return m;
 }
 
-// coarsest-level solve in shared memory: f (in sf, modified) made mean-free if
-// sigma == 0, u (su) from zero by red-black sweeps, then made mean-free if
-// sigma == 0
-template <int D, typename T>
-__device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int sweeps, double* red) {
+// coarsest-level solve in shared memory: for a singular field f (in sf,
+// modified) is made mean-free, u (su) from zero by red-black sweeps, then made
+// mean-free
+template <int D, bool W, typename T>
+__device__ void coarse_block(T* su, T* sf, const Geo& g, int fld, T sigma, T kh2, int sweeps, double* red) {
     int tid = threadIdx.x, nt = blockDim.x;
-    T fmean = sigma == T(0) ? (T)block_mean(sf, g.ncell, red) : T(0);
+    const bool sing = singular_field(g, fld, (double)sigma);
+    T fmean = sing ? (T)block_mean(sf, g.ncell, red) : T(0);
     for (long long c = tid; c < g.ncell; c += nt) {
         sf[c] -= fmean;
         su[c] = T(0);
@@ -209,51 +419,54 @@ __device__ void coarse_block(T* su, T* sf, const Geo& g, T sigma, T kh2, int swe
                 int j = (int)(r % g.n1);
                 int k = (int)(r / g.n1);
                 if (((i + j + k) & 1) != color) continue;
-                Nbr n = neighbours<D>(g, i, j, k);
-                su[c] = (sf[c] + kh2 * nbr_sum<D, T>(su, n)) * inv;
+                rbgs_cell<D, W, T>(su, sf, g, fld, sigma, kh2, inv, 0, i, j, k);
             }
             __syncthreads();
         }
     }
-    T umean = sigma == T(0) ? (T)block_mean(su, g.ncell, red) : T(0);
+    T umean = sing ? (T)block_mean(su, g.ncell, red) : T(0);
     for (long long c = tid; c < g.ncell; c += nt) su[c] -= umean;
     __syncthreads();
 }
 
-// red-black Gauss-Seidel half sweep on C stacked fields (component = blockIdx.y)
-template <int D, typename T>
-__global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, T kh2, T inv_diag,
-                                              int color, int zero_init) {
+// red-black Gauss-Seidel half sweep on C stacked fields (component from blockIdx.z)
+template <int D, bool W, typename T>
+__global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, int fld0, T sigma,
+                                              T kh2, T inv_diag, int color, int zero_init) {
     int ih = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     int k = blockIdx.z % g.n2, cmp = blockIdx.z / g.n2;
     if (ih >= (g.n0 >> 1) || j >= g.n1) return;
     long long off = (long long)cmp * g.ncell;
-    rbgs_cell<D, T>(u + off, f + off, g, kh2, inv_diag, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
+    rbgs_cell<D, W, T>(u + off, f + off, g, field_of(fld0, cmp), sigma, kh2, inv_diag, zero_init,
+                       2 * ih + ((j + k + color) & 1), j, k);
 }
 
-template <int D, typename T>
+template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
-                                                        T* __restrict__ fc, Geo gf, Geo gc, T sigma, T kh2) {
+                                                        T* __restrict__ fc, Geo gf, Geo gc, int fld0, T sigma,
+                                                        T kh2) {
     int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
     int K = blockIdx.z % gc.n2, cmp = blockIdx.z / gc.n2;
     if (I >= gc.n0 || J >= gc.n1) return;
     long long t = I + (long long)gc.n0 * (J + (long long)gc.n1 * K);
-    fc[cmp * gc.ncell + t] = restrict_cell<D, T>(u + cmp * gf.ncell, f + cmp * gf.ncell, gf, sigma, kh2, I, J, K);
+    fc[cmp * gc.ncell + t] = restrict_cell<D, W, T>(u + cmp * gf.ncell, f + cmp * gf.ncell, gf,
+                                                    field_of(fld0, cmp), sigma, kh2, I, J, K);
 }
 
-template <int D, typename T>
-__global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __restrict__ uc, Geo gf, Geo gc) {
+template <int D, bool W, typename T>
+__global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __restrict__ uc, Geo gf, Geo gc,
+                                                 int fld0) {
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     int k = blockIdx.z % gf.n2, cmp = blockIdx.z / gf.n2;
     if (i >= gf.n0 || j >= gf.n1) return;
     long long t = i + (long long)gf.n0 * (j + (long long)gf.n1 * k);
-    u[cmp * gf.ncell + t] += prolong_cell<D, T>(uc + cmp * gc.ncell, gc, i, j, k);
+    u[cmp * gf.ncell + t] += prolong_cell<D, W, T>(uc + cmp * gc.ncell, gc, field_of(fld0, cmp), i, j, k);
 }
 
 // single-CTA coarse solve of the coarsest level (one CTA per field)
-template <int D, typename T>
-__global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __restrict__ f, Geo g, T sigma, T kh2,
-                                                 int sweeps) {
+template <int D, bool W, typename T>
+__global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __restrict__ f, Geo g, int fld0,
+                                                 T sigma, T kh2, int sweeps) {
     extern __shared__ unsigned char smem_raw[];
     T* su = reinterpret_cast<T*>(smem_raw);
     T* sf = su + g.ncell;
@@ -263,7 +476,7 @@ __global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __r
     T* uu = u + cmp * g.ncell;
     for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) sf[c] = ff[c];
     __syncthreads();
-    coarse_block<D, T>(su, sf, g, sigma, kh2, sweeps, red);
+    coarse_block<D, W, T>(su, sf, g, field_of(fld0, cmp), sigma, kh2, sweeps, red);
     for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) uu[c] = su[c];
 }
 
@@ -278,15 +491,16 @@ struct TailLevels {
     int foff[MG_TAIL_MAX_LEVELS];
 };
 
-template <int D, typename T>
+template <int D, bool W, typename T>
 __global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__ ug, const T* __restrict__ fg,
-                                                  T sigma, double kappa, int zero_start, int pre, int post,
+                                                  int fld0, T sigma, double kappa, int zero_start, int pre, int post,
                                                   int sweeps) {
     extern __shared__ unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[32];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int cmp = blockIdx.x;
+    const int fld = field_of(fld0, cmp);
     const Geo g0 = tl.g[0];
     ug += cmp * g0.ncell;
     fg += cmp * g0.ncell;
@@ -304,14 +518,16 @@ __global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__
         T kh2 = (T)(kappa / (g.h * g.h));
         T* u = sm + tl.uoff[l];
         const T* f = sm + tl.foff[l];
-        for (long long t = tid; t < (g.ncell >> 1); t += nt) rbgs_point<D, T>(u, f, g, sigma, kh2, color, zero, t);
+        for (long long t = tid; t < (g.ncell >> 1); t += nt)
+            rbgs_point<D, W, T>(u, f, g, fld, sigma, kh2, color, zero, t);
         __syncthreads();
     };
     const int L = tl.nl;
     if (L == 1) {
         const Geo& g = tl.g[0];
         if (zero_start) {
-            coarse_block<D, T>(sm + tl.uoff[0], sm + tl.foff[0], g, sigma, (T)(kappa / (g.h * g.h)), sweeps, red);
+            coarse_block<D, W, T>(sm + tl.uoff[0], sm + tl.foff[0], g, fld, sigma, (T)(kappa / (g.h * g.h)), sweeps,
+                                  red);
         } else {
             for (int s = 0; s < sweeps; ++s) {
                 half(0, 0, 0);
@@ -336,20 +552,21 @@ __global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__
             const T* u = sm + tl.uoff[l];
             const T* f = sm + tl.foff[l];
             T* fc = sm + tl.foff[l + 1];
-            for (long long t = tid; t < gc.ncell; t += nt) fc[t] = restrict_point<D, T>(u, f, gf, gc, sigma, kh2, t);
+            for (long long t = tid; t < gc.ncell; t += nt)
+                fc[t] = restrict_point<D, W, T>(u, f, gf, gc, fld, sigma, kh2, t);
             __syncthreads();
         }
         {
             const Geo& g = tl.g[L - 1];
-            coarse_block<D, T>(sm + tl.uoff[L - 1], sm + tl.foff[L - 1], g, sigma, (T)(kappa / (g.h * g.h)), sweeps,
-                               red);
+            coarse_block<D, W, T>(sm + tl.uoff[L - 1], sm + tl.foff[L - 1], g, fld, sigma,
+                                  (T)(kappa / (g.h * g.h)), sweeps, red);
         }
         for (int l = L - 2; l >= 0; --l) {
             const Geo& gf = tl.g[l];
             const Geo& gc = tl.g[l + 1];
             T* u = sm + tl.uoff[l];
             const T* uc = sm + tl.uoff[l + 1];
-            for (long long t = tid; t < gf.ncell; t += nt) u[t] += prolong_point<D, T>(uc, gf, gc, t);
+            for (long long t = tid; t < gf.ncell; t += nt) u[t] += prolong_point<D, W, T>(uc, gf, gc, fld, t);
             __syncthreads();
             for (int it = 0; it < post; ++it) {
                 half(l, 1, 0);
@@ -364,40 +581,124 @@ __global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__
 }
 
 // q = -D y - hd ; qr = rhs_scale * q
-template <int D, typename T>
+template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_ps_div(const T* __restrict__ y, const T* __restrict__ hd,
                                                 T* __restrict__ qr, T rhs_scale, T* __restrict__ q, Geo g, T ih) {
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
-    const long long pp[3] = {n.xp, n.yp, n.zp};
+    const int pp[3] = {n.xp, n.yp, n.zp};
+    const int id[3] = {i, j, k};
+    const int ns[3] = {g.n0, g.n1, g.n2};
     T div = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T* u = y + a * g.ncell;
-        div += u[n.c + pp[a]] - u[n.c];
+        if (!W) {
+            div += u[n.c + pp[a]] - u[n.c];
+        } else {
+            const bool wa = (g.wall >> a) & 1;
+            T hi = (wa && id[a] == ns[a] - 1) ? T(0) : u[n.c + pp[a]];
+            T lo = (wa && id[a] == 0) ? T(0) : u[n.c];
+            div += hi - lo;
+        }
     }
     T qq = -div * ih - hd[n.c];
     q[n.c] = qq;
     qr[n.c] = rhs_scale * qq;
 }
 
-// z_v^a = y^a + h^2 (G phi)^a = y^a + h (phi_c - phi_{c-e_a}) ; z_p = c_q q + c_phi phi
-template <int D, typename T>
+// z_v^a = y^a + h^2 (G phi)^a = y^a + h (phi_c - phi_{c-e_a}) (wall faces:
+// no gradient) ; z_p = c_q q + c_phi phi
+template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_ps_finish(const T* __restrict__ y, const T* __restrict__ phi,
                                                    const T* __restrict__ q, T* __restrict__ z, Geo g, T h, T c_q,
                                                    T c_phi) {
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
-    const long long pm[3] = {n.xm, n.ym, n.zm};
+    const int pm[3] = {n.xm, n.ym, n.zm};
+    const int id[3] = {i, j, k};
     T pc = phi[n.c];
 #pragma unroll
-    for (int a = 0; a < D; ++a) z[a * g.ncell + n.c] = y[a * g.ncell + n.c] + h * (pc - phi[n.c + pm[a]]);
+    for (int a = 0; a < D; ++a) {
+        if (W && ((g.wall >> a) & 1) && id[a] == 0)
+            z[a * g.ncell + n.c] = y[a * g.ncell + n.c];
+        else
+            z[a * g.ncell + n.c] = y[a * g.ncell + n.c] + h * (pc - phi[n.c + pm[a]]);
+    }
     z[D * g.ncell + n.c] = c_q * q[n.c] + c_phi * pc;
 }
 
+// boundary data of one wall into the right-hand side (one thread per face point)
+__global__ void k_wall_lift(Geo g, int a, int side, const double* __restrict__ data, double* __restrict__ b,
+                            double kh2, double ih) {
+    const int ns[3] = {g.n0, g.n1, g.n2};
+    const long long nf = g.ncell / ns[a];
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    int id[3] = {0, 0, 0};
+    long long r = t;
+    for (int e = 0; e < g.d; ++e) {
+        if (e == a) continue;
+        id[e] = (int)(r % ns[e]);
+        r /= ns[e];
+    }
+    const long long st[3] = {1, ns[0], (long long)ns[0] * ns[1]};
+    auto cell = [&](int xa) {
+        long long c = 0;
+        for (int e = 0; e < g.d; ++e) c += (long long)(e == a ? xa : id[e]) * st[e];
+        return c;
+    };
+    const int n = ns[a];
+    double* bp = b + (long long)g.d * g.ncell;
+    for (int c = 0; c < g.d; ++c) {
+        const double val = data[c * nf + t];
+        double* bc = b + (long long)c * g.ncell;
+        if (c == a) {
+            if (side == 0) {
+                bc[cell(0)] = val;         // the wall face: v = wall value
+                bc[cell(1)] += kh2 * val;  // its neighbour face
+                bp[cell(0)] -= ih * val;   // inflow through the low face of cell 0
+            } else {
+                bc[cell(n - 1)] += kh2 * val;
+                bp[cell(n - 1)] += ih * val;
+            }
+        } else {
+            // the cell next to the wall: ghost = 2 u_wall - u; a wall-face
+            // row of component c keeps its own equation
+            if (((g.wall >> c) & 1) && id[c] == 0) continue;
+            bc[cell(side ? n - 1 : 0)] += 2.0 * kh2 * val;
+        }
+    }
+}
+
+// the stored low-wall faces of the normal component set to the wall value
+__global__ void k_wall_set(Geo g, int a, const double* __restrict__ data, double* __restrict__ x) {
+    const int ns[3] = {g.n0, g.n1, g.n2};
+    const long long nf = g.ncell / ns[a];
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    long long r = t, c = 0, st = 1;
+    for (int e = 0; e < g.d; ++e) {
+        if (e != a) {
+            c += (r % ns[e]) * st;
+            r /= ns[e];
+        }
+        st *= ns[e];
+    }
+    x[(long long)a * g.ncell + c] = data[(long long)a * nf + t];
+}
+
 }  // namespace
+
+void wall_set_faces(const Geo& g, int a, const double* data, double* x, cudaStream_t s) {
+    const int ns[3] = {g.n0, g.n1, g.n2};
+    long long nf = g.ncell / ns[a];
+    ProfScope ps(KID_SMALL, s, 0.0);
+    k_wall_set<<<grid_1d(nf, 128), 128, 0, s>>>(g, a, data, x);
+    IBR_CHECK_LAUNCH();
+}
 
 template <typename T>
 void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, const double* shift_dev,
@@ -406,74 +707,114 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
     T ih = (T)(1.0 / g.h);
     dim3 grid((g.n0 + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2), blk(BX, BY);
     ProfScope ps(KID_STOKES, s, 2.0 * (g.d + 1) * g.ncell * sizeof(T));
-    if (g.d == 3)
-        k_stokes<3, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
-    else
-        k_stokes<2, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+    const bool w = g.wall != 0;
+    if (g.d == 3) {
+        if (w)
+            k_stokes<3, true, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+        else
+            k_stokes<3, false, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+    } else {
+        if (w)
+            k_stokes<2, true, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+        else
+            k_stokes<2, false, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+    }
     IBR_CHECK_LAUNCH();
 }
 
 template <typename T>
-void mg_smooth(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int color, bool zero_init,
-               cudaStream_t s) {
+void mg_smooth(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, double kappa, int color,
+               bool zero_init, cudaStream_t s) {
     T kh2 = (T)(kappa / (g.h * g.h));
     dim3 grid(((g.n0 >> 1) + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2 * C), blk(BX, BY);
     // half sweep: read the other colour and f of this colour, write this colour
     ProfScope ps(KID_RBGS, s, (zero_init ? 1.0 : 1.5) * C * g.ncell * sizeof(T));
-    if (g.d == 3)
-        k_rbgs<3, T><<<grid, blk, 0, s>>>(u, f, g, kh2, rbgs_inv_diag<3, T>((T)sigma, kh2), color, zero_init ? 1 : 0);
-    else
-        k_rbgs<2, T><<<grid, blk, 0, s>>>(u, f, g, kh2, rbgs_inv_diag<2, T>((T)sigma, kh2), color, zero_init ? 1 : 0);
+    const int zi = zero_init ? 1 : 0;
+    const T sg = (T)sigma;
+    if (g.d == 3) {
+        T inv = rbgs_inv_diag<3, T>(sg, kh2);
+        if (g.wall)
+            k_rbgs<3, true, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+        else
+            k_rbgs<3, false, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+    } else {
+        T inv = rbgs_inv_diag<2, T>(sg, kh2);
+        if (g.wall)
+            k_rbgs<2, true, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+        else
+            k_rbgs<2, false, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+    }
     IBR_CHECK_LAUNCH();
 }
 
 template <typename T>
-void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, double sigma,
-                          double kappa, cudaStream_t s) {
+void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, T* fc, int C, int fld0,
+                          double sigma, double kappa, cudaStream_t s) {
     T kh2 = (T)(kappa / (gf.h * gf.h));
     dim3 grid((gc.n0 + BX - 1) / BX, (gc.n1 + BY - 1) / BY, gc.n2 * C), blk(BX, BY);
     ProfScope ps(KID_RESTRICT, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
-    if (gf.d == 3)
-        k_resid_restrict<3, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
-    else
-        k_resid_restrict<2, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, (T)sigma, kh2);
+    if (gf.d == 3) {
+        if (gf.wall)
+            k_resid_restrict<3, true, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+        else
+            k_resid_restrict<3, false, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+    } else {
+        if (gf.wall)
+            k_resid_restrict<2, true, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+        else
+            k_resid_restrict<2, false, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+    }
     IBR_CHECK_LAUNCH();
 }
 
 template <typename T>
-void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, cudaStream_t s) {
+void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, int fld0, cudaStream_t s) {
     dim3 grid((gf.n0 + BX - 1) / BX, (gf.n1 + BY - 1) / BY, gf.n2 * C), blk(BX, BY);
     ProfScope ps(KID_PROLONG, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
-    if (gf.d == 3)
-        k_prolong<3, T><<<grid, blk, 0, s>>>(u, uc, gf, gc);
-    else
-        k_prolong<2, T><<<grid, blk, 0, s>>>(u, uc, gf, gc);
+    if (gf.d == 3) {
+        if (gf.wall)
+            k_prolong<3, true, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+        else
+            k_prolong<3, false, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+    } else {
+        if (gf.wall)
+            k_prolong<2, true, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+        else
+            k_prolong<2, false, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+    }
     IBR_CHECK_LAUNCH();
 }
 
 template <typename T>
-void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, double sigma, double kappa, int sweeps,
+void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, double kappa, int sweeps,
                      cudaStream_t s) {
     T kh2 = (T)(kappa / (g.h * g.h));
     size_t sm = 2 * (size_t)g.ncell * sizeof(T);
     int nt = g.ncell >= 1024 ? 1024 : (int)((g.ncell + 31) / 32 * 32);
     ProfScope ps(KID_COARSE, s, 2.0 * C * g.ncell * sizeof(T));
-    if (g.d == 3)
-        k_coarse<3, T><<<C, nt, sm, s>>>(u, f, g, (T)sigma, kh2, sweeps);
-    else
-        k_coarse<2, T><<<C, nt, sm, s>>>(u, f, g, (T)sigma, kh2, sweeps);
+    if (g.d == 3) {
+        if (g.wall)
+            k_coarse<3, true, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+        else
+            k_coarse<3, false, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+    } else {
+        if (g.wall)
+            k_coarse<2, true, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+        else
+            k_coarse<2, false, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+    }
     IBR_CHECK_LAUNCH();
 }
-
 
 template <typename T>
 void mg_set_attributes() {
     static bool done = false;
     if (done) return;
-    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)MG_TAIL_MAX_SMEM));
-    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)MG_TAIL_MAX_SMEM));
+    const int sm = (int)MG_TAIL_MAX_SMEM;
+    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     done = true;
 }
 
@@ -486,8 +827,8 @@ static size_t tail_smem(const Geo* lev, int l0, int L) {
 }
 
 template <typename T>
-void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, double sigma, double kappa,
-               bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s) {
+void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
+               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s) {
     // the tail: the longest suffix of levels with <= MG_TAIL_MAX_CELLS cells each
     // that fits in shared memory (the coarsest level always does)
     int lt = L - 1;
@@ -499,10 +840,10 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         bool zs = (l > 0) || zero_start;
         if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(T) * C * lev[l].ncell, s));
         for (int it = 0; it < pre; ++it) {
-            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 0, zs && it == 0, s);
-            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 1, false, s);
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, fld0, sigma, kappa, 0, zs && it == 0, s);
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, fld0, sigma, kappa, 1, false, s);
         }
-        mg_residual_restrict<T>(lev[l], lev[l + 1], U[l], Fl(l), Fw[l + 1], C, sigma, kappa, s);
+        mg_residual_restrict<T>(lev[l], lev[l + 1], U[l], Fl(l), Fw[l + 1], C, fld0, sigma, kappa, s);
     }
     {
         TailLevels tl;
@@ -522,20 +863,30 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         bool zs = (lt > 0) || zero_start;
         ProfScope ps(KID_COARSE, s, 2.0 * C * n0 * sizeof(T));
         mg_set_attributes<T>();
+        const int z = zs ? 1 : 0;
+        const T sg = (T)sigma;
         if (lev[0].d == 3) {
-            k_mg_tail<3, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), (T)sigma, kappa, zs ? 1 : 0, pre, post,
-                                              coarse_sweeps);
+            if (lev[0].wall)
+                k_mg_tail<3, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                                                       coarse_sweeps);
+            else
+                k_mg_tail<3, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                                                        coarse_sweeps);
         } else {
-            k_mg_tail<2, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), (T)sigma, kappa, zs ? 1 : 0, pre, post,
-                                              coarse_sweeps);
+            if (lev[0].wall)
+                k_mg_tail<2, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                                                       coarse_sweeps);
+            else
+                k_mg_tail<2, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                                                        coarse_sweeps);
         }
         IBR_CHECK_LAUNCH();
     }
     for (int l = lt - 1; l >= 0; --l) {
-        mg_prolong_correct<T>(lev[l], lev[l + 1], U[l], U[l + 1], C, s);
+        mg_prolong_correct<T>(lev[l], lev[l + 1], U[l], U[l + 1], C, fld0, s);
         for (int it = 0; it < post; ++it) {
-            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 1, false, s);
-            mg_smooth<T>(lev[l], U[l], Fl(l), C, sigma, kappa, 0, false, s);
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, fld0, sigma, kappa, 1, false, s);
+            mg_smooth<T>(lev[l], U[l], Fl(l), C, fld0, sigma, kappa, 0, false, s);
         }
     }
 }
@@ -544,10 +895,18 @@ template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s) {
     dim3 grid((g.n0 + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2), blk(BX, BY);
     ProfScope ps(KID_PS_DIV, s, (g.d + 3.0) * g.ncell * sizeof(T));
-    if (g.d == 3)
-        k_ps_div<3, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
-    else
-        k_ps_div<2, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, (T)rhs_scale, q, g, (T)(1.0 / g.h));
+    const T ih = (T)(1.0 / g.h), rs = (T)rhs_scale;
+    if (g.d == 3) {
+        if (g.wall)
+            k_ps_div<3, true, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+        else
+            k_ps_div<3, false, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+    } else {
+        if (g.wall)
+            k_ps_div<2, true, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+        else
+            k_ps_div<2, false, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+    }
     IBR_CHECK_LAUNCH();
 }
 
@@ -556,23 +915,39 @@ void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double 
                cudaStream_t s) {
     dim3 grid((g.n0 + BX - 1) / BX, (g.n1 + BY - 1) / BY, g.n2), blk(BX, BY);
     ProfScope ps(KID_PS_FINISH, s, (2.0 * g.d + 3.0) * g.ncell * sizeof(T));
-    if (g.d == 3)
-        k_ps_finish<3, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
-    else
-        k_ps_finish<2, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, (T)g.h, (T)c_q, (T)c_phi);
+    const T h = (T)g.h, cq = (T)c_q, cp = (T)c_phi;
+    if (g.d == 3) {
+        if (g.wall)
+            k_ps_finish<3, true, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+        else
+            k_ps_finish<3, false, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+    } else {
+        if (g.wall)
+            k_ps_finish<2, true, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+        else
+            k_ps_finish<2, false, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+    }
+    IBR_CHECK_LAUNCH();
+}
+
+void wall_lift(const Geo& g, int a, int side, const double* data, double* b, double eta, cudaStream_t s) {
+    const int ns[3] = {g.n0, g.n1, g.n2};
+    long long nf = g.ncell / ns[a];
+    ProfScope ps(KID_SMALL, s, 0.0);
+    k_wall_lift<<<grid_1d(nf, 128), 128, 0, s>>>(g, a, side, data, b, eta / (g.h * g.h), 1.0 / g.h);
     IBR_CHECK_LAUNCH();
 }
 
 #define IBR_INST(T)                                                                                        \
     template void stokes_apply<T>(const Geo&, const T*, T*, double, double, const double*, cudaStream_t); \
-    template void mg_smooth<T>(const Geo&, T*, const T*, int, double, double, int, bool, cudaStream_t);   \
-    template void mg_residual_restrict<T>(const Geo&, const Geo&, const T*, const T*, T*, int, double,    \
+    template void mg_smooth<T>(const Geo&, T*, const T*, int, int, double, double, int, bool, cudaStream_t); \
+    template void mg_residual_restrict<T>(const Geo&, const Geo&, const T*, const T*, T*, int, int, double, \
                                           double, cudaStream_t);                                          \
-    template void mg_prolong_correct<T>(const Geo&, const Geo&, T*, const T*, int, cudaStream_t);         \
-    template void mg_coarse_solve<T>(const Geo&, T*, const T*, int, double, double, int, cudaStream_t);   \
+    template void mg_prolong_correct<T>(const Geo&, const Geo&, T*, const T*, int, int, cudaStream_t);    \
+    template void mg_coarse_solve<T>(const Geo&, T*, const T*, int, int, double, double, int, cudaStream_t); \
     template void mg_set_attributes<T>();                                                                   \
-    template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, double, double, bool, int,   \
-                               int, int, cudaStream_t);                                                      \
+    template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, int, double, double, bool, \
+                               int, int, int, cudaStream_t);                                                \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \
     template void ps_finish<T>(const Geo&, const T*, const T*, const T*, T*, double, double, cudaStream_t);
 IBR_INST(double)

@@ -18,6 +18,11 @@ __all__ = [
     "small_2d",
     "small_3d",
     "random_velocities",
+    "wall_2d",
+    "wall_3d",
+    "nozzle",
+    "nozzle_walls",
+    "parabolic_inflow",
 ]
 
 
@@ -56,10 +61,14 @@ class Workload:
     dt: float = 0.0
     bodies: list = field(default_factory=list)
     tol: float = 1e-8
+    walls: tuple = ()           # per axis: True for walls at both ends (empty: all periodic)
 
     @property
     def d(self):
         return len(self.n)
+
+    def wall_flags(self):
+        return tuple(bool(w) for w in self.walls) if self.walls else (False,) * self.d
 
     def markers(self):
         """(q[N,d] lab positions, rel[N,d], body[N]) concatenated over bodies."""
@@ -119,3 +128,88 @@ def small_3d(n=8, N=12, seed=11, rho=0.0, dt=0.0, radius_h=1.6):
     rel = sphere_markers(radius_h * h, N)
     body = Body(c, rel, random_velocities(rng, 3, 1)[0])
     return Workload(f"small3d_{n}", (n, n, n), (1.0, 1.0, 1.0), rho=rho, dt=dt, bodies=[body], tol=1e-10)
+
+
+def wall_2d(n=(24, 16), walls=(True, True), nbody=2, seed=31, rho=0.0, dt=0.0, radius_h=2.5):
+    """Small 2-D box of height 1 (cells h = 1/n[1]) with walls on the flagged
+    axes; disks of radius radius_h*h, markers at ~2h, one of them pushed
+    into the kernel support of the low y-wall (and of the low x-wall when
+    walls[0])."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n[1]
+    L = (n[0] * h, 1.0)
+    r = radius_h * h
+    bodies = []
+    for b in range(nbody):
+        c = np.array([(b + 0.5) / nbody * L[0], 0.55]) + rng.uniform(-0.5, 0.5, 2) * h
+        if b == 0:
+            c[1] = r + rng.uniform(0.6, 1.4) * h
+            if walls[0]:
+                c[0] = r + rng.uniform(0.6, 1.4) * h
+        bodies.append(Body(c, disk_markers(r, h), random_velocities(rng, 2, 1)[0]))
+    return Workload(f"wall2d_{n[0]}x{n[1]}", tuple(n), L, rho=rho, dt=dt, bodies=bodies, tol=1e-10,
+                    walls=tuple(walls))
+
+
+def wall_3d(n=(8, 12, 8), walls=(False, True, True), seed=37, rho=0.0, dt=0.0, radius_h=1.6, N=12):
+    """Small 3-D duct (height 1 along y) with walls on the flagged axes; one
+    sphere of markers within the kernel support of the low y-wall."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n[1]
+    L = tuple(m * h for m in n)
+    r = radius_h * h
+    c = np.array([0.5 * L[0], r + rng.uniform(0.6, 1.2) * h, 0.5 * L[2]]) + np.array([1, 0, 1]) * rng.uniform(-0.5, 0.5, 3) * h
+    body = Body(c, sphere_markers(r, N), random_velocities(rng, 3, 1)[0])
+    return Workload(f"wall3d_{n[0]}x{n[1]}x{n[2]}", tuple(n), L, rho=rho, dt=dt, bodies=[body], tol=1e-10,
+                    walls=tuple(walls))
+
+
+def nozzle_walls(h, depth=0.3, half_len=0.9, spacing=2.0, min_gap=1.0):
+    """Marker rows of the two nozzle walls in the channel [0,2] x [0,1]: the
+    upper wall y = 1 - depth (1 + cos(pi (x - 1) / half_len)) / 2 for
+    |x - 1| <= half_len, the lower one its mirror image y -> 1 - y (throat
+    [0.3, 0.7] for depth 0.3).  Markers at arc-length spacing `spacing` h,
+    symmetric about x = 1; markers closer than min_gap h to the channel wall
+    (where the nozzle wall merges with it) are left out: that wall already
+    holds the fluid there, and a marker on it would give a zero constraint
+    row.  Returns [(centre, rel)] for the upper and lower walls."""
+    x = np.linspace(1.0 - half_len, 1.0 + half_len, 200001)
+    y = 1.0 - depth * 0.5 * (1.0 + np.cos(np.pi * (x - 1.0) / half_len))
+    seg = np.hypot(np.diff(x), np.diff(y))
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    smid = s[-1] / 2.0
+    k = np.arange(-int(smid / (spacing * h)), int(smid / (spacing * h)) + 1)
+    sk = smid + k * spacing * h
+    xs = np.interp(sk, s, x)
+    ys = np.interp(sk, s, y)
+    keep = (1.0 - ys) >= min_gap * h
+    up = np.stack([xs[keep], ys[keep]], axis=1)
+    lo = np.stack([xs[keep], 1.0 - ys[keep]], axis=1)
+    out = []
+    for q in (up, lo):
+        c = q.mean(axis=0)
+        out.append((c, q - c))
+    return out
+
+
+def parabolic_inflow(n1, U=1.0):
+    """Normal velocity 4 U y (1 - y) at the cell-centred heights of a wall
+    face column of a channel of height 1 with n1 cells."""
+    y = (np.arange(n1) + 0.5) / n1
+    return 4.0 * U * y * (1.0 - y)
+
+
+def nozzle(n=(256, 128), Re=0.0, U=1.0):
+    """2-D nozzle flow: channel [0,2] x [0,1], no-slip at y = 0, 1, parabolic
+    inflow/outflow 4 U y (1 - y) at x = 0 and x = 2, two fixed rigid nozzle
+    walls (nozzle_walls) forming a throat of width 0.4.  Re = rho U 0.4 / eta
+    with rho = 1 (Re = 0: steady Stokes, eta = 1); the time step is
+    0.5 h / U (the inflow peak)."""
+    h = 1.0 / n[1]
+    bodies = [Body(c, rel, np.zeros(3)) for c, rel in nozzle_walls(h)]
+    if Re == 0:
+        eta, rho, dt = 1.0, 0.0, 0.0
+    else:
+        eta, rho, dt = U * 0.4 / Re, 1.0, 0.5 * h / U
+    return Workload(f"nozzle_{n[0]}x{n[1]}_Re{Re:g}", tuple(n), (2.0, 1.0), eta=eta, rho=rho, dt=dt, bodies=bodies,
+                    tol=1e-8, walls=(True, True))

@@ -53,7 +53,7 @@ def test_struct_layouts(abi):
 
 def test_default_options(abi):
     o = abi.solve_opts_default()
-    assert o.tol == 1e-8 and o.restart == 50 and o.n_s == 2 and o.variant == abi.PC_LOWER
+    assert o.tol == 1e-8 and o.restart == 50 and o.n_s == 0 and o.variant == abi.PC_LOWER
     assert o.mg_pre == 2 and o.mg_post == 2 and o.mob_model == abi.MOB_AUTO
 
 
@@ -61,7 +61,8 @@ def test_default_options(abi):
     ((4, [8, 8], [1, 1]), "dim must be 2 or 3"),
     ((2, [7, 8], [1, 1]), "even"),
     ((2, [8, 8], [1, 2]), "cubes"),
-    ((2, [8, 8], [1, 1], [0, 0, 1, 1]), "periodic"),
+    ((2, [8, 8], [1, 1], [0, 1, 1, 1]), "periodic at both ends"),   # one periodic side, one wall
+    ((2, [8, 8], [1, 1], [7, 7, 0, 0]), "bounded by walls"),        # unknown condition
 ])
 def test_create_grid_validation_without_gpu(abi, args, msg):
     with pytest.raises(abi.IbrError) as e:
