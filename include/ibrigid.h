@@ -121,7 +121,15 @@ int ibr_solve_opts_default(ibr_solve_opts* opts);
 
 /* Creates a uniform MAC grid (Sec. III).  dim in {2,3}; n[0..dim-1] cells per
  * axis (each even, >= 4); L[0..dim-1] box lengths (cubic cells: L[a]/n[a]
- * equal for all a).  bc[a][s]: only IBR_PERIODIC is accepted by this build.
+ * equal for all a).  bc[2a + s] (s = 0 low, 1 high end of axis a): both
+ * IBR_PERIODIC, or both walls, IBR_NOSLIP (zero velocity) or IBR_VELOCITY
+ * (velocity given by ibr_set_boundary_velocity, zero until then).  Walls
+ * follow App. D: fields are extended beyond a wall by linear extrapolation
+ * through the wall value, and the same extension gives interpolation and
+ * spreading near the wall.  On a wall axis the velocity component normal to
+ * the wall stores faces 0..n-1 of its n+1 faces: face 0 lies on the low wall
+ * (its equation is v = wall value, and it holds that value in the solution),
+ * the high wall face is not stored.
  * eta > 0 viscosity; rho, dt >= 0 (rho == 0 or dt == 0: steady Stokes, A =
  * -eta h^-2 Lap).  kernel: IBR_KERNEL_PESKIN4.  precision: IBR_FP64 or
  * IBR_MIXED.  cuda_stream: a cudaStream_t, or NULL for a library-created
@@ -142,15 +150,21 @@ int ibr_add_body(ibr_grid* g, const double* x_c, const double* quat, int kinemat
 
 /* Sets the N markers of a body from body-frame offsets r_body[N*dim] (host).
  * Lab positions q_i = x_c + Q(quat) r_i are wrapped into [0, L) on periodic
- * axes.  Marks the geometry dirty: the next solve (or ibr_prepare) rebins the
+ * axes and must lie in [0, L] on wall axes (IBR_EINVAL at set-up).  Marks the geometry dirty: the next solve (or ibr_prepare) rebins the
  * markers and rebuilds and refactors M~.  N >= 1.  M~ is factorised by
  * Cholesky; a block that is not positive definite (the analytic M~ need not
  * be, Sec. V.C) is factorised as M~ + delta I with the smallest delta in
  * 1e-3 f(0) * 2^k that succeeds (IBR_ENUMERIC if none up to k = 40). */
 int ibr_set_markers(ibr_grid* g, int body_id, const double* r_body, int N);
 
-/* Inhomogeneous boundary data for IBR_VELOCITY faces.  Not supported by this
- * build (periodic only): returns IBR_EINVAL. */
+/* Velocity on the wall face = 2a + s (an IBR_VELOCITY side): values[dim][P]
+ * (host, copied), P = cells of the other axes (lower axis fastest); values[a]
+ * is the normal velocity at the wall's normal faces, values[b] (b != a) the
+ * tangential velocity at the wall positions of component b's faces.  The
+ * data enters the right-hand side (the lifted App. D extension); the net
+ * flux through all walls must vanish (checked at solve time: IBR_EINVAL),
+ * and markers must stay 2h away from walls with nonzero data (checked in the
+ * set-up: IBR_EINVAL).  IBR_EINVAL for other faces. */
 int ibr_set_boundary_velocity(ibr_grid* g, int face, const double* values);
 
 /* Runs the geometry set-up now (marker lab positions, kernel weights, the
