@@ -261,18 +261,21 @@ class WallGrid:
         return e
 
     def _ext_data(self, bd, a, s, field, cur_shape, ax):
-        """wall data for `field` on wall (a, s), padded with zeros on axes
-        already extended (corners are never read by the 2d+1 stencils)."""
+        """wall data for `field` on wall (a, s), extended over the axes
+        already extended: periodically on periodic axes, by zeros on wall
+        axes (those corners are read by no stencil of this module)."""
         if bd is None or field == PFIELD:
             shp = list(cur_shape)
             shp[ax] = 1
             return np.zeros(shp)
         v = self._wall_values(bd, a, s, field)
-        pad = [(0, 0)] * self.d
         for b in range(self.d):
-            if self.ax(b) != ax and v.shape[self.ax(b)] != cur_shape[self.ax(b)]:
-                pad[self.ax(b)] = (1, cur_shape[self.ax(b)] - v.shape[self.ax(b)] - 1)
-        return np.pad(v, pad)
+            axb = self.ax(b)
+            if axb != ax and v.shape[axb] != cur_shape[axb]:
+                pad = [(0, 0)] * self.d
+                pad[axb] = (1, cur_shape[axb] - v.shape[axb] - 1)
+                v = np.pad(v, pad, mode="wrap" if not self.walls[b] else "constant")
+        return v
 
     def apply_full(self, v, p, bd):
         """Route X: the affine fluid operator.  Returns (momentum rows per
