@@ -114,6 +114,16 @@ typedef struct ibr_solve_info {
     double ms_solve;       /* FGMRES, wall ms                                    */
 } ibr_solve_info;
 
+typedef struct ibr_step_info {
+    int    status;         /* same as the return code of ibr_advance             */
+    int    steps;          /* time steps taken                                   */
+    int    iters_total;    /* outer FGMRES iterations over all steps             */
+    int    iters_last;     /* outer FGMRES iterations of the last step           */
+    double change;         /* ||v^{n+1} - v^n|| / ||v^{n+1}|| of the last step   */
+    double rel_res_last;   /* true relative residual of the last step's solve    */
+    double ms;             /* wall ms of the call                                */
+} ibr_step_info;
+
 /* Fills opts with the defaults: tol 1e-8, restart 50, max_iters 1000, N_s 0 (automatic),
  * IBR_PC_LOWER, mg 2/2, IBR_MOB_AUTO, a/h 0 (=1.25 in 3-D, see ibr_solve_coupled),
  * the library's 2-D coefficient set, no time cap. */
@@ -183,6 +193,28 @@ int ibr_prepare(ibr_grid* g, const ibr_solve_opts* opts);
 int ibr_solve_coupled(ibr_grid* g, const double* body_UO, const double* gforce, int g_on_device,
                       const ibr_solve_opts* opts, ibr_solve_info* info);
 
+/* Time stepping (Sec. VII.F; the nozzle flow).  Advances the fluid state v^n
+ * (the last solution's velocity; at rest with the wall values if there is
+ * none) by up to nsteps steps of size dt: each step solves the constrained
+ * system with the backward-Euler operator A = rho/dt I - eta h^-2 Lap and
+ *     g = (rho/dt) v^n - rho (3/2 N(v^n) - 1/2 N(v^{n-1})) + f
+ * (the first step of a history uses N(v^n) alone), N(v) = div(v v) in the
+ * centred second-order flux form on the MAC grid with the same wall
+ * extension as the fluid operators; FGMRES starts from the previous step's
+ * solution.  Stops early when ||v^{n+1} - v^n|| <= steady_tol ||v^{n+1}||
+ * (steady state; 0: never).  body_UO as in ibr_solve_coupled (fixed for all
+ * steps); gforce: a constant body force f (dim face arrays, device if
+ * g_on_device, else host) or NULL.  Needs rho > 0 and dt > 0 (IBR_EINVAL).
+ * A step whose solve does not converge stops the march with its status. */
+int ibr_advance(ibr_grid* g, const double* body_UO, const double* gforce, int g_on_device, int nsteps,
+                double steady_tol, const ibr_solve_opts* opts, ibr_step_info* info);
+
+/* Sets the fluid velocity state v (dim face arrays; device if on_device, else
+ * host) that ibr_advance starts from (pressure and Lambda zero; the wall
+ * faces take the wall values); restarts the AB2 history.  Runs the geometry
+ * set-up if needed. */
+int ibr_set_velocity(ibr_grid* g, const double* v, int on_device);
+
 /* Copies the marker forces Lambda[N*dim] (may be NULL) and the per-body
  * K^T Lambda = [force; torque] of each body on the fluid, body_FT[B*(dim+rot)]
  * (may be NULL), of the last solve to host memory. */
@@ -234,6 +266,11 @@ int ibr_op_mtilde_solve(ibr_grid* g, const double* rhs, double* out);
  * Eq. P1_practical) in the preconditioner precision, r and z of length
  * (dim+1)*cells (velocity then pressure). */
 int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
+
+/* N = div(v v) (the advection term of ibr_advance: centred flux form, the
+ * wall extension with the wall data), v and N device arrays of dim face
+ * arrays (FP64). */
+int ibr_op_advect(ibr_grid* g, const double* v, double* N);
 
 /* k V-cycles of the scalar multigrid for (sigma I - kappa Delta_h) u = f on the
  * cell grid, starting from u (in/out); on wall axes the cell-centred

@@ -59,6 +59,21 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class StepInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("steps", ctypes.c_int),
+        ("iters_total", ctypes.c_int),
+        ("iters_last", ctypes.c_int),
+        ("change", ctypes.c_double),
+        ("rel_res_last", ctypes.c_double),
+        ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class IbrError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"[{code}] {msg}")
@@ -84,6 +99,9 @@ _SIGS = {
     "ibr_prepare": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts)]),
     "ibr_solve_coupled": (ctypes.c_int, [_P, _D, _P, ctypes.c_int, ctypes.POINTER(SolveOpts),
                                          ctypes.POINTER(SolveInfo)]),
+    "ibr_advance": (ctypes.c_int, [_P, _D, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   ctypes.POINTER(SolveOpts), ctypes.POINTER(StepInfo)]),
+    "ibr_set_velocity": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "ibr_get_forces": (ctypes.c_int, [_P, _D, _D]),
     "ibr_get_fields": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "ibr_get_body_velocities": (ctypes.c_int, [_P, _D, _D]),
@@ -96,6 +114,7 @@ _SIGS = {
     "ibr_op_mtilde": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "ibr_op_mtilde_solve": (ctypes.c_int, [_P, _P, _P]),
     "ibr_op_stokes_pc": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_advect": (ctypes.c_int, [_P, _P, _P]),
     "ibr_op_vcycle": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_int]),
     "ibr_destroy_grid": (ctypes.c_int, [_P]),
     "ibr_last_error": (ctypes.c_char_p, []),
@@ -209,6 +228,33 @@ def solve_coupled(grid, body_UO, g=None, opts=None, raise_on_notconv=False):
     return info
 
 
+def _field_arg(g):
+    if g is None:
+        return None, 0, None
+    if hasattr(g, "is_cuda"):
+        return _dev(g), 1, g
+    arr = _host(g)
+    return arr.ctypes.data_as(_P), 0, arr
+
+
+def advance(grid, body_UO, nsteps, steady_tol=0.0, g=None, opts=None, raise_on_notconv=False):
+    """Time steps (ibr_advance); g: constant body force (host array or CUDA tensor) or None."""
+    uo = _host(body_UO)
+    info = StepInfo()
+    gp, on_dev, _keep = _field_arg(g)
+    rc = _lib.ibr_advance(grid, _dptr(uo), gp, on_dev, int(nsteps), float(steady_tol),
+                          None if opts is None else ctypes.byref(opts), ctypes.byref(info))
+    if rc in (ENOTCONV, ETIMEOUT) and not raise_on_notconv:
+        return info
+    _check(rc)
+    return info
+
+
+def set_velocity(grid, v):
+    vp, on_dev, _keep = _field_arg(v)
+    _check(_lib.ibr_set_velocity(grid, vp, on_dev))
+
+
 def sizes(grid):
     ln = ctypes.c_longlong()
     nm = ctypes.c_int()
@@ -271,6 +317,10 @@ def op_mtilde(grid, body, out):
 
 def op_mtilde_solve(grid, rhs, out):
     _check(_lib.ibr_op_mtilde_solve(grid, _dev(rhs), _dev(out)))
+
+
+def op_advect(grid, v, N):
+    _check(_lib.ibr_op_advect(grid, _dev(v), _dev(N)))
 
 
 def op_stokes_pc(grid, r, z):

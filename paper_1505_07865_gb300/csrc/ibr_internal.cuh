@@ -39,7 +39,7 @@ enum KernelId {
     KID_STOKES, KID_RBGS, KID_RESTRICT, KID_PROLONG, KID_COARSE, KID_PS_DIV, KID_PS_FINISH,
     KID_AXPBY, KID_SCALE, KID_CONVERT, KID_MDOT, KID_UPD_MDOT, KID_UPD_NORM, KID_NORM2, KID_COMBINE,
     KID_BLOCK_MEANS, KID_SUB_MEANS, KID_SMALL, KID_SPREAD, KID_INTERP, KID_LAMSUM, KID_RIGID_K,
-    KID_RIGID_KT, KID_MARKERS, KID_MTILDE, KID_SPD_INV, KID_GEMV, KID_COUNT
+    KID_RIGID_KT, KID_MARKERS, KID_MTILDE, KID_SPD_INV, KID_GEMV, KID_ADVECT, KID_COUNT
 };
 // records CUDA events around the launches in its scope when profiling is on;
 // bytes = the algorithmic bytes those launches move
@@ -154,6 +154,18 @@ void wall_lift(const Geo& g, int a, int side, const double* data, double* b, dou
 // x's stored low-wall faces of component a set to the wall value (their rows
 // are the identity and nothing else couples to them)
 void wall_set_faces(const Geo& g, int a, const double* data, double* x, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// advect.cu -- explicit advection of the time-stepped problems (FP64)
+// wall velocities per wall side 2a + s ([d][face points]; NULL on periodic axes)
+struct WallData {
+    const double* data[6];
+};
+// N = div(v v), centred flux form, App. D extension with the wall data
+void advect(const Geo& g, const double* v, const WallData& wd, double* N, cudaStream_t s);
+// out = sigma v - (rho_c1 Nn + rho_c0 Np) + f   (f may be NULL), m entries
+void step_force(long long m, const double* v, const double* Nn, const double* Np, const double* f, double sigma,
+                double rho_c1, double rho_c0, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // blas.cu -- vector kernels; dots reduce deterministically (fixed blocks)

@@ -185,6 +185,10 @@ struct ibr_grid {
     // periodic steady Stokes: <v> = 0 is part of the problem and S~ = S - vol^-1 1^T
     bool null_v() const { return steady() && !walls(); }
     long long face_points(int a) const { return geo.ncell / n[a]; }
+    // time stepping (ibr_advance): v^n, N(v^n), N(v^{n-1}), the step forcing,
+    // the constant body force; hist: N(v^{n-1}) is valid (AB2 from then on)
+    double *adv_v = nullptr, *adv_N = nullptr, *adv_Np = nullptr, *adv_g = nullptr, *adv_f = nullptr;
+    bool adv_hist = false;
     int rot() const { return d == 2 ? 1 : 3; }
 };
 
@@ -919,18 +923,20 @@ void project_solution(ibr_grid* G, double* x) {
         subtract_means<double>(n, 1, x + (long long)d * n, G->means + d, s);
 }
 
-int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
+// warm: start from the x already in G->x (time stepping), else from x = 0
+int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm = false) {
     cudaStream_t s = G->stream;
     long long len = G->len;
     int m = o.restart;
     double t0 = now_ms();
     norm2<double>(len, G->b, G->partial, G->sc + 0, s);
     double bnorm = std::sqrt(read_scalar(G, G->sc + 0));
-    IBR_CUDA_TRY(cudaMemsetAsync(G->x, 0, len * sizeof(double), s));
+    if (!warm) IBR_CUDA_TRY(cudaMemsetAsync(G->x, 0, len * sizeof(double), s));
     info.iters = 0;
     info.restarts = 0;
     if (!(bnorm > 0.0)) {
         if (std::isnan(bnorm)) throw Error{IBR_ENUMERIC, "right-hand side contains NaN/Inf"};
+        if (warm) IBR_CUDA_TRY(cudaMemsetAsync(G->x, 0, len * sizeof(double), s));
         info.rel_res_est = info.rel_res_true = 0.0;
         return IBR_OK;
     }
@@ -939,7 +945,7 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info) {
     // residual at each restart to stderr (diagnostics only)
     const char* ve = std::getenv("IBR_VERBOSE");
     bool verbose = ve && ve[0] && ve[0] != '0';
-    bool first = true;
+    bool first = !warm;
     bool last_cycle_converged_est = false;
     int stalls = 0;
     double last_rn = 0.0;
@@ -1036,6 +1042,125 @@ int run_guarded(const char* fn, const std::function<void()>& body) {
     }
 }
 }  // namespace
+
+// One solve of the constrained system: options checked, set-up on demand,
+// b = [g + wall data; wall data; W = -K U; F], FGMRES (from x = 0, or from
+// the current x when warm), wall faces set.  Returns the FGMRES status.
+int solve_core(ibr_grid* G, const double* body_UO, const double* gforce, int g_on_device,
+               const ibr_solve_opts* opts, ibr_solve_info& info, bool warm) {
+    require(G && body_UO, "grid and body_UO must be non-NULL");
+    ibr_solve_opts o;
+    if (opts)
+        o = *opts;
+    else
+        opts_default(&o);
+    require(o.tol > 0 && o.tol < 1, "tol must be in (0,1)");
+    require(o.restart >= 1 && o.restart <= 120, "restart must be in [1,120]");
+    require(o.n_s >= 0 && o.n_s <= 16, "n_s must be in [0,16]");
+    // N_s = 2 for periodic problems (Sec. VII.A); near no-slip walls the
+    // projection preconditioner is further from the Stokes inverse and
+    // N_s = 4 is the robust choice (Sec. VII.A)
+    if (o.n_s == 0) o.n_s = G->walls() ? 4 : 2;
+    require(o.max_iters >= 1, "max_iters must be >= 1");
+    require(o.variant == IBR_PC_LOWER || o.variant == IBR_PC_FULL, "bad variant");
+    require(o.mg_pre >= 0 && o.mg_post >= 0 && o.mg_pre + o.mg_post >= 1, "bad mg sweeps");
+    cudaStream_t s = G->stream;
+    double t0 = now_ms();
+    if (G->dirty || !mob_opts_equal(o, G->prepared_opts)) prepare(G, o);
+    ensure_pc(G, o.n_s);
+    ensure_outer(G, o.restart);
+    double t1 = now_ms();
+    int B = (int)G->bodies.size();
+    int nuo = B * (G->d + G->rot());
+    for (int i = 0; i < nuo; ++i)
+        if (!std::isfinite(body_UO[i])) throw Error{IBR_ENUMERIC, "body_UO contains NaN/Inf"};
+    // prescribed bodies' velocities (free bodies' rows zeroed: their markers
+    // have W = 0) and free bodies' loads
+    std::vector<double> uo(body_UO, body_UO + nuo), load;
+    int nr = G->d + G->rot();
+    for (int bi = 0; bi < B; ++bi)
+        if (G->bfree[bi] >= 0) {
+            load.insert(load.end(), uo.begin() + bi * nr, uo.begin() + (bi + 1) * nr);
+            std::fill(uo.begin() + bi * nr, uo.begin() + (bi + 1) * nr, 0.0);
+        }
+    IBR_CUDA_TRY(cudaMemcpyAsync(G->UO, uo.data(), nuo * sizeof(double), cudaMemcpyHostToDevice, s));
+    // b = [g; 0; W = -K U; F]
+    long long nS = G->nS;
+    IBR_CUDA_TRY(cudaMemsetAsync(G->b, 0, nS * sizeof(double), s));
+    if (gforce) {
+        size_t bytes = (size_t)G->d * G->geo.ncell * sizeof(double);
+        IBR_CUDA_TRY(cudaMemcpyAsync(G->b, gforce, bytes,
+                                     g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    rigid_K(G->d, G->N, G->md.rel, G->md.body, G->UO, G->b + nS, -1.0, s);
+    if (G->walls()) {
+        // no net flux through the walls (solvability of the divergence rows)
+        double flux = 0.0, scale = 0.0;
+        for (int a = 0; a < G->d; ++a) {
+            if (!((G->geo.wall >> a) & 1)) continue;
+            const long long nf = G->face_points(a);
+            const double* lo = G->wdata_host[2 * a].data() + (size_t)a * nf;
+            const double* hi = G->wdata_host[2 * a + 1].data() + (size_t)a * nf;
+            for (long long t = 0; t < nf; ++t) {
+                flux += hi[t] - lo[t];
+                scale += std::fabs(hi[t]) + std::fabs(lo[t]);
+            }
+        }
+        require(std::fabs(flux) <= 1e-10 * scale, "the wall velocities have a net flux (inflow != outflow)");
+        for (int a = 0; a < G->d; ++a)
+            if ((G->geo.wall >> a) & 1)
+                for (int sd = 0; sd < 2; ++sd) wall_lift(G->geo, a, sd, G->wdata[2 * a + sd], G->b, G->eta, s);
+    }
+    if (G->nfree > 0)
+        IBR_CUDA_TRY(cudaMemcpyAsync(G->b + nS + (long long)G->N * G->d, load.data(),
+                                     load.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    auto setup_pc = [&](auto* pc) {
+        pc->ns = o.n_s;
+        pc->pre = o.mg_pre;
+        pc->post = o.mg_post;
+        pc->variant = o.variant;
+        pc->ps_count = 0;
+    };
+    if (G->precision == IBR_FP64) {
+        setup_pc(G->pc64);
+        G->pc64->Minv = G->Minv64;
+        G->pc64->setup_free();
+    } else {
+        setup_pc(G->pc32);
+        G->pc32->Minv = G->Minv32;
+        G->pc32->setup_free();
+    }
+    int status = fgmres(G, o, info, warm);
+    if (G->walls())
+        for (int a = 0; a < G->d; ++a)
+            if ((G->geo.wall >> a) & 1) wall_set_faces(G->geo, a, G->wdata[2 * a], G->x, s);
+    IBR_CUDA_TRY(cudaStreamSynchronize(s));
+    double t2 = now_ms();
+    info.ms_setup = t1 - t0;
+    info.ms_solve = t2 - t1;
+    info.ps_applications =
+        (int)(G->precision == IBR_FP64 ? G->pc64->ps_count : G->pc32->ps_count);
+    G->have_solution = true;
+    return status;
+}
+
+// makes G->x usable as a state: set-up, workspaces, and x = 0 with the wall
+// values on the wall faces if there is no solution yet
+void ensure_state(ibr_grid* G, const ibr_solve_opts& o) {
+    if (G->dirty || !mob_opts_equal(o, G->prepared_opts)) prepare(G, o);
+    ensure_pc(G, o.n_s > 0 ? o.n_s : (G->walls() ? 4 : 2));
+    ensure_outer(G, o.restart);
+    if (!G->have_solution) {
+        IBR_CUDA_TRY(cudaMemsetAsync(G->x, 0, G->len * sizeof(double), G->stream));
+        for (int a = 0; a < G->d; ++a)
+            if ((G->geo.wall >> a) & 1) wall_set_faces(G->geo, a, G->wdata[2 * a], G->x, G->stream);
+        G->have_solution = true;
+        G->adv_hist = false;
+    }
+    const long long m = (long long)G->d * G->geo.ncell;
+    for (double** p : {&G->adv_v, &G->adv_N, &G->adv_Np, &G->adv_g})
+        if (!*p) *p = dalloc<double>(m);
+}
 
 extern "C" {
 
@@ -1194,98 +1319,7 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
     int status = IBR_OK;
     int rc = run_guarded("ibr_solve_coupled", [&] {
         require(G && body_UO, "grid and body_UO must be non-NULL");
-        ibr_solve_opts o;
-        if (opts)
-            o = *opts;
-        else
-            opts_default(&o);
-        require(o.tol > 0 && o.tol < 1, "tol must be in (0,1)");
-        require(o.restart >= 1 && o.restart <= 120, "restart must be in [1,120]");
-        require(o.n_s >= 0 && o.n_s <= 16, "n_s must be in [0,16]");
-        // N_s = 2 for periodic problems (Sec. VII.A); near no-slip walls the
-        // projection preconditioner is further from the Stokes inverse and
-        // N_s = 4 is the robust choice (Sec. VII.A)
-        if (o.n_s == 0) o.n_s = G->walls() ? 4 : 2;
-        require(o.max_iters >= 1, "max_iters must be >= 1");
-        require(o.variant == IBR_PC_LOWER || o.variant == IBR_PC_FULL, "bad variant");
-        require(o.mg_pre >= 0 && o.mg_post >= 0 && o.mg_pre + o.mg_post >= 1, "bad mg sweeps");
-        cudaStream_t s = G->stream;
-        double t0 = now_ms();
-        if (G->dirty || !mob_opts_equal(o, G->prepared_opts)) prepare(G, o);
-        ensure_pc(G, o.n_s);
-        ensure_outer(G, o.restart);
-        double t1 = now_ms();
-        int B = (int)G->bodies.size();
-        int nuo = B * (G->d + G->rot());
-        for (int i = 0; i < nuo; ++i)
-            if (!std::isfinite(body_UO[i])) throw Error{IBR_ENUMERIC, "body_UO contains NaN/Inf"};
-        // prescribed bodies' velocities (free bodies' rows zeroed: their markers
-        // have W = 0) and free bodies' loads
-        std::vector<double> uo(body_UO, body_UO + nuo), load;
-        int nr = G->d + G->rot();
-        for (int bi = 0; bi < B; ++bi)
-            if (G->bfree[bi] >= 0) {
-                load.insert(load.end(), uo.begin() + bi * nr, uo.begin() + (bi + 1) * nr);
-                std::fill(uo.begin() + bi * nr, uo.begin() + (bi + 1) * nr, 0.0);
-            }
-        IBR_CUDA_TRY(cudaMemcpyAsync(G->UO, uo.data(), nuo * sizeof(double), cudaMemcpyHostToDevice, s));
-        // b = [g; 0; W = -K U; F]
-        long long nS = G->nS;
-        IBR_CUDA_TRY(cudaMemsetAsync(G->b, 0, nS * sizeof(double), s));
-        if (gforce) {
-            size_t bytes = (size_t)G->d * G->geo.ncell * sizeof(double);
-            IBR_CUDA_TRY(cudaMemcpyAsync(G->b, gforce, bytes,
-                                         g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        }
-        rigid_K(G->d, G->N, G->md.rel, G->md.body, G->UO, G->b + nS, -1.0, s);
-        if (G->walls()) {
-            // no net flux through the walls (solvability of the divergence rows)
-            double flux = 0.0, scale = 0.0;
-            for (int a = 0; a < G->d; ++a) {
-                if (!((G->geo.wall >> a) & 1)) continue;
-                const long long nf = G->face_points(a);
-                const double* lo = G->wdata_host[2 * a].data() + (size_t)a * nf;
-                const double* hi = G->wdata_host[2 * a + 1].data() + (size_t)a * nf;
-                for (long long t = 0; t < nf; ++t) {
-                    flux += hi[t] - lo[t];
-                    scale += std::fabs(hi[t]) + std::fabs(lo[t]);
-                }
-            }
-            require(std::fabs(flux) <= 1e-10 * scale, "the wall velocities have a net flux (inflow != outflow)");
-            for (int a = 0; a < G->d; ++a)
-                if ((G->geo.wall >> a) & 1)
-                    for (int sd = 0; sd < 2; ++sd) wall_lift(G->geo, a, sd, G->wdata[2 * a + sd], G->b, G->eta, s);
-        }
-        if (G->nfree > 0)
-            IBR_CUDA_TRY(cudaMemcpyAsync(G->b + nS + (long long)G->N * G->d, load.data(),
-                                         load.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        auto setup_pc = [&](auto* pc) {
-            pc->ns = o.n_s;
-            pc->pre = o.mg_pre;
-            pc->post = o.mg_post;
-            pc->variant = o.variant;
-            pc->ps_count = 0;
-        };
-        if (G->precision == IBR_FP64) {
-            setup_pc(G->pc64);
-            G->pc64->Minv = G->Minv64;
-            G->pc64->setup_free();
-        } else {
-            setup_pc(G->pc32);
-            G->pc32->Minv = G->Minv32;
-            G->pc32->setup_free();
-        }
-        status = fgmres(G, o, info);
-        if (G->walls())
-            for (int a = 0; a < G->d; ++a)
-                if ((G->geo.wall >> a) & 1) wall_set_faces(G->geo, a, G->wdata[2 * a], G->x, s);
-        IBR_CUDA_TRY(cudaStreamSynchronize(s));
-        double t2 = now_ms();
-        info.ms_setup = t1 - t0;
-        info.ms_solve = t2 - t1;
-        info.ps_applications =
-            (int)(G->precision == IBR_FP64 ? G->pc64->ps_count : G->pc32->ps_count);
-        G->have_solution = true;
+        status = solve_core(G, body_UO, gforce, g_on_device, opts, info, false);
     });
     if (rc == IBR_OK && status != IBR_OK) {
         rc = status;
@@ -1295,6 +1329,100 @@ int ibr_solve_coupled(ibr_grid* G, const double* body_UO, const double* gforce, 
     info.status = rc;
     if (info_out) *info_out = info;
     return rc;
+}
+
+int ibr_set_velocity(ibr_grid* G, const double* v, int on_device) {
+    return run_guarded("ibr_set_velocity", [&] {
+        require(G && v, "grid and v must be non-NULL");
+        ibr_solve_opts o = G->prepared_opts;
+        ensure_state(G, o);
+        cudaStream_t s = G->stream;
+        const long long m = (long long)G->d * G->geo.ncell;
+        IBR_CUDA_TRY(cudaMemsetAsync(G->x, 0, G->len * sizeof(double), s));
+        IBR_CUDA_TRY(cudaMemcpyAsync(G->x, v, m * sizeof(double),
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        for (int a = 0; a < G->d; ++a)
+            if ((G->geo.wall >> a) & 1) wall_set_faces(G->geo, a, G->wdata[2 * a], G->x, s);
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        G->have_solution = true;
+        G->adv_hist = false;
+    });
+}
+
+int ibr_advance(ibr_grid* G, const double* body_UO, const double* gforce, int g_on_device, int nsteps,
+                double steady_tol, const ibr_solve_opts* opts, ibr_step_info* out) {
+    ibr_step_info si;
+    std::memset(&si, 0, sizeof(si));
+    int status = IBR_OK;
+    double t0 = now_ms();
+    int rc = run_guarded("ibr_advance", [&] {
+        require(G && body_UO, "grid and body_UO must be non-NULL");
+        require(!G->steady(), "time stepping needs rho > 0 and dt > 0");
+        require(nsteps >= 1, "nsteps must be >= 1");
+        require(steady_tol >= 0.0, "steady_tol must be >= 0");
+        ibr_solve_opts o;
+        if (opts)
+            o = *opts;
+        else
+            opts_default(&o);
+        ensure_state(G, o);
+        cudaStream_t s = G->stream;
+        const Geo& g = G->geo;
+        const long long m = (long long)G->d * g.ncell;
+        if (gforce) {
+            if (!G->adv_f) G->adv_f = dalloc<double>(m);
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->adv_f, gforce, m * sizeof(double),
+                                         g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        }
+        WallData wd;
+        for (int f = 0; f < 6; ++f) wd.data[f] = G->wdata[f];
+        for (int step = 0; step < nsteps; ++step) {
+            // g = (rho/dt) v^n - rho (3/2 N(v^n) - 1/2 N(v^{n-1})) (+ f); Euler on the first step
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->adv_v, G->x, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            advect(g, G->adv_v, wd, G->adv_N, s);
+            const bool ab2 = G->adv_hist;
+            step_force(m, G->adv_v, G->adv_N, ab2 ? G->adv_Np : G->adv_N, gforce ? G->adv_f : nullptr, G->sigma(),
+                       G->rho * (ab2 ? 1.5 : 1.0), G->rho * (ab2 ? -0.5 : 0.0), G->adv_g, s);
+            ibr_solve_info info;
+            std::memset(&info, 0, sizeof(info));
+            status = solve_core(G, body_UO, G->adv_g, 1, &o, info, true);
+            si.steps = step + 1;
+            si.iters_total += info.iters;
+            si.iters_last = info.iters;
+            si.rel_res_last = info.rel_res_true;
+            // ||v^{n+1} - v^n|| / ||v^{n+1}||
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->adv_g, G->x, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            vec_axpby<double>(m, -1.0, G->adv_v, 1.0, G->adv_g, s);
+            norm2<double>(m, G->adv_g, G->partial, G->sc + 4, s);
+            norm2<double>(m, G->x, G->partial, G->sc + 5, s);
+            IBR_CUDA_TRY(cudaMemcpyAsync(G->host_sc + 4, G->sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            IBR_CUDA_TRY(cudaStreamSynchronize(s));
+            const double num = std::sqrt(G->host_sc[4]), den = std::sqrt(G->host_sc[5]);
+            si.change = den > 0.0 ? num / den : 0.0;
+            std::swap(G->adv_N, G->adv_Np);
+            G->adv_hist = true;
+            if (status != IBR_OK) break;
+            if (si.change <= steady_tol) break;
+        }
+    });
+    if (rc == IBR_OK && status != IBR_OK) {
+        rc = status;
+        ibr::set_error(status == IBR_ENOTCONV ? "ibr_advance: a step's solve reached max_iters"
+                                              : "ibr_advance: a step's solve reached the time cap");
+    }
+    si.status = rc;
+    si.ms = now_ms() - t0;
+    if (out) *out = si;
+    return rc;
+}
+
+int ibr_op_advect(ibr_grid* G, const double* v, double* N) {
+    return run_guarded("ibr_op_advect", [&] {
+        require(G && v && N, "grid, v, N must be non-NULL");
+        WallData wd;
+        for (int f = 0; f < 6; ++f) wd.data[f] = G->wdata[f];
+        advect(G->geo, v, wd, N, G->stream);
+    });
 }
 
 int ibr_get_forces(ibr_grid* G, double* Lambda, double* body_FT) {
@@ -1489,6 +1617,7 @@ int ibr_destroy_grid(ibr_grid* G) {
         dfree(G->info_dev);
         if (G->host_sc) cudaFreeHost(G->host_sc);
         for (double* p : G->wdata) dfree(p);
+        for (double** p : {&G->adv_v, &G->adv_N, &G->adv_Np, &G->adv_g, &G->adv_f}) dfree(*p);
         if (G->own_stream) cudaStreamDestroy(G->stream);
         delete G;
     });
