@@ -414,6 +414,259 @@ __global__ void k_scale_rsqrt(long long n, const double* __restrict__ nrm2, cons
     }
 }
 
+
+// ---- the outer FGMRES basis in double-float -------------------------------
+// V is stored as pairs of floats (value = hi + lo, a 48-bit significand) and
+// its Gram-Schmidt dot products and updates run on the FP32 pipe with the
+// error-free transformations of Knuth (two-sum) and of the fused multiply-add
+// (two-product): on this part the FP64 pipe is ~1/60 of the FP32 pipe, so FP64
+// dot and update passes were bound by FP64 arithmetic instead of HBM.  The
+// vectors that build the solution (Z, x) stay FP64.
+__device__ __forceinline__ dflt df_from(double x) {
+    const float h = __double2float_rn(x);
+    dflt r;
+    r.hi = h;
+    r.lo = __double2float_rn(x - (double)h);
+    return r;
+}
+__device__ __forceinline__ double df_to(dflt a) { return (double)a.hi + (double)a.lo; }
+// s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// renormalise (|a| >= |b|)
+__device__ __forceinline__ dflt quick_two_sum(float a, float b) {
+    dflt r;
+    r.hi = __fadd_rn(a, b);
+    r.lo = __fsub_rn(b, __fsub_rn(r.hi, a));
+    return r;
+}
+// a * b + c
+__device__ __forceinline__ dflt df_fma(dflt a, dflt b, dflt c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    float s, e;
+    two_sum(p, c.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(pe, c.lo));
+    return quick_two_sum(s, e);
+}
+// a - b
+__device__ __forceinline__ dflt df_sub(dflt a, dflt b) {
+    float s, e;
+    two_sum(a.hi, -b.hi, s, e);
+    e = __fadd_rn(e, __fsub_rn(a.lo, b.lo));
+    return quick_two_sum(s, e);
+}
+__device__ __forceinline__ dflt df_zero() {
+    dflt r;
+    r.hi = 0.f;
+    r.lo = 0.f;
+    return r;
+}
+
+// The basis kernels below work on pairs of entries (one 16-byte load each):
+// n2 = number of pairs, ld2 = leading dimension in pairs (the basis is
+// allocated with an even length, its pad entry zero).  Loads of the next
+// pair are issued before the arithmetic on the current one, and sums over
+// basis vectors use independent partial accumulators, so that enough bytes
+// are in flight per SM to stream at HBM speed.
+__device__ __forceinline__ void ld_pair(const dflt* __restrict__ p, long long q, dflt& a, dflt& b) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p) + q);
+    a.hi = v.x;
+    a.lo = v.y;
+    b.hi = v.z;
+    b.lo = v.w;
+}
+__device__ __forceinline__ void ld_pair_rw(const dflt* p, long long q, dflt& a, dflt& b) {
+    const float4 v = reinterpret_cast<const float4*>(p)[q];
+    a.hi = v.x;
+    a.lo = v.y;
+    b.hi = v.z;
+    b.lo = v.w;
+}
+__device__ __forceinline__ void st_pair(dflt* p, long long q, dflt a, dflt b) {
+    reinterpret_cast<float4*>(p)[q] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return quick_two_sum(s, e);
+}
+
+// w (FP64, n entries) -> double-float in place (same 8 bytes per entry): the
+// one pass per Arnoldi step that uses the FP64 pipe
+__global__ void k_to_df(long long n, double* w) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const dflt v = df_from(w[i]);
+        reinterpret_cast<dflt*>(w)[i] = v;
+    }
+}
+
+// partial[blk*(k+1) + j] = V_j . w (j < k) and w . w (j == k)
+__global__ void __launch_bounds__(RED_THREADS) k_df_mdot_norm(long long n2, const dflt* __restrict__ V, long long ld2,
+                                                              int k, const dflt* __restrict__ w,
+                                                              double* __restrict__ partial,
+                                                              const double* __restrict__ st) {
+    if (st && st[1] == 0.0) return;
+    const int K1 = k + 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int j0 = 0; j0 < K1; j0 += MDOT_CHUNK) {
+        const int nv = min(MDOT_CHUNK, k - j0);  // basis vectors in this chunk (may be <= 0)
+        const bool with_norm = j0 + MDOT_CHUNK >= K1;
+        dflt acc[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = df_zero();
+        dflt cv[MDOT_CHUNK][2], cw[2];
+        long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (p < n2) {
+            ld_pair(w, p, cw[0], cw[1]);
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q)
+                if (q < nv) ld_pair(V, (long long)(j0 + q) * ld2 + p, cv[q][0], cv[q][1]);
+        }
+        while (p < n2) {
+            const long long pn = p + stride;
+            dflt nv2[MDOT_CHUNK][2], nw[2];
+            if (pn < n2) {
+                ld_pair(w, pn, nw[0], nw[1]);
+#pragma unroll
+                for (int q = 0; q < MDOT_CHUNK; ++q)
+                    if (q < nv) ld_pair(V, (long long)(j0 + q) * ld2 + pn, nv2[q][0], nv2[q][1]);
+            }
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q) {
+                if (q < nv) {
+                    acc[q] = df_fma(cv[q][0], cw[0], acc[q]);
+                    acc[q] = df_fma(cv[q][1], cw[1], acc[q]);
+                } else if (q == nv && with_norm) {
+                    acc[q] = df_fma(cw[0], cw[0], acc[q]);
+                    acc[q] = df_fma(cw[1], cw[1], acc[q]);
+                }
+            }
+            if (pn < n2) {
+                cw[0] = nw[0];
+                cw[1] = nw[1];
+#pragma unroll
+                for (int q = 0; q < MDOT_CHUNK; ++q) {
+                    cv[q][0] = nv2[q][0];
+                    cv[q][1] = nv2[q][1];
+                }
+            }
+            p = pn;
+        }
+        double out[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) out[q] = df_to(acc[q]);
+        __shared__ double outv[MDOT_CHUNK];
+        block_sum<MDOT_CHUNK>(out, outv);
+        const int nq = min(MDOT_CHUNK, K1 - j0);
+        if (threadIdx.x < nq) partial[(long long)blockIdx.x * K1 + j0 + threadIdx.x] = outv[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// s = sum_{j<k} hs_j V_j at pair q: 8 vectors per trip, loads issued together,
+// four independent partial sums
+__device__ __forceinline__ void df_combo_pair(const dflt* __restrict__ V, long long ld2, int k, const dflt* hs,
+                                              long long q, dflt& s0, dflt& s1) {
+    dflt a[4][2];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t][0] = a[t][1] = df_zero();
+    int j = 0;
+    for (; j + 8 <= k; j += 8) {
+        dflt v[8][2];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ld_pair(V, (long long)(j + u) * ld2 + q, v[u][0], v[u][1]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            a[u & 3][0] = df_fma(hs[j + u], v[u][0], a[u & 3][0]);
+            a[u & 3][1] = df_fma(hs[j + u], v[u][1], a[u & 3][1]);
+        }
+    }
+    for (; j < k; ++j) {
+        dflt v0, v1;
+        ld_pair(V, (long long)j * ld2 + q, v0, v1);
+        a[0][0] = df_fma(hs[j], v0, a[0][0]);
+        a[0][1] = df_fma(hs[j], v1, a[0][1]);
+    }
+    s0 = df_add(df_add(a[0][0], a[1][0]), df_add(a[2][0], a[3][0]));
+    s1 = df_add(df_add(a[0][1], a[1][1]), df_add(a[2][1], a[3][1]));
+}
+
+// second Gram-Schmidt pass (only when st[1] != 0): w <- w - V h
+__global__ void __launch_bounds__(RED_THREADS) k_df_sub(long long n2, const dflt* __restrict__ V, long long ld2, int k,
+                                                        const double* __restrict__ h, dflt* __restrict__ w,
+                                                        const double* __restrict__ st) {
+    if (st[1] == 0.0) return;
+    __shared__ dflt hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = df_from(h[j]);
+    __syncthreads();
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
+         p += (long long)gridDim.x * blockDim.x) {
+        dflt s0, s1, w0, w1;
+        ld_pair_rw(w, p, w0, w1);
+        df_combo_pair(V, ld2, k, hs, p, s0, s1);
+        st_pair(w, p, df_sub(w0, s0), df_sub(w1, s1));
+    }
+}
+
+// V_k = (w - V hsel) / sqrt(st[2]) (hsel = st[1] ? h2 : h1); out32[i] (i <
+// n32) its float value, out64[i] (from64 <= i < n64) its FP64 value
+__global__ void __launch_bounds__(RED_THREADS) k_df_normalize(long long n2, const dflt* __restrict__ V, long long ld2,
+                                                              int k, const double* __restrict__ h1,
+                                                              const double* __restrict__ h2,
+                                                              const double* __restrict__ st,
+                                                              const dflt* __restrict__ w, dflt* __restrict__ vout,
+                                                              float* __restrict__ out32, long long n32,
+                                                              double* __restrict__ out64, long long from64,
+                                                              long long n64) {
+    __shared__ dflt hs[128];
+    const double* h = st[1] != 0.0 ? h2 : h1;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = df_from(h[j]);
+    __syncthreads();
+    const double nu = sqrt(st[2]);
+    const dflt inv = df_from(nu > 0.0 ? 1.0 / nu : 0.0);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
+         p += (long long)gridDim.x * blockDim.x) {
+        dflt s0, s1, w0, w1;
+        ld_pair(w, p, w0, w1);
+        df_combo_pair(V, ld2, k, hs, p, s0, s1);
+        const dflt v0 = df_fma(df_sub(w0, s0), inv, df_zero());
+        const dflt v1 = df_fma(df_sub(w1, s1), inv, df_zero());
+        st_pair(vout, p, v0, v1);
+        const long long i = 2 * p;
+        if (out32) {
+            if (i < n32) out32[i] = v0.hi;
+            if (i + 1 < n32) out32[i + 1] = v1.hi;
+        }
+        if (out64) {
+            if (i >= from64 && i < n64) out64[i] = df_to(v0);
+            if (i + 1 >= from64 && i + 1 < n64) out64[i + 1] = df_to(v1);
+        }
+    }
+}
+
+// V_0 = x / sqrt(*nrm2) in double-float (n entries, even), with the same copies
+__global__ void k_df_scale(long long n, const double* __restrict__ nrm2, const double* __restrict__ x,
+                           dflt* __restrict__ vout, float* __restrict__ out32, long long n32,
+                           double* __restrict__ out64, long long from64, long long n64) {
+    const double nr = sqrt(fmax(*nrm2, 0.0));
+    const dflt a = df_from(nr > 0.0 ? 1.0 / nr : 0.0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const dflt v = df_fma(df_from(x[i]), a, df_zero());
+        vout[i] = v;
+        if (out32 && i < n32) out32[i] = v.hi;
+        if (out64 && i >= from64 && i < n64) out64[i] = df_to(v);
+    }
+}
+
 }  // namespace
 
 template <typename T, typename T2>
@@ -454,6 +707,59 @@ template <typename T, typename T2>
 void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s) {
     ProfScope ps(KID_SCALE, s, 2.0 * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
     k_scale_rsqrt<T, T2><<<blocks_for(n), 256, 0, s>>>(n, nrm2, x, y, out2, n2);
+    IBR_CHECK_LAUNCH();
+}
+
+
+void cgs_orthonormalize_df(long long n, long long n_real, const dflt* V, long long ld, int k, double* w, dflt* vout,
+                           float* out32, long long n32, double* out64, long long from64, double* partial, double* h1,
+                           double* h2, double* hk2, double* st, cudaStream_t s) {
+    if ((n & 1) || (ld & 1) || n_real > n)
+        throw Error{IBR_EINVAL, "double-float basis: length and leading dimension must be even"};
+    dflt* wd = reinterpret_cast<dflt*>(w);
+    const long long n2 = n / 2, ld2 = ld / 2;
+    {
+        ProfScope ps(KID_CONVERT, s, 2.0 * n * 8.0);
+        k_to_df<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        ProfScope ps(KID_MDOT, s, (k + 1.0) * n * 8.0);
+        k_df_mdot_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, wd, partial, nullptr);
+        IBR_CHECK_LAUNCH();
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, h1);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        ProfScope ps(KID_SMALL, s, 0.0);
+        k_cgs_state<<<1, 1, 0, s>>>(h1, k, st, h2);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        // second pass, skipped inside the kernels unless st[1] != 0
+        ProfScope ps(KID_UPD_MDOT, s, (2.0 * k + 3.0) * n * 8.0);
+        k_df_sub<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, h1, wd, st);
+        IBR_CHECK_LAUNCH();
+        k_df_mdot_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, wd, partial, st);
+        IBR_CHECK_LAUNCH();
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, hk2);
+        IBR_CHECK_LAUNCH();
+        k_cgs_state2<<<1, 1, 0, s>>>(hk2, k, st, h2);
+        IBR_CHECK_LAUNCH();
+    }
+    {
+        ProfScope ps(KID_UPD_NORM, s,
+                     (k + 2.0) * n * 8.0 + (out32 ? 4.0 * n32 : 0.0) + (out64 ? 8.0 * (n_real - from64) : 0.0));
+        k_df_normalize<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, h1, h2, st, wd, vout, out32, n32, out64,
+                                                          from64, n_real);
+        IBR_CHECK_LAUNCH();
+    }
+}
+
+void scale_df(long long n, long long n_real, const double* nrm2, const double* x, dflt* vout, float* out32,
+              long long n32, double* out64, long long from64, cudaStream_t s) {
+    ProfScope ps(KID_SCALE, s, 16.0 * n);
+    k_df_scale<<<blocks_for(n), 256, 0, s>>>(n, nrm2, x, vout, out32, n32, out64, from64, n_real);
     IBR_CHECK_LAUNCH();
 }
 

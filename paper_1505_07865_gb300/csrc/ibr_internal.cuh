@@ -217,6 +217,25 @@ void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* v
 template <typename T, typename T2>
 void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s);
 
+// The outer FGMRES basis in double-float: value = hi + lo (48-bit
+// significand), 8 bytes per entry like FP64; its Gram-Schmidt passes run on
+// the FP32 pipe (error-free two-sum / two-product).
+struct __align__(8) dflt {
+    float hi, lo;
+};
+// cgs_orthonormalize for a double-float basis V and an FP64 w (converted to
+// double-float in place, w's contents are consumed): the same passes and
+// outputs (h1, h2, hk2, st), vout = the new basis vector; out32
+// (first n32 entries, float) and out64 (entries from64..n_real-1, FP64)
+// copies of it for the preconditioner (either may be NULL).  n and ld even
+// (entries n_real..n-1 are a zero pad of w and of every basis vector).
+void cgs_orthonormalize_df(long long n, long long n_real, const dflt* V, long long ld, int k, double* w, dflt* vout,
+                           float* out32, long long n32, double* out64, long long from64, double* partial, double* h1,
+                           double* h2, double* hk2, double* st, cudaStream_t s);
+// vout = x / sqrt(*nrm2) in double-float (n entries), with the same copies
+void scale_df(long long n, long long n_real, const double* nrm2, const double* x, dflt* vout, float* out32,
+              long long n32, double* out64, long long from64, cudaStream_t s);
+
 // small single-thread kernels for the Arnoldi/Givens bookkeeping (FP64)
 // H column j (k = j+2 entries) assembled from h1 + h2 and the norm; Givens
 // rotations applied, new rotation formed, res_out = |g[j+1]|.

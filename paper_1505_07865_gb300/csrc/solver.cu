@@ -161,7 +161,9 @@ struct ibr_grid {
     // outer FGMRES workspace
     int m_alloc = 0;
     long long len_alloc = 0;
-    double *V = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *w = nullptr;
+    // V: the basis in double-float (dflt, 8 bytes per entry); vk64: the FP64
+    // copy of the current basis vector that the preconditioner reads
+    double *V = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *w = nullptr, *vk64 = nullptr;
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
     double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr, *shift = nullptr, *means = nullptr;
     double *hk2 = nullptr, *st = nullptr;
@@ -185,6 +187,7 @@ struct ibr_grid {
     // periodic steady Stokes: <v> = 0 is part of the problem and S~ = S - vol^-1 1^T
     bool null_v() const { return steady() && !walls(); }
     long long face_points(int a) const { return geo.ncell / n[a]; }
+    long long len_pad() const { return (len + 1) & ~1LL; }
     // time stepping (ibr_advance): v^n, N(v^n), N(v^{n-1}), the step forcing,
     // the constant body force; hist: N(v^{n-1}) is valid (AB2 from then on)
     double *adv_v = nullptr, *adv_N = nullptr, *adv_Np = nullptr, *adv_g = nullptr, *adv_f = nullptr;
@@ -526,9 +529,10 @@ void free_markers(ibr_grid* G) {
 
 void free_outer(ibr_grid* G) {
     double** ps[] = {&G->V, &G->Z, &G->b, &G->x, &G->w, &G->H, &G->cs, &G->sn, &G->gv, &G->yv,
-                     &G->h1, &G->h2, &G->sc, &G->partial, &G->shift, &G->means, &G->hk2, &G->st};
+                     &G->h1, &G->h2, &G->sc, &G->partial, &G->shift, &G->means, &G->hk2, &G->st, &G->vk64};
     for (double** p : ps) dfree(*p);
     G->m_alloc = 0;
+    G->have_solution = false;  // x is gone
 }
 
 // fill default options
@@ -849,11 +853,16 @@ void ensure_outer(ibr_grid* G, int m) {
     if (G->m_alloc >= m && G->V && G->len_alloc == G->len) return;
     free_outer(G);
     long long len = G->len;
-    G->V = dalloc<double>((size_t)(m + 1) * len);
+    // the double-float basis is read in pairs: an even leading dimension,
+    // and w carries the same zero pad entry
+    const long long lp = G->len_pad();
+    G->V = dalloc<double>((size_t)(m + 1) * lp);
+    G->vk64 = dalloc<double>(len);
     G->Z = dalloc<double>((size_t)m * len);
     G->b = dalloc<double>(len);
     G->x = dalloc<double>(len);
-    G->w = dalloc<double>(len);
+    G->w = dalloc<double>(lp);
+    IBR_CUDA_TRY(cudaMemsetAsync(G->w, 0, lp * sizeof(double), G->stream));
     G->H = dalloc<double>((size_t)(m + 1) * (m + 1));
     G->cs = dalloc<double>(m + 1);
     G->sn = dalloc<double>(m + 1);
@@ -987,16 +996,20 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
         // V_0 = r / |r|; in mixed precision the preconditioner's FP32 copy of
         // its fluid part is written by the same pass
         float* rs32 = G->precision == IBR_MIXED ? G->pc32->rs : nullptr;
-        scale_rsqrt<double, float>(len, G->sc + 0, G->w, G->V, rs32, G->nS, s);
+        // the preconditioner reads the fluid part from rs32 (mixed) or vk64
+        // (FP64), the constraint part from vk64
+        const long long from64 = rs32 ? G->nS : 0;
+        dflt* Vd = reinterpret_cast<dflt*>(G->V);
+        const long long lp = G->len_pad();
+        scale_df(lp, len, G->sc + 0, G->w, Vd, rs32, G->nS, G->vk64, from64, s);
         int k = 0;
         last_cycle_converged_est = false;
         for (int j = 0; j < m; ++j) {
-            double* Vj = G->V + (long long)j * len;
             double* Zj = G->Z + (long long)j * len;
-            pc_apply(G, Vj, Zj, true);
+            pc_apply(G, G->vk64, Zj, true);
             full_matvec(G, Zj, G->w);
-            cgs_orthonormalize<double, float>(len, G->V, len, j + 1, G->w, G->V + (long long)(j + 1) * len, rs32,
-                                              G->nS, G->partial, G->h1, G->h2, G->hk2, G->st, s);
+            cgs_orthonormalize_df(lp, len, Vd, lp, j + 1, G->w, Vd + (long long)(j + 1) * lp, rs32, G->nS, G->vk64,
+                                  from64, G->partial, G->h1, G->h2, G->hk2, G->st, s);
             arnoldi_column(G->H, m + 1, G->h1, G->h2, G->st + 2, j, G->cs, G->sn, G->gv, G->sc + 3, G->sc + 4, s);
             k = j + 1;
             info.iters++;
