@@ -12,6 +12,8 @@
 // The kernels are templated on W (some axis has walls); the W = false
 // instances are the plain wrapped stencils.  Boundary data enters only the
 // right-hand side (wall_lift).
+#include <algorithm>
+
 #include "ibr_internal.cuh"
 
 namespace ibr {
@@ -441,6 +443,42 @@ __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __rest
                        2 * ih + ((j + k + color) & 1), j, k);
 }
 
+// the same half sweep on a periodic 3-D grid, each thread a column of kz
+// cells along z at fixed (ih, j): the y wrap and the block decomposition
+// are paid once per column, the cells of a column are independent (one
+// colour) so their loads overlap.  Same arithmetic and summation order as
+// rbgs_cell, so the result is bitwise that of k_rbgs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rbgs_col(T* __restrict__ u, const T* __restrict__ f, Geo g, int nkb, int kz,
+                                                  T kh2, T inv_diag, int color, int zero_init) {
+    const int ih = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int cmp = blockIdx.z / nkb, kb = blockIdx.z - cmp * nkb;
+    if (ih >= (g.n0 >> 1) || j >= g.n1) return;
+    const long long off = (long long)cmp * g.ncell;
+    u += off;
+    f += off;
+    const int n0 = g.n0, n1 = g.n1, n2 = g.n2;
+    const int sy = n0, sz = n0 * n1;
+    const int yp = (j == n1 - 1) ? (1 - n1) * sy : sy;
+    const int ym = (j == 0) ? (n1 - 1) * sy : -sy;
+    const int k0 = kb * kz, k1 = min(k0 + kz, n2);
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+        const int i = 2 * ih + ((j + k + color) & 1);
+        const int c = i + sy * j + sz * k;
+        const int xp = (i == n0 - 1) ? 1 - n0 : 1;
+        const int xm = (i == 0) ? n0 - 1 : -1;
+        const int zp = (k == n2 - 1) ? (1 - n2) * sz : sz;
+        const int zm = (k == 0) ? (n2 - 1) * sz : -sz;
+        T nb = T(0);
+        if (!zero_init) {
+            nb = u[c + xp] + u[c + xm] + u[c + yp] + u[c + ym];
+            nb += u[c + zp] + u[c + zm];
+        }
+        u[c] = (f[c] + kh2 * nb) * inv_diag;
+    }
+}
+
 template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
                                                         T* __restrict__ fc, Geo gf, Geo gc, int fld0, T sigma,
@@ -733,10 +771,16 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, do
     const T sg = (T)sigma;
     if (g.d == 3) {
         T inv = rbgs_inv_diag<3, T>(sg, kh2);
-        if (g.wall)
+        if (g.wall) {
             k_rbgs<3, true, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
-        else
-            k_rbgs<3, false, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+        } else {
+            // columns of kz cells; kz shrinks on small levels to keep ~1.5e5 threads busy
+            const long long cells = (long long)(g.n0 >> 1) * g.n1 * g.n2 * C;
+            int kz = (int)std::min<long long>(8, std::max<long long>(1, cells / 150000));
+            const int nkb = (g.n2 + kz - 1) / kz;
+            dim3 gc(((g.n0 >> 1) + BX - 1) / BX, (g.n1 + BY - 1) / BY, nkb * C);
+            k_rbgs_col<T><<<gc, blk, 0, s>>>(u, f, g, nkb, kz, kh2, inv, color, zi);
+        }
     } else {
         T inv = rbgs_inv_diag<2, T>(sg, kh2);
         if (g.wall)
