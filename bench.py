@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--quick", action="store_true",
                     help="mixed-precision arm only (no profile, e2e, FP64 or CPU legs); for profiler runs")
+    ap.add_argument("--workload", default="sphere128", choices=["sphere128", "nozzle"],
+                    help="nozzle: the 256x128 nozzle time stepping (its own JSON line; not the headline)")
+    ap.add_argument("--re", type=float, default=10.0, help="Reynolds number of the nozzle workload")
     return ap.parse_args()
 
 
@@ -380,11 +383,80 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_nozzle(args):
+    """Time steps of the 256x128 nozzle (one constrained solve per step, mixed
+    precision, the precomputed true mobility as the Schur block): the steady
+    Stokes flow first (its largest speed fixes dt = 0.5 h / u_max), then
+    W warm-up steps (including the set-up) and K timed steps from there."""
+    import torch
+    from paper_1505_07865_gb300 import abi
+    from synthetic import nozzle, parabolic_inflow
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    def grid(wl):
+        G = abi.create_grid(2, wl.n, wl.L, bc=[abi.VELOCITY, abi.VELOCITY, abi.NOSLIP, abi.NOSLIP], eta=wl.eta,
+                            rho=wl.rho, dt=wl.dt, precision=abi.MIXED, stream=stream.cuda_stream)
+        for s_ in (0, 1):
+            v = np.zeros((2, wl.n[1]))
+            v[0] = parabolic_inflow(wl.n[1])
+            abi.set_boundary_velocity(G, s_, v.ravel())
+        for b in wl.bodies:
+            bid = abi.add_body(G, b.center)
+            abi.set_markers(G, bid, b.rel)
+        return G
+
+    opts = abi.solve_opts_default()
+    opts.tol = TOL
+    opts.mob_model = abi.MOB_TRUE
+    ws = nozzle(Re=0.0)
+    Gs = grid(ws)
+    t0 = time.perf_counter()
+    si = abi.solve_coupled(Gs, ws.UO(), opts=opts, raise_on_notconv=True)
+    stokes_ms = (time.perf_counter() - t0) * 1e3
+    nc = int(np.prod(ws.n))
+    v0 = np.zeros(2 * nc)
+    abi.get_fields(Gs, v0, None)
+    abi.destroy_grid(Gs)
+    u_max = float(np.abs(v0).max())
+    wl = nozzle(Re=args.re, u_max=u_max)
+    G = grid(wl)
+    abi.set_velocity(G, v0)
+    t0 = time.perf_counter()
+    w = abi.advance(G, wl.UO(), max(1, args.warmup), opts=opts, raise_on_notconv=True)
+    warm_ms = (time.perf_counter() - t0) * 1e3
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = abi.launch_count()
+    e0.record(stream)
+    info = abi.advance(G, wl.UO(), args.steps, opts=opts, raise_on_notconv=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = abi.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    abi.destroy_grid(G)
+    out = {"metric": "nozzle time steps/s (one constrained solve to rel. residual 1e-8 per step)",
+           "value": args.steps / (ms / 1e3), "unit": "steps/s", "n_gpus": 1, "steps": info.steps,
+           "warmup": w.steps, "ms_per_step": ms / max(1, info.steps), "higher_is_better": True,
+           "dtype": "f64+f32 (mixed)", "data": "synthetic",
+           "config": {"workload": f"nozzle 256x128, Re={args.re:g}, dt=0.5h/u_max (u_max={u_max:.4f} of the Stokes flow),"
+                                  " 222 markers, true-mobility Schur block"},
+           "iters_per_step": info.iters_total / max(1, info.steps), "change_last_step": info.change,
+           "rel_res_last": info.rel_res_last, "stokes_solve_ms_incl_setup": stokes_ms,
+           "warmup_ms_incl_setup": warm_ms, "gpu_launches": launches}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "nozzle":
+        if rank == 0:
+            run_nozzle(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

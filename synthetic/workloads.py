@@ -199,17 +199,18 @@ def parabolic_inflow(n1, U=1.0):
     return 4.0 * U * y * (1.0 - y)
 
 
-def nozzle(n=(256, 128), Re=0.0, U=1.0):
+def nozzle(n=(256, 128), Re=0.0, U=1.0, u_max=None):
     """2-D nozzle flow: channel [0,2] x [0,1], no-slip at y = 0, 1, parabolic
     inflow/outflow 4 U y (1 - y) at x = 0 and x = 2, two fixed rigid nozzle
     walls (nozzle_walls) forming a throat of width 0.4.  Re = rho U 0.4 / eta
     with rho = 1 (Re = 0: steady Stokes, eta = 1); the time step is
-    0.5 h / U (the inflow peak)."""
+    0.5 h / u_max (u_max: the largest speed of the flow, e.g. of the steady
+    Stokes solution; default U, the inflow peak)."""
     h = 1.0 / n[1]
     bodies = [Body(c, rel, np.zeros(3)) for c, rel in nozzle_walls(h)]
     if Re == 0:
         eta, rho, dt = 1.0, 0.0, 0.0
     else:
-        eta, rho, dt = U * 0.4 / Re, 1.0, 0.5 * h / U
+        eta, rho, dt = U * 0.4 / Re, 1.0, 0.5 * h / (U if u_max is None else u_max)
     return Workload(f"nozzle_{n[0]}x{n[1]}_Re{Re:g}", tuple(n), (2.0, 1.0), eta=eta, rho=rho, dt=dt, bodies=bodies,
                     tol=1e-8, walls=(True, True))
