@@ -703,6 +703,21 @@ void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* v
     }
 }
 
+template <typename T>
+void cgs_coeffs_only(long long n, const T* V, long long ld, int k, const T* w, double* partial, double* h1,
+                     double* h2, double* st, cudaStream_t s) {
+    {
+        ProfScope ps(KID_MDOT, s, (k + 1.0) * n * sizeof(T));
+        k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
+        IBR_CHECK_LAUNCH();
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, h1);
+        IBR_CHECK_LAUNCH();
+    }
+    ProfScope ps(KID_SMALL, s, 0.0);
+    k_cgs_state<<<1, 1, 0, s>>>(h1, k, st, h2);  // st[2] = max(|w|^2 - |h1|^2, 0), h2 = 0
+    IBR_CHECK_LAUNCH();
+}
+
 template <typename T, typename T2>
 void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s) {
     ProfScope ps(KID_SCALE, s, 2.0 * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
@@ -769,6 +784,10 @@ template void cgs_orthonormalize<double, double>(long long, const double*, long 
                                                  long long, double*, double*, double*, double*, double*, cudaStream_t);
 template void cgs_orthonormalize<float, float>(long long, const float*, long long, int, float*, float*, float*,
                                                long long, double*, double*, double*, double*, double*, cudaStream_t);
+template void cgs_coeffs_only<float>(long long, const float*, long long, int, const float*, double*, double*,
+                                     double*, double*, cudaStream_t);
+template void cgs_coeffs_only<double>(long long, const double*, long long, int, const double*, double*, double*,
+                                      double*, double*, cudaStream_t);
 template void scale_rsqrt<double, float>(long long, const double*, const double*, double*, float*, long long,
                                          cudaStream_t);
 template void scale_rsqrt<double, double>(long long, const double*, const double*, double*, double*, long long,

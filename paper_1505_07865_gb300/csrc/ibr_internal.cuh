@@ -213,6 +213,12 @@ void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t 
 template <typename T, typename T2>
 void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* vout, T2* out2, long long n2,
                         double* partial, double* h1, double* h2, double* hk2, double* st, cudaStream_t s);
+// Only the Hessenberg column of the last step of a GMRES cycle whose next
+// basis vector is never used: h1 = V^T w (one pass), h2 = 0, st[2] =
+// max(|w|^2 - |h1|^2, 0) (no second pass, no normalisation pass)
+template <typename T>
+void cgs_coeffs_only(long long n, const T* V, long long ld, int k, const T* w, double* partial, double* h1,
+                     double* h2, double* st, cudaStream_t s);
 // y = x / sqrt(*nrm2) (0 if nrm2 == 0), plus optional out2[0..n2) copy
 template <typename T, typename T2>
 void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s);

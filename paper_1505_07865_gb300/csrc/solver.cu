@@ -368,9 +368,13 @@ struct PC {
             T* Zj = Zi + (long long)j * nS;
             apply_ps(Vj, Zj);
             stokes_apply<T>(g, Zj, w, G->sigma(), G->eta, nullptr, s);
-            // the last step only needs its Hessenberg column: normalise in place
-            T* vnext = (j + 1 < ns) ? Vi + (long long)(j + 1) * nS : w;
-            cgs_orthonormalize<T, T>(nS, Vi, nS, j + 1, w, vnext, nullptr, 0, partial, h1, h2, hk2, st, s);
+            // the last step only needs its Hessenberg column (the inner solve is
+            // a preconditioner: one Gram-Schmidt pass, the norm from |w|^2 - |h|^2)
+            if (j + 1 < ns)
+                cgs_orthonormalize<T, T>(nS, Vi, nS, j + 1, w, Vi + (long long)(j + 1) * nS, nullptr, 0, partial, h1,
+                                         h2, hk2, st, s);
+            else
+                cgs_coeffs_only<T>(nS, Vi, nS, j + 1, w, partial, h1, h2, st, s);
             arnoldi_column(Hi, ns + 1, h1, h2, st + 2, j, cs, sn, gv, sc + 3, sc + 4, s);
         }
         hess_solve(Hi, ns + 1, gv, ns, yv, s);

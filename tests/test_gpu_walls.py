@@ -199,14 +199,14 @@ def test_nozzle_full_size_true_mobility(abi, Re):
     data = _nozzle_data(wl)
     _, vo, po, lo, fo = _oracle_solve(wl, data)
     # steady Stokes in the enclosed channel is ill-conditioned (an error of
-    # ~6e-6 at residual 1e-8, ~600x): there the 1e-7 bar is checked at 1e-10
-    tol = 1e-10 if Re == 0.0 else 1e-8
+    # ~6e-6 at residual 1e-8, ~1e3 x): there the 1e-7 bar is checked at 3e-11
+    tol = 3e-11 if Re == 0.0 else 1e-8
     info, v, p, lam, ft = _gpu_solve(abi, wl, abi.MIXED, tol=tol, data=data, mob_model=abi.MOB_TRUE)
     assert info.status == abi.OK, info.as_dict()
     assert info.rel_res_true <= tol * (1 + 1e-9)
     # steady Stokes in the enclosed channel: P_S is furthest from the Stokes
     # inverse there (the wall-normal pressure Neumann rule), more iterations
-    assert info.iters <= (160 if Re == 0.0 else 40), info.as_dict()
+    assert info.iters <= (200 if Re == 0.0 else 40), info.as_dict()
     for a, b in ((v, vo), (p, po), (lam, lo)):
         assert rel_err(a, b) < 1e-7, info.as_dict()
 
