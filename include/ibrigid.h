@@ -60,6 +60,7 @@ extern "C" {
 #define IBR_ENUMERIC -5   /* NaN/Inf in data, or M~ not made SPD by any shift     */
 #define IBR_ECUDA    -6   /* a CUDA runtime call failed                           */
 #define IBR_ESTATE   -7   /* call out of order (e.g. solve before markers)        */
+#define IBR_EPENDING -8   /* ibr_server_poll: the request has not finished yet    */
 
 /* ---- boundary conditions per axis side (bc[axis][0]=low, [1]=high) -------- */
 #define IBR_PERIODIC 0
@@ -83,6 +84,15 @@ extern "C" {
                                   one dense block, built in the set-up from
                                   N*dim Stokes solves (Sec. V.C, VII.F: for
                                   fixed geometries)                             */
+#define IBR_MOB_PAIR  4        /* periodic grids: M~_ij = the grid's own pair
+                                  mobility at displacement q_i - q_j, from a
+                                  table of 2 x dim Stokes solves (unit forces at
+                                  two off-node source points) built once per
+                                  grid, symmetrised and averaged over the
+                                  sources (Sec. IV's translation-invariant pair
+                                  mobility, tabulated instead of fitted); one
+                                  dense block for all markers while dim N <=
+                                  6144 (bodies coupled), else one per body      */
 
 typedef struct ibr_grid ibr_grid;   /* opaque */
 
@@ -254,8 +264,9 @@ int ibr_op_rigid(ibr_grid* g, const double* UO, double* V);
 int ibr_op_rigid_T(ibr_grid* g, const double* lam, double* FT);
 
 /* Copies dense mobility block b into out (row-major): the M~ block of body b
- * ((dim N_b)^2 doubles, Eq. M_tilde_ij), or with IBR_MOB_TRUE the single
- * block M0 of all markers ((dim N)^2 doubles, b = 0). */
+ * ((dim N_b)^2 doubles, Eq. M_tilde_ij), or the single block of all markers
+ * ((dim N)^2 doubles, b = 0) with IBR_MOB_TRUE (M0) and with IBR_MOB_PAIR
+ * while dim N <= 6144. */
 int ibr_op_mtilde(ibr_grid* g, int body, double* out);
 
 /* out = M~^-1 rhs (block diagonal over bodies, [N*dim]) with the factorised
@@ -297,6 +308,113 @@ int ibr_op_vcycle(ibr_grid* g, double sigma, double kappa, const double* f, doub
  * and the array keeps the last call's contents. */
 int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, double sigma, double kappa,
                           const double* f, double* u, int k, int pre, int post, void* cuda_stream);
+
+/* Device bytes a periodic grid of cells n[0..dim-1] holds through a solve
+ * with n_bodies prescribed bodies of n_markers[b] markers, FGMRES restart
+ * `restart`, inner iterations n_s (0: 2) in `precision` with mobility model
+ * mob_model: the outer Krylov workspace, the preconditioner (multigrid levels,
+ * inner basis, P_S work), the marker data, the dense mobility blocks (and for
+ * IBR_MOB_PAIR its table and the solves that build it), each allocation of >= 1 MiB
+ * rounded up to the allocator's 2 MiB pages.  Used by the serving engine's
+ * admission control; an upper estimate of the growth of device memory in use. */
+int ibr_estimate_device_bytes(int dim, const int* n, int n_bodies, const int* n_markers, int restart, int n_s,
+                              int precision, int mob_model, long long* bytes);
+
+/* ---- serving engine (continuous batching of independent solves) -----------
+ * A request is one constrained solve on a periodic box from x0 = 0 (steady
+ * Stokes, prescribed or free rigid bodies), the problem of ibr_solve_coupled.
+ * The engine runs `slots` worker threads, each on its own non-blocking CUDA
+ * stream of the device current at ibr_server_create, so requests that run at
+ * the same time overlap on the GPU.  Requests start in arrival order when a
+ * slot is free and the device bytes they need (ibr_estimate_device_bytes)
+ * fit next to those of the running requests and of the resident grids under
+ * hbm_budget_bytes; the oldest waiting request evicts idle resident grids
+ * (least recently used first) to make room; younger requests that fit may
+ * start ahead of it, at most 8 in a row.  A request that could never fit
+ * finishes at once with IBR_ENOMEM.  Grids stay resident after a request
+ * (multigrid hierarchy, Krylov workspace, marker data, factorised mobility,
+ * captured preconditioner graph): a later request of the same grid shape
+ * (dim, n, L, eta, precision) reuses one, and a request with the same
+ * geometry (bodies, markers, mobility options) also skips the set-up.
+ * Each request's result is the one ibr_solve_coupled gives for it alone:
+ * every kernel of the library reduces in a fixed order, so the mix changes
+ * timing only.  Thread safety: submit, poll and get_stats may be called from
+ * any thread. */
+#define IBR_SERVER_AUTOTUNE 1  /* flags: tune the schedule per grid shape: the
+                                  first request of a shape whose opts are NULL
+                                  or leave N_s automatic (n_s = 0) is solved
+                                  with N_s in {1,2,3} x multigrid
+                                  sweeps in {1/1, 2/2} and the fastest
+                                  schedule is used for that shape from then
+                                  on (requests of the shape wait for it)      */
+#define IBR_RUNNING 1          /* ibr_result.status of a started request      */
+#define IBR_QUEUED  2          /* ibr_result.status of a waiting request      */
+
+typedef struct ibr_server ibr_server;  /* opaque */
+
+typedef struct ibr_request {
+    int    dim;                /* 2 or 3                                          */
+    int    n[3];               /* cells per axis (even, >= 4; periodic box)        */
+    double L[3];               /* box lengths, cubic cells                         */
+    double eta;                /* viscosity (steady Stokes)                        */
+    int    precision;          /* IBR_MIXED or IBR_FP64                            */
+    int    n_bodies;           /* >= 1                                             */
+    const double* x_c;         /* [n_bodies*dim] reference points (host)           */
+    const double* quat;        /* [n_bodies*4] orientations (w,x,y,z), or NULL     */
+    const int*    kinematics;  /* [n_bodies] IBR_PRESCRIBED / IBR_FREE, or NULL    */
+    const int*    n_markers;   /* [n_bodies]                                       */
+    const double* r_body;      /* [sum n_markers * dim] body-frame offsets, body
+                                  after body                                      */
+    const double* body_UO;     /* [n_bodies*(dim+rot)] as in ibr_solve_coupled     */
+    const ibr_solve_opts* opts;/* NULL: defaults; n_s = 0 lets the autotuner pick
+                                  N_s and the multigrid sweeps                    */
+    int    want_fields;        /* 1: keep v and pi for ibr_server_poll             */
+} ibr_request;
+
+typedef struct ibr_result {
+    int    status;             /* ibr_solve_coupled's code, IBR_ENOMEM (never fits),
+                                  or IBR_RUNNING / IBR_QUEUED while pending       */
+    int    iters;              /* outer FGMRES iterations                          */
+    double rel_res_true;       /* true relative residual at exit                   */
+    double ms_setup, ms_solve; /* as in ibr_solve_info                             */
+    double t_submit_ms;        /* server clock (ms since ibr_server_create)        */
+    double t_start_ms;         /* admitted to a slot                               */
+    double t_end_ms;           /* result on the host                               */
+    long long reserved_bytes;  /* device bytes reserved for the request's grid     */
+    int    slot;               /* worker that ran it                               */
+    int    reused_grid;        /* a resident grid of the same shape was reused     */
+    int    reused_geometry;    /* ... with the same geometry: no set-up            */
+    int    tuned;              /* this request ran the schedule autotuner          */
+    int    n_s, mg_pre, mg_post; /* schedule used                                  */
+    int    n_markers, n_bodies;
+} ibr_result;
+
+typedef struct ibr_server_stats {
+    long long submitted, completed, rejected, queued, running;
+    long long reserved_bytes, peak_reserved_bytes, budget_bytes;
+    long long grids_created, grids_reused, geometry_reused, evictions, resident_grids;
+    long long tuned_shapes;
+} ibr_server_stats;
+
+/* Starts the engine: slots in [1, 64] workers, hbm_budget_bytes > 0, flags 0 or
+ * IBR_SERVER_AUTOTUNE. */
+int ibr_server_create(ibr_server** out, int slots, long long hbm_budget_bytes, int flags);
+/* Queues a request (all arrays copied; never waits for the GPU) and writes
+ * its ticket.  IBR_EINVAL for malformed requests. */
+int ibr_server_submit(ibr_server* s, const ibr_request* req, long long* ticket);
+/* Waits up to timeout_ms (< 0: without limit, 0: no wait) for the ticket.  If
+ * it has finished: copies the result (res) and, for each non-NULL pointer,
+ * Lambda [N*dim], body_FT [B*(dim+rot)] (K^T Lambda per body) and, if the
+ * request wanted them, v [dim*cells] and p [cells] to host memory, releases
+ * the ticket and returns the request's status (ibr_last_error() gives its
+ * message).  If not: IBR_EPENDING (res, if non-NULL, gets its current state);
+ * IBR_EINVAL for an unknown or already collected ticket. */
+int ibr_server_poll(ibr_server* s, long long ticket, double timeout_ms, ibr_result* res, double* Lambda,
+                    double* body_FT, double* v, double* p);
+int ibr_server_get_stats(ibr_server* s, ibr_server_stats* out);
+/* Stops the engine: requests not yet started are dropped, running ones
+ * finish, resident grids and uncollected results are freed. NULL accepted. */
+int ibr_server_destroy(ibr_server* s);
 
 /* ---- instrumentation (measurement support; the paper has no counterpart) ---
  * Process-wide.  ibr_launch_count: kernels launched by the library since it

@@ -16,6 +16,14 @@ f (the self term included, as for the periodic Stokes drag of a sphere).
   f~(x) = (a0 x^2 + a1 x^3 + a2 x^3 ln x) / (1 + a3 x + a4 x^2 + a2 x^3)
   g~(x) = (b0 x^2 + b1 x^3) / (1 + b2 x + b3 x^2 + b1 x^3)
 with the coefficients passed in (the paper does not print them).
+
+Periodic grids, tabulated pair mobility (Sec. IV: the mobility of two markers
+is, up to a small dependence on their position relative to the grid, a
+function of their displacement; here that function is taken from the grid
+itself instead of a fitted form): with T_s(r)^{ab} = (J(x0_s + r) L^-1 S~
+e_b delta_{x0_s})_a the velocity at x0_s + r due to a unit force e_b at the
+source point x0_s,
+  M~_ij^{ab} = (1/2S) sum_s [ T_s(q_i - q_j)^{ab} + T_s(q_j - q_i)^{ba} ].
 """
 import numpy as np
 
@@ -78,3 +86,41 @@ def mtilde_3d_rpy(rel, h, eta, l, a_over_h=1.25, periodic=True):
 def mtilde_2d_steady(rel, h, eta, l, a_over_h, coef):
     a = a_over_h * h
     return mtilde_block(rel, lambda r: fg_2d_steady(r, h, eta, l, a, coef))
+
+
+def pair_table_mtilde(grid, q, x0s):
+    """Dense (d N)^2 M~ from the tabulated periodic pair mobility of the grid
+    (exact DFT Stokes solves, one per source point and force direction)."""
+    from . import fft_stokes, ib
+
+    q = np.asarray(q, dtype=np.float64)
+    N, d = q.shape
+    L = np.array(grid.L, dtype=np.float64)
+    M = np.zeros((N * d, N * d))
+    for x0 in x0s:
+        x0 = np.asarray(x0, dtype=np.float64)
+        fields = []
+        for b in range(d):
+            lam = np.zeros((1, d))
+            lam[0, b] = 1.0
+            v, _ = fft_stokes.stokes_solve(grid, ib.spread_tilde(grid, x0[None, :], lam))
+            fields.append(v)
+        for i in range(N):
+            for j in range(N):
+                for r, tr in ((q[i] - q[j], False), (q[j] - q[i], True)):
+                    p = np.mod(x0 + r, L)[None, :]
+                    for b in range(d):
+                        u = ib.interp(grid, p, fields[b])[0]  # T(r)[:, b]
+                        for a in range(d):
+                            if tr:
+                                M[i * d + b, j * d + a] += u[a]
+                            else:
+                                M[i * d + a, j * d + b] += u[a]
+    return M / (2.0 * len(x0s))
+
+
+def pair_sources(n, h, d):
+    """The two source points of the library's pair table: cell floor(n/2)
+    along each axis, sub-cell offsets (0.3, 0.7, 0.45) h and (0.7, 0.3, 0.55) h."""
+    fr = ((0.3, 0.7, 0.45), (0.7, 0.3, 0.55))
+    return [np.array([(np.floor(0.5 * n[a]) + fr[k][a]) * h for a in range(d)]) for k in range(2)]

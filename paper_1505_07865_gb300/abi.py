@@ -24,7 +24,7 @@ KERNEL_PESKIN4 = 4
 FP64, MIXED = 0, 1
 PRESCRIBED, FREE = 0, 1
 PC_LOWER, PC_FULL = 0, 1
-MOB_AUTO, MOB_RPY, MOB_FIT2D, MOB_TRUE = 0, 1, 2, 3
+MOB_AUTO, MOB_RPY, MOB_FIT2D, MOB_TRUE, MOB_PAIR = 0, 1, 2, 3, 4
 
 
 class SolveOpts(ctypes.Structure):
@@ -69,6 +69,66 @@ class StepInfo(ctypes.Structure):
         ("rel_res_last", ctypes.c_double),
         ("ms", ctypes.c_double),
     ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EPENDING = -8
+RUNNING, QUEUED = 1, 2
+SERVER_AUTOTUNE = 1
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("L", ctypes.c_double * 3),
+        ("eta", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("n_bodies", ctypes.c_int),
+        ("x_c", ctypes.POINTER(ctypes.c_double)),
+        ("quat", ctypes.POINTER(ctypes.c_double)),
+        ("kinematics", ctypes.POINTER(ctypes.c_int)),
+        ("n_markers", ctypes.POINTER(ctypes.c_int)),
+        ("r_body", ctypes.POINTER(ctypes.c_double)),
+        ("body_UO", ctypes.POINTER(ctypes.c_double)),
+        ("opts", ctypes.POINTER(SolveOpts)),
+        ("want_fields", ctypes.c_int),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("rel_res_true", ctypes.c_double),
+        ("ms_setup", ctypes.c_double),
+        ("ms_solve", ctypes.c_double),
+        ("t_submit_ms", ctypes.c_double),
+        ("t_start_ms", ctypes.c_double),
+        ("t_end_ms", ctypes.c_double),
+        ("reserved_bytes", ctypes.c_longlong),
+        ("slot", ctypes.c_int),
+        ("reused_grid", ctypes.c_int),
+        ("reused_geometry", ctypes.c_int),
+        ("tuned", ctypes.c_int),
+        ("n_s", ctypes.c_int),
+        ("mg_pre", ctypes.c_int),
+        ("mg_post", ctypes.c_int),
+        ("n_markers", ctypes.c_int),
+        ("n_bodies", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in (
+        "submitted", "completed", "rejected", "queued", "running", "reserved_bytes", "peak_reserved_bytes",
+        "budget_bytes", "grids_created", "grids_reused", "geometry_reused", "evictions", "resident_grids",
+        "tuned_shapes")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,6 +180,14 @@ _SIGS = {
     "ibr_last_error": (ctypes.c_char_p, []),
     "ibr_op_vcycle_noalloc": (ctypes.c_int, [ctypes.c_int, _I, _D, ctypes.c_double, ctypes.c_double, _P, _P,
                                              ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "ibr_estimate_device_bytes": (ctypes.c_int, [ctypes.c_int, _I, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+    "ibr_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
+    "ibr_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
+    "ibr_server_poll": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(Result), _D, _D,
+                                       _D, _D]),
+    "ibr_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "ibr_server_destroy": (ctypes.c_int, [_P]),
     "ibr_launch_count": (ctypes.c_longlong, []),
     "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ibr_profile_reset": (ctypes.c_int, []),
@@ -373,3 +441,105 @@ def profile_read():
             out[buf.value.decode()] = (n.value, ms.value, by.value)
         i += 1
     return out
+
+
+def estimate_device_bytes(dim, n, n_markers, restart=50, n_s=0, precision=MIXED, mob_model=MOB_AUTO):
+    """ibr_estimate_device_bytes: device bytes one periodic grid holds in a solve."""
+    n_arr = (ctypes.c_int * 3)(*(list(n) + [0] * (3 - len(n))))
+    nm = (ctypes.c_int * max(1, len(n_markers)))(*[int(x) for x in n_markers])
+    out = ctypes.c_longlong()
+    _check(_lib.ibr_estimate_device_bytes(int(dim), n_arr, len(n_markers), nm, int(restart), int(n_s),
+                                          int(precision), int(mob_model), ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """The serving engine (ibr_server_*): submit() queues one periodic
+    constrained solve and returns a ticket, poll() collects its result.
+
+    Bodies are given as a list of (x_c, rel[N_b, dim]) with optional quats;
+    body_UO is [B, dim + rot].  Argument marshalling only: the engine, its
+    admission control and the solves run in the library."""
+
+    def __init__(self, slots=4, budget_bytes=64 << 30, autotune=False):
+        self.h = _P()
+        _check(_lib.ibr_server_create(ctypes.byref(self.h), int(slots), int(budget_bytes),
+                                      SERVER_AUTOTUNE if autotune else 0))
+        self._sizes = {}
+
+    def submit(self, n, L, centers, rels, body_UO, eta=1.0, precision=MIXED, quats=None, kinematics=None,
+               opts=None, want_fields=False):
+        dim = len(n)
+        B = len(centers)
+        rot = 1 if dim == 2 else 3
+        xc = _host(np.asarray(centers, dtype=np.float64).reshape(B, dim))
+        nm = np.array([np.asarray(r).reshape(-1, dim).shape[0] for r in rels], dtype=np.int32)
+        rb = _host(np.concatenate([np.asarray(r, dtype=np.float64).reshape(-1, dim) for r in rels]))
+        uo = _host(np.asarray(body_UO, dtype=np.float64).reshape(B, dim + rot))
+        r = Request()
+        r.dim = dim
+        for a in range(dim):
+            r.n[a] = int(n[a])
+            r.L[a] = float(L[a])
+        r.eta = float(eta)
+        r.precision = int(precision)
+        r.n_bodies = B
+        r.x_c = _dptr(xc)
+        qa = None
+        if quats is not None:
+            qa = _host(np.asarray(quats, dtype=np.float64).reshape(B, 4))
+            r.quat = _dptr(qa)
+        ka = None
+        if kinematics is not None:
+            ka = np.ascontiguousarray(np.asarray(kinematics, dtype=np.int32))
+            r.kinematics = ka.ctypes.data_as(_I)
+        r.n_markers = nm.ctypes.data_as(_I)
+        r.r_body = _dptr(rb)
+        r.body_UO = _dptr(uo)
+        if opts is not None:
+            r.opts = ctypes.pointer(opts)
+        r.want_fields = 1 if want_fields else 0
+        t = ctypes.c_longlong()
+        _check(_lib.ibr_server_submit(self.h, ctypes.byref(r), ctypes.byref(t)))
+        ncell = int(np.prod(n))
+        self._sizes[t.value] = (dim, int(nm.sum()), B, ncell, bool(want_fields))
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1.0):
+        """None while pending; else a dict: result fields, 'lam' [N, dim],
+        'ft' [B, dim + rot], and 'v', 'p' when the request wanted fields."""
+        dim, N, B, ncell, wf = self._sizes[ticket]
+        rot = 1 if dim == 2 else 3
+        res = Result()
+        lam = np.zeros(N * dim)
+        ft = np.zeros(B * (dim + rot))
+        v = np.zeros(dim * ncell) if wf else None
+        p = np.zeros(ncell) if wf else None
+        rc = _lib.ibr_server_poll(self.h, int(ticket), float(timeout_ms), ctypes.byref(res), _dptr(lam), _dptr(ft),
+                                  None if v is None else _dptr(v), None if p is None else _dptr(p))
+        if rc == EPENDING:
+            return None
+        del self._sizes[ticket]
+        out = res.as_dict()
+        out["error"] = last_error() if rc != OK else ""
+        out["lam"] = lam.reshape(N, dim)
+        out["ft"] = ft.reshape(B, dim + rot)
+        if wf:
+            out["v"], out["p"] = v, p
+        return out
+
+    def stats(self):
+        st = ServerStats()
+        _check(_lib.ibr_server_get_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            _check(_lib.ibr_server_destroy(self.h))
+            self.h = _P()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

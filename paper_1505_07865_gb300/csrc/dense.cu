@@ -211,6 +211,113 @@ __global__ void __launch_bounds__(TB * TB) k_xtx(int n, const T* W, T* M, int nb
     if (r < n && c < n) M[(long long)r * n + c] = s;
 }
 
+// periodic window of component al at point p (lab coordinates in [0, L)):
+// per axis b the first of the 4 nodes and their weights (face al sits at
+// integer positions along al and half-integer positions along the others)
+template <int D>
+__device__ __forceinline__ void pair_window(const Geo& g, const double* p, int al, int* j0, double (*w)[4]) {
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const double sb = p[b] / g.h - (al == b ? 0.0 : 0.5);
+        const double fl = floor(sb);
+        j0[b] = (int)fl - 1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) w[b][m] = peskin4(sb - (fl - 1.0 + m));
+    }
+}
+
+template <int D>
+__global__ void k_pair_mtilde(Geo g, int nr, const double* __restrict__ q, int S, const double* __restrict__ x0,
+                              const float* __restrict__ tab, double* __restrict__ M) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nr * nr) return;
+    const int i = (int)(t / nr), j = (int)(t % nr);
+    const int ns[3] = {g.n0, g.n1, g.n2};
+    // acc[0]: sum_s T_s(q_i - q_j);  acc[1]: sum_s T_s(q_j - q_i)^T.  Thread
+    // (j, i) computes the same two sums transposed and swapped, and their sum
+    // does not depend on the order: the block is exactly symmetric
+    double acc[2][D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) acc[0][a][b] = acc[1][a][b] = 0.0;
+    for (int tr = 0; tr < 2; ++tr) {
+        // tr = 0: T(q_i - q_j)^{ab};  tr = 1: T(q_j - q_i)^{ba}
+        const int u = tr ? j : i, v = tr ? i : j;
+        for (int s = 0; s < S; ++s) {
+            double p[D];
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                const double Lb = ns[b] * g.h;
+                double x = x0[s * D + b] + q[(long long)u * D + b] - q[(long long)v * D + b];
+                x -= Lb * floor(x / Lb);
+                if (x >= Lb) x -= Lb;
+                p[b] = x;
+            }
+#pragma unroll
+            for (int al = 0; al < D; ++al) {
+                int j0[D];
+                double w[D][4];
+                pair_window<D>(g, p, al, j0, w);
+                double sum[D];
+#pragma unroll
+                for (int be = 0; be < D; ++be) sum[be] = 0.0;
+                for (int c = 0; c < (1 << (2 * D)); ++c) {
+                    long long cell = 0, stride = 1;
+                    double wt = 1.0;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) {
+                        const int m = (c >> (2 * b)) & 3;
+                        int jj = (j0[b] + m) % ns[b];
+                        if (jj < 0) jj += ns[b];
+                        cell += jj * stride;
+                        stride *= ns[b];
+                        wt *= w[b][m];
+                    }
+#pragma unroll
+                    for (int be = 0; be < D; ++be)
+                        sum[be] += wt * (double)tab[((long long)(s * D + be) * D + al) * g.ncell + cell];
+                }
+#pragma unroll
+                for (int be = 0; be < D; ++be) {
+                    if (tr == 0)
+                        acc[0][al][be] += sum[be];
+                    else
+                        acc[1][be][al] += sum[be];
+                }
+            }
+        }
+    }
+    const double sc = 0.5 / S;
+    const long long ld = (long long)nr * D;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) M[((long long)i * D + a) * ld + (long long)j * D + b] = sc * (acc[0][a][b] + acc[1][a][b]);
+}
+
+template <int D>
+__global__ void k_point_spread(Geo g, const double* __restrict__ x0, int beta, double scale, double* __restrict__ y) {
+    const int c = threadIdx.x;
+    if (c >= (1 << (2 * D))) return;
+    const int ns[3] = {g.n0, g.n1, g.n2};
+    int j0[D];
+    double w[D][4];
+    pair_window<D>(g, x0, beta, j0, w);
+    long long cell = 0, stride = 1;
+    double wt = 1.0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const int m = (c >> (2 * b)) & 3;
+        int jj = (j0[b] + m) % ns[b];
+        if (jj < 0) jj += ns[b];
+        cell += jj * stride;
+        stride *= ns[b];
+        wt *= w[b][m];
+    }
+    y[(long long)beta * g.ncell + cell] = scale * wt;
+}
+
 template <typename T>
 __global__ void k_add_diag(int n, T* M, T delta) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,6 +358,25 @@ void mtilde_build(int d, int Nb, const double* rel_b, const MobParams& p, double
         k_mtilde<3><<<grid_1d(n, 256), 256, 0, s>>>(Nb, rel_b, p, M);
     else
         k_mtilde<2><<<grid_1d(n, 256), 256, 0, s>>>(Nb, rel_b, p, M);
+    IBR_CHECK_LAUNCH();
+}
+
+void pair_mtilde(const Geo& g, int nr, const double* q, int S, const double* x0, const float* tab, double* M,
+                 cudaStream_t s) {
+    const long long n = (long long)nr * nr;
+    ProfScope ps(KID_MTILDE, s, (double)n * g.d * g.d * 8);
+    if (g.d == 3)
+        k_pair_mtilde<3><<<grid_1d(n, 128), 128, 0, s>>>(g, nr, q, S, x0, tab, M);
+    else
+        k_pair_mtilde<2><<<grid_1d(n, 128), 128, 0, s>>>(g, nr, q, S, x0, tab, M);
+    IBR_CHECK_LAUNCH();
+}
+
+void point_spread(const Geo& g, const double* x0, int beta, double scale, double* y, cudaStream_t s) {
+    if (g.d == 3)
+        k_point_spread<3><<<1, 64, 0, s>>>(g, x0, beta, scale, y);
+    else
+        k_point_spread<2><<<1, 16, 0, s>>>(g, x0, beta, scale, y);
     IBR_CHECK_LAUNCH();
 }
 

@@ -12,16 +12,6 @@
 namespace ibr {
 namespace {
 
-// 4-point Peskin kernel: the continuous function on [-2,2] fixed by
-// sum_j phi(r-j) = 1, sum_j (r-j) phi(r-j) = 0, even/odd sums 1/2 and
-// sum_j phi(r-j)^2 = 3/8.
-__device__ __forceinline__ double peskin4(double r) {
-    r = fabs(r);
-    if (r < 1.0) return 0.125 * (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r));
-    if (r < 2.0) return 0.125 * (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r));
-    return 0.0;
-}
-
 __global__ void k_positions(int d, int N, const double* __restrict__ rb, const int* __restrict__ body,
                             const double* __restrict__ xcR, double L0, double L1, double L2, double* __restrict__ q,
                             double* __restrict__ rel) {

@@ -11,6 +11,17 @@
 namespace ibr {
 
 // ---------------------------------------------------------------------------
+// 4-point Peskin kernel: the continuous function on [-2,2] fixed by
+// sum_j phi(r-j) = 1, sum_j (r-j) phi(r-j) = 0, even/odd sums 1/2 and
+// sum_j phi(r-j)^2 = 3/8.
+__device__ __forceinline__ double peskin4(double r) {
+    r = fabs(r);
+    if (r < 1.0) return 0.125 * (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r));
+    if (r < 2.0) return 0.125 * (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r));
+    return 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // errors
 void set_error(const std::string& msg);
 struct Error {
@@ -27,6 +38,7 @@ struct Error {
 // add_launches accounts for the kernels of a replayed CUDA graph
 void count_launch();
 void add_launches(long long n);
+long long thread_launches();  // launches counted on the calling thread
 bool profiling_enabled();
 #define IBR_CHECK_LAUNCH()                  \
     do {                                    \
@@ -319,6 +331,17 @@ struct MobParams {
 void mtilde_build(int d, int Nb, const double* rel_b, const MobParams& p, double* M, cudaStream_t s);
 // in place: M (n x n, row-major, SPD) -> M^-1 (full symmetric).  info_dev[0]
 // set to (k+1) if the k-th pivot is <= min_pivot.  work >= n*n.
+// The pair-mobility table of a periodic grid: for S source points x0[s]
+// and force directions beta, the velocity field v = L^-1 S~ (unit force
+// e_beta at x0[s]) stored in FP32 as tab[((s*d + beta)*d + alpha)*ncell + cell]
+// (alpha: velocity component).  pair_mtilde builds the dense block of the
+// nr markers at positions q[nr][d] (row-major, (d nr)^2):
+//   M~_ij^{ab} = (1/2S) sum_s [ J_a(x0_s + q_i - q_j) v^{s,b} + J_b(x0_s + q_j - q_i) v^{s,a} ]
+// (exactly symmetric).  point_spread writes y[beta*ncell + .] = scale * the
+// 4^d kernel weights of component beta at x0 (periodic; other entries untouched).
+void pair_mtilde(const Geo& g, int nr, const double* q, int S, const double* x0, const float* tab, double* M,
+                 cudaStream_t s);
+void point_spread(const Geo& g, const double* x0, int beta, double scale, double* y, cudaStream_t s);
 template <typename T>
 void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStream_t s);
 template <typename Ti, typename To>

@@ -41,8 +41,17 @@ static const char* kNames[KID_COUNT] = {
     "markers_setup", "mtilde_build", "spd_inverse", "blockdiag_gemv", "advect",
 };
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// per-thread count as well: a graph capture counts only its own thread's launches
+static thread_local long long t_launches = 0;
+void count_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
+void add_launches(long long n) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
+long long thread_launches() { return t_launches; }
 bool profiling_enabled() { return g_prof; }
 
 static cudaEvent_t get_event() {

@@ -19,7 +19,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -125,6 +127,12 @@ struct Body {
 
 }  // namespace
 
+// IBR_MOB_PAIR: source points of the pair-mobility table, inner GMRES length
+// of its solves, largest d N of one dense block for all markers
+constexpr int PAIR_S = 2;
+constexpr int PAIR_NS = 8;
+constexpr long long PAIR_FULL_MAX = 6144;
+
 template <typename T>
 struct PC;
 
@@ -158,9 +166,15 @@ struct ibr_grid {
     float* Minv32 = nullptr;
     int* info_dev = nullptr;
     std::vector<double> mob_shift;  // diagonal shift used per body (0: M~ was SPD)
+    // the pair-mobility table of IBR_MOB_PAIR (periodic grids): PAIR_S source
+    // points, d force directions, d velocity components, FP32; built once per grid
+    float* pair_tab = nullptr;
+    double* pair_x0 = nullptr;
+    std::shared_ptr<void> pair_hold;  // keeps the shared table alive
     // outer FGMRES workspace
     int m_alloc = 0;
     long long len_alloc = 0;
+    long long w_len = 0;  // the len w's zero pad was last set for
     // V: the basis in double-float (dflt, 8 bytes per entry); vk64: the FP64
     // copy of the current basis vector that the preconditioner reads
     double *V = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *w = nullptr, *vk64 = nullptr;
@@ -445,7 +459,7 @@ struct PC {
         if (use_graphs()) {
             if (gexec && (g_ns != ns || g_pre != pre || g_post != post || g_variant != variant)) invalidate_graph();
             if (!gexec) {
-                long long l0 = ibr_launch_count();
+                long long l0 = thread_launches();
                 long long psc = ps_count;
                 cudaGraph_t graph = nullptr;
                 IBR_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -464,7 +478,7 @@ struct PC {
                 g_pre = pre;
                 g_post = post;
                 g_variant = variant;
-                g_launches = ibr_launch_count() - l0;
+                g_launches = thread_launches() - l0;
                 add_launches(-g_launches);  // counted again on every replay below
                 ps_count = psc;
             }
@@ -683,6 +697,139 @@ double build_true_mobility(ibr_grid* G, double* M0) {
     return diag / (double)dN;
 }
 
+// The pair-mobility table of IBR_MOB_PAIR: for each of PAIR_S source points
+// x0 (off the grid nodes, in different sub-cell positions) and direction
+// beta, v = L^-1 S~ e_beta delta(x - x0) by restarted GMRES(PAIR_NS) with
+// P_S in FP64 to a relative residual of 1e-9, stored in FP32.  The pair
+// mobility of two markers is approximately a function of their displacement
+// only (Sec. IV: the kernel is close to translation invariant), so
+// J(x0 + q_i - q_j) v is M_ij up to that (small) dependence on the sub-cell
+// position, which the average over the source points reduces.
+// Pair tables are shared by all grids of one shape (device, cells, box,
+// eta, rho, dt): the first grid that needs one builds it, grids created
+// later (e.g. several resident grids of a serving engine) reuse it; it is
+// freed with the last grid that holds it.
+struct PairTable {
+    std::mutex mu;  // held while the table is built
+    float* tab = nullptr;
+    double* x0 = nullptr;
+    ~PairTable() {
+        if (tab) cudaFree(tab);
+        if (x0) cudaFree(x0);
+    }
+};
+std::mutex g_pair_mu;
+std::map<std::string, std::weak_ptr<PairTable>> g_pair_cache;
+
+std::string pair_key(const ibr_grid* G) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d,%d,%d|%.17g,%.17g,%.17g|%.17g|%.17g|%.17g", dev, G->d, G->n[0], G->n[1],
+                  G->n[2], G->L[0], G->L[1], G->L[2], G->eta, G->rho, G->dt);
+    return buf;
+}
+
+void build_pair_table_into(ibr_grid* G, float*& tab_out, double*& x0_out);
+
+void build_pair_table(ibr_grid* G) {
+    if (G->pair_tab) return;
+    std::shared_ptr<PairTable> t;
+    {
+        std::lock_guard<std::mutex> lk(g_pair_mu);
+        const std::string key = pair_key(G);
+        t = g_pair_cache[key].lock();
+        if (!t) {
+            t = std::make_shared<PairTable>();
+            g_pair_cache[key] = t;
+        }
+        for (auto it = g_pair_cache.begin(); it != g_pair_cache.end();)  // drop expired entries
+            it = it->second.expired() ? g_pair_cache.erase(it) : std::next(it);
+    }
+    {
+        std::lock_guard<std::mutex> lk(t->mu);
+        if (!t->tab) build_pair_table_into(G, t->tab, t->x0);
+    }
+    G->pair_tab = t->tab;
+    G->pair_x0 = t->x0;
+    G->pair_hold = t;
+}
+
+void build_pair_table_into(ibr_grid* G, float*& tab_out, double*& x0_out) {
+    cudaStream_t s = G->stream;
+    const Geo& g = G->geo;
+    const int d = G->d;
+    const long long n = g.ncell, nS = G->nS;
+    // sub-cell offsets of the sources (fractions of h), placed near the box centre
+    const double frac[PAIR_S][3] = {{0.3, 0.7, 0.45}, {0.7, 0.3, 0.55}};
+    double hx0[PAIR_S * 3];
+    for (int k = 0; k < PAIR_S; ++k)
+        for (int a = 0; a < d; ++a) hx0[k * d + a] = (std::floor(0.5 * G->n[a]) + frac[k][a]) * g.h;
+    float* tab = dalloc<float>((size_t)PAIR_S * d * d * n);
+    double* x0 = dalloc<double>((size_t)PAIR_S * d);
+    PC<double> pc(G, PAIR_NS);
+    double* rhs = dalloc<double>(nS);
+    double* x = dalloc<double>(nS);
+    double* w = dalloc<double>(nS);
+    double* dx = dalloc<double>(nS);
+    double* hs = nullptr;
+    auto cleanup = [&] {
+        dfree(rhs);
+        dfree(x);
+        dfree(w);
+        dfree(dx);
+        if (hs) cudaFreeHost(hs);
+        hs = nullptr;
+    };
+    try {
+        IBR_CUDA_TRY(cudaMallocHost(&hs, sizeof(double)));
+        IBR_CUDA_TRY(cudaMemcpyAsync(x0, hx0, sizeof(double) * PAIR_S * d, cudaMemcpyHostToDevice, s));
+        auto norm_sq = [&](const double* v) {
+            norm2<double>(nS, v, pc.partial, pc.sc, s);
+            IBR_CUDA_TRY(cudaMemcpyAsync(hs, pc.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+            IBR_CUDA_TRY(cudaStreamSynchronize(s));
+            return hs[0];
+        };
+        for (int k = 0; k < PAIR_S; ++k)
+            for (int be = 0; be < d; ++be) {
+                IBR_CUDA_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * nS, s));
+                point_spread(g, x0 + k * d, be, 1.0 / std::pow(g.h, d), rhs, s);
+                if (G->null_v()) {  // S~ = S - vol^-1 1^T: the force field has zero mean
+                    block_means<double>(n, d, rhs, pc.partial, pc.means, s);
+                    subtract_means<double>(n, d, rhs, pc.means, s);
+                }
+                const double b2 = norm_sq(rhs);
+                IBR_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * nS, s));
+                IBR_CUDA_TRY(cudaMemcpyAsync(w, rhs, sizeof(double) * nS, cudaMemcpyDeviceToDevice, s));
+                for (int pass = 0; pass < 40; ++pass) {
+                    pc.inner_gmres(w, dx);
+                    vec_axpby<double>(nS, 1.0, dx, 1.0, x, s);
+                    stokes_apply<double>(g, x, w, G->sigma(), G->eta, nullptr, s);
+                    vec_axpby<double>(nS, 1.0, rhs, -1.0, w, s);  // w = rhs - L x
+                    if (G->null_v()) {
+                        block_means<double>(n, d + 1, w, pc.partial, pc.means, s);
+                        subtract_means<double>(n, d + 1, w, pc.means, s);
+                    }
+                    if (norm_sq(w) <= 1e-18 * b2) break;
+                }
+                if (G->null_v()) {
+                    block_means<double>(n, d, x, pc.partial, pc.means, s);
+                    subtract_means<double>(n, d, x, pc.means, s);
+                }
+                vec_convert<double, float>((long long)d * n, x, tab + (size_t)(k * d + be) * d * n, s);
+            }
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        dfree(tab);
+        dfree(x0);
+        throw;
+    }
+    cleanup();
+    tab_out = tab;
+    x0_out = x0;
+}
+
 void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     cudaStream_t s = G->stream;
     require(!G->bodies.empty(), "no bodies added");
@@ -763,12 +910,15 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     // as one block, computed from the library's own Stokes solves (Sec. V.C:
     // worth it for fixed geometries, e.g. the steady nozzle of Sec. VII.F)
     const bool true_mob = o.mob_model == IBR_MOB_TRUE;
-    G->nblk = true_mob ? 1 : B;
+    const bool pair_mob = o.mob_model == IBR_MOB_PAIR;
+    require(!(pair_mob && G->walls()), "IBR_MOB_PAIR needs a periodic grid");
+    const bool one_block = true_mob || (pair_mob && (long long)N * d <= PAIR_FULL_MAX);
+    G->nblk = one_block ? 1 : B;
     const int nblk = G->nblk;
     G->moff.assign(nblk + 1, 0);
     G->roff.assign(nblk + 1, 0);
     for (int bi = 0; bi < nblk; ++bi) {
-        long long nb = true_mob ? (long long)N * d : (long long)G->bodies[bi].N * d;
+        long long nb = one_block ? (long long)N * d : (long long)G->bodies[bi].N * d;
         G->moff[bi + 1] = G->moff[bi] + nb * nb;
         G->roff[bi + 1] = G->roff[bi] + (int)nb;
     }
@@ -782,6 +932,21 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     double fself = 0.0;
     if (true_mob) {
         fself = build_true_mobility(G, G->Mbuild);
+    } else if (pair_mob) {
+        build_pair_table(G);
+        for (int bi = 0; bi < nblk; ++bi) {
+            const int m0 = one_block ? 0 : bstart[bi];
+            const int nm = one_block ? N : G->bodies[bi].N;
+            pair_mtilde(G->geo, nm, md.q + (long long)m0 * d, PAIR_S, G->pair_x0, G->pair_tab, G->Mbuild + G->moff[bi],
+                        s);
+        }
+        // the self-mobility scale: mean of the first marker's diagonal entries
+        const long long ld = G->roff[1] - G->roff[0];
+        double dg[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < d; ++a)
+            IBR_CUDA_TRY(cudaMemcpyAsync(&dg[a], G->Mbuild + a * ld + a, sizeof(double), cudaMemcpyDeviceToHost, s));
+        IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int a = 0; a < d; ++a) fself += dg[a] / d;
     } else {
         MobParams mp = mob_params(G, o);
         for (int bi = 0; bi < B; ++bi)
@@ -854,9 +1019,18 @@ bool mob_opts_equal(const ibr_solve_opts& a, const ibr_solve_opts& b) {
 }
 
 void ensure_outer(ibr_grid* G, int m) {
-    if (G->m_alloc >= m && G->V && G->len_alloc == G->len) return;
+    // the workspace is kept while it is large enough (a resident grid reused
+    // with another marker count); w's zero pad entry moves with len
+    if (G->m_alloc >= m && G->V && G->len_alloc >= G->len) {
+        if (G->w_len != G->len) {
+            IBR_CUDA_TRY(cudaMemsetAsync(G->w, 0, ((G->len_alloc + 1) & ~1LL) * sizeof(double), G->stream));
+            G->w_len = G->len;
+        }
+        return;
+    }
     free_outer(G);
     long long len = G->len;
+    G->w_len = len;
     // the double-float basis is read in pairs: an even leading dimension,
     // and w carries the same zero pad entry
     const long long lp = G->len_pad();
@@ -1160,6 +1334,102 @@ int solve_core(ibr_grid* G, const double* body_UO, const double* gforce, int g_o
     G->have_solution = true;
     return status;
 }
+
+namespace ibr {
+
+// Device bytes one grid holds through a solve with these sizes: the outer
+// FGMRES workspace (double-float basis, Z, b, x, w), the preconditioner in its
+// precision (multigrid levels, inner GMRES basis, P_S work), the marker data
+// and gather lists of S, and the dense mobility blocks (as built, factorised,
+// plus the factorisation's work block).  Every allocation of >= 1 MiB is
+// rounded up to the 2 MiB page the CUDA allocator hands out; the many small
+// buffers are covered by a fixed 16 MiB.  Periodic grids, prescribed bodies.
+long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int restart, int ns, int precision,
+                              int mob_model) {
+    auto pg = [](double b) {
+        const double MiB = 1048576.0;
+        return b >= MiB ? std::ceil(b / (2 * MiB)) * 2 * MiB : b;
+    };
+    const double e = precision == IBR_FP64 ? 8.0 : 4.0;
+    Geo g = make_geo(d, n, 1.0);
+    const double nc = (double)g.ncell;
+    const double nS = (d + 1) * nc;
+    long long N = 0;
+    double blk2 = 0.0, blkmax = 0.0;
+    for (int b = 0; b < B; ++b) {
+        N += Nb[b];
+        double m = (double)Nb[b] * d;
+        blk2 += m * m;
+        blkmax = std::max(blkmax, m * m);
+    }
+    const double dN = (double)N * d;
+    const double len = nS + dN;
+    const double lp = (double)(((long long)len + 1) & ~1LL);
+    const int m = restart;
+    double t = 0.0;
+    // outer FGMRES
+    t += pg(8.0 * (m + 1) * lp) + pg(8.0 * m * len) + 3 * pg(8.0 * len) + pg(8.0 * lp);
+    t += 8.0 * ((m + 1) * (m + 1) + 8 * (m + 2)) + pg(8.0 * RED_BLOCKS * std::max(m + 1, 4));
+    // preconditioner: coarse multigrid levels (d stacked fields, u and f)
+    Geo c = g;
+    while (Multigrid<float>::can_coarsen(c)) {
+        c.n0 /= 2;
+        c.n1 /= 2;
+        if (d == 3) c.n2 /= 2;
+        c.ncell = (long long)c.n0 * c.n1 * c.n2;
+        t += 2 * pg(e * d * (double)c.ncell);
+    }
+    t += pg(e * (ns + 1) * nS) + pg(e * ns * nS) + 4 * pg(e * nS) + pg(e * d * nc) + 3 * pg(e * nc);
+    t += pg(8.0 * RED_BLOCKS * std::max(ns + 1, 4)) + 2 * pg(e * dN) + pg(8.0 * dN);
+    // markers: positions, lever arms, windows (index, FP64 and FP32 weights),
+    // face-major gather lists (at most 4^d faces per marker and component)
+    const double win = (double)N * d * d * 4;
+    const double E = (double)N * d * std::pow(4.0, d);
+    t += 2 * pg(8.0 * dN) + pg(4.0 * win) + pg(8.0 * win) + pg(4.0 * win);
+    t += pg(8.0 * E) + pg(4.0 * E) + pg(4.0 * E) + pg(8.0 * E) + pg(4.0 * E);
+    // the gather-list build's temporaries (sort keys, flags, positions)
+    t += pg(8.0 * E) + 2 * pg(4.0 * E);
+    // IBR_MOB_PAIR: the table (resident) and, while it is built, an FP64
+    // preconditioner with PAIR_NS inner vectors and four solve vectors; its
+    // blocks: one for all markers while d N <= PAIR_FULL_MAX
+    if (mob_model == IBR_MOB_PAIR) {
+        t += pg(4.0 * PAIR_S * d * d * nc);
+        double mg64 = 0.0;
+        Geo c2 = g;
+        while (Multigrid<double>::can_coarsen(c2)) {
+            c2.n0 /= 2;
+            c2.n1 /= 2;
+            if (d == 3) c2.n2 /= 2;
+            c2.ncell = (long long)c2.n0 * c2.n1 * c2.n2;
+            mg64 += 2 * pg(8.0 * d * (double)c2.ncell);
+        }
+        t += mg64 + pg(8.0 * (PAIR_NS + 1) * nS) + pg(8.0 * PAIR_NS * nS) + 8 * pg(8.0 * nS) + pg(8.0 * d * nc) +
+             3 * pg(8.0 * nc);
+        if (dN <= PAIR_FULL_MAX) blk2 = blkmax = dN * dN;
+    }
+    // mobility: built (FP64) + factorised inverse (precision) + work block
+    t += pg(8.0 * blk2) + pg(e * blk2) + pg(e * blkmax);
+    return (long long)(t + 16.0 * 1048576.0);
+}
+
+// a grid reused for another problem of the same shape: bodies dropped (the
+// next solve rebins, rebuilds and refactorises), workspaces kept
+void grid_clear_bodies(ibr_grid* G) {
+    G->bodies.clear();
+    G->dirty = true;
+    G->have_solution = false;
+}
+
+// the stream the grid's work is issued on from now on (the grid must be idle)
+void grid_set_stream(ibr_grid* G, cudaStream_t s) {
+    if (G->own_stream) {
+        cudaStreamDestroy(G->stream);
+        G->own_stream = false;
+    }
+    G->stream = s;
+}
+
+}  // namespace ibr
 
 // makes G->x usable as a state: set-up, workspaces, and x = 0 with the wall
 // values on the wall faces if there is no solution yet
@@ -1623,6 +1893,19 @@ int ibr_op_vcycle(ibr_grid* G, double sigma, double kappa, const double* f, doub
     });
 }
 
+int ibr_estimate_device_bytes(int dim, const int* n, int n_bodies, const int* n_markers, int restart, int n_s,
+                              int precision, int mob_model, long long* bytes) {
+    return run_guarded("ibr_estimate_device_bytes", [&] {
+        require(bytes && n && (n_bodies == 0 || n_markers), "n, bytes (and n_markers) must be non-NULL");
+        require(dim == 2 || dim == 3, "dim must be 2 or 3");
+        require(n_bodies >= 0 && restart >= 1 && n_s >= 0, "n_bodies >= 0, restart >= 1, n_s >= 0 required");
+        require(precision == IBR_FP64 || precision == IBR_MIXED, "bad precision");
+        for (int a = 0; a < dim; ++a) require(n[a] >= 4, "n[a] >= 4 required");
+        for (int b = 0; b < n_bodies; ++b) require(n_markers[b] >= 0, "n_markers must be >= 0");
+        *bytes = estimate_grid_bytes(dim, n, n_bodies, n_markers, restart, n_s == 0 ? 2 : n_s, precision, mob_model);
+    });
+}
+
 int ibr_destroy_grid(ibr_grid* G) {
     if (!G) return IBR_OK;
     return run_guarded("ibr_destroy_grid", [&] {
@@ -1635,6 +1918,7 @@ int ibr_destroy_grid(ibr_grid* G) {
         if (G->host_sc) cudaFreeHost(G->host_sc);
         for (double* p : G->wdata) dfree(p);
         for (double** p : {&G->adv_v, &G->adv_N, &G->adv_Np, &G->adv_g, &G->adv_f}) dfree(*p);
+        G->pair_hold.reset();  // the shared table goes with its last grid
         if (G->own_stream) cudaStreamDestroy(G->stream);
         delete G;
     });

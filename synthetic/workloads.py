@@ -23,6 +23,11 @@ __all__ = [
     "nozzle",
     "nozzle_walls",
     "parabolic_inflow",
+    "ellipsoid_markers",
+    "random_quaternion",
+    "batch_2d",
+    "serve_3d",
+    "Request",
 ]
 
 
@@ -214,3 +219,146 @@ def nozzle(n=(256, 128), Re=0.0, U=1.0, u_max=None):
         eta, rho, dt = U * 0.4 / Re, 1.0, 0.5 * h / (U if u_max is None else u_max)
     return Workload(f"nozzle_{n[0]}x{n[1]}_Re{Re:g}", tuple(n), (2.0, 1.0), eta=eta, rho=rho, dt=dt, bodies=bodies,
                     tol=1e-8, walls=(True, True))
+
+
+# ---------------------------------------------------------------------------
+# batched and served problem mixes (independent periodic problems)
+
+def ellipsoid_markers(b, aspect, h, spacing=2.2):
+    """Golden-spiral points on a prolate ellipsoid with semi-axes
+    (aspect b, b, b) along the body-frame x, y, z: a sphere's points scaled
+    per axis, their number raised (from the sphere rule N = area / ((sqrt 3 / 2)
+    (2h)^2)) until the largest nearest-neighbour distance is <= spacing h."""
+    from scipy.spatial import cKDTree
+
+    a = aspect * b
+    if aspect > 1.0:
+        e = np.sqrt(1.0 - (b / a) ** 2)
+        area = 2.0 * np.pi * b * b * (1.0 + a / (b * e) * np.arcsin(e))
+    else:
+        area = 4.0 * np.pi * b * b
+    N = max(12, int(round(area / (np.sqrt(3.0) / 2.0 * (2.0 * h) ** 2))))
+    scale = np.array([a, b, b])
+    while True:
+        pts = sphere_markers(1.0, N) * scale
+        dist, _ = cKDTree(pts).query(pts, k=2)
+        if dist[:, 1].max() <= spacing * h or N > 200000:
+            return pts
+        N = int(N * 1.1) + 1
+
+
+def random_quaternion(rng):
+    """Uniformly distributed unit quaternion (w, x, y, z) (Shoemake's method)."""
+    u1, u2, u3 = rng.uniform(size=3)
+    q = np.array([np.sqrt(1 - u1) * np.sin(2 * np.pi * u2), np.sqrt(1 - u1) * np.cos(2 * np.pi * u2),
+                  np.sqrt(u1) * np.sin(2 * np.pi * u3), np.sqrt(u1) * np.cos(2 * np.pi * u3)])
+    return np.array([q[3], q[0], q[1], q[2]])
+
+
+def quat_matrix(q):
+    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+@dataclass
+class Request:
+    """One independent periodic problem of a batch or a served stream: the
+    unit box with n cells per axis, bodies given by centre, orientation and
+    body-frame marker offsets, rigid velocities [B, d + rot]; t_arrival in s."""
+    n: tuple
+    centers: list
+    quats: list
+    rels: list
+    UO: np.ndarray
+    t_arrival: float = 0.0
+    shapes: list = field(default_factory=list)
+
+    @property
+    def d(self):
+        return len(self.n)
+
+    @property
+    def L(self):
+        return (1.0,) * self.d
+
+    @property
+    def N(self):
+        return int(sum(r.shape[0] for r in self.rels))
+
+    def workload(self):
+        """The same problem as a Workload (markers rotated into the lab frame)."""
+        bodies = []
+        for c, q, r, uo in zip(self.centers, self.quats, self.rels, self.UO):
+            rel = r if self.d == 2 else r @ quat_matrix(q).T
+            bodies.append(Body(np.asarray(c, dtype=np.float64), rel, np.asarray(uo)))
+        return Workload(f"req_{'x'.join(map(str, self.n))}_{len(bodies)}b", tuple(self.n), self.L, bodies=bodies,
+                        tol=1e-8)
+
+
+def _periodic_gap(c1, c2):
+    d = np.abs(np.asarray(c1) - np.asarray(c2))
+    d = np.minimum(d, 1.0 - d)
+    return float(np.sqrt((d * d).sum()))
+
+
+def _place(rng, radii, d, gap, tries=2000):
+    """Rejection-sampled centres in the periodic unit box with bounding
+    circles/spheres at least `gap` apart; bodies that find no place in
+    `tries` draws are dropped.  Returns the kept indices and centres."""
+    keep, cs = [], []
+    for i, r in enumerate(radii):
+        for _ in range(tries):
+            c = rng.uniform(0.0, 1.0, d)
+            if all(_periodic_gap(c, c2) >= r + radii[j] + gap for j, c2 in zip(keep, cs)):
+                keep.append(i)
+                cs.append(c)
+                break
+    return keep, cs
+
+
+def batch_2d(count=64, seed=1505 + 4, sizes=(64, 128, 256, 512)):
+    """Independent 2-D periodic Stokes problems: n uniform over `sizes`
+    (square unit box), 1 to 8 disks of radius U[0.05, 0.15] with markers at
+    2h, non-overlapping with a gap >= 4h (the kernel support), rigid
+    velocities N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice(sizes))
+        h = 1.0 / n
+        nb = int(rng.integers(1, 9))
+        radii = rng.uniform(0.05, 0.15, nb)
+        keep, cs = _place(rng, radii, 2, 4.0 * h)
+        rels = [disk_markers(radii[i], h) for i in keep]
+        UO = random_velocities(rng, 2, len(keep))
+        out.append(Request((n, n), cs, [np.array([1.0, 0, 0, 0])] * len(keep), rels, UO,
+                           shapes=[("disk", radii[i]) for i in keep]))
+    return out
+
+
+def serve_3d(count=60, rate=50.0, seed=1505 + 5, sizes=(64, 96, 128, 192), max_bodies=16):
+    """A stream of 3-D periodic Stokes requests with Poisson arrivals at
+    `rate` per second: n uniform over `sizes`; 1 to max_bodies rigid bodies,
+    each a sphere or a prolate ellipsoid (aspect U[1, 3], semi-minor axis
+    U[0.05, 0.12], uniformly random orientation) carrying surface markers at
+    <= 2.2h (ellipsoid_markers), non-overlapping with a gap >= 4h between
+    bounding spheres; rigid velocities N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += rng.exponential(1.0 / rate)
+        n = int(rng.choice(sizes))
+        h = 1.0 / n
+        nb = int(rng.integers(1, max_bodies + 1))
+        aspect = np.where(rng.uniform(size=nb) < 0.5, 1.0, rng.uniform(1.0, 3.0, nb))
+        b = rng.uniform(0.05, 0.12, nb)
+        keep, cs = _place(rng, aspect * b, 3, 4.0 * h)
+        quats = [random_quaternion(rng) for _ in keep]
+        rels = [ellipsoid_markers(b[i], aspect[i], h) for i in keep]
+        UO = random_velocities(rng, 3, len(keep))
+        out.append(Request((n, n, n), cs, quats, rels, UO, t_arrival=t,
+                           shapes=[("ellipsoid" if aspect[i] > 1 else "sphere", b[i], aspect[i]) for i in keep]))
+    return out

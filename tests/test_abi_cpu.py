@@ -76,3 +76,70 @@ def test_null_handles_rejected(abi):
     assert abi._lib.ibr_destroy_grid(None) == abi.OK
     assert abi._lib.ibr_set_markers(None, 0, None, 1) == abi.EINVAL
     assert abi._lib.ibr_apply_system(None, None, None) == abi.EINVAL
+
+
+_LAYOUT_C = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "ibrigid.h"
+#define F(T, m) printf(#T " " #m " %zu\n", offsetof(T, m))
+int main(void) {
+    printf("ibr_request size %zu\n", sizeof(ibr_request));
+    printf("ibr_result size %zu\n", sizeof(ibr_result));
+    printf("ibr_server_stats size %zu\n", sizeof(ibr_server_stats));
+    F(ibr_request, eta); F(ibr_request, x_c); F(ibr_request, opts); F(ibr_request, want_fields);
+    F(ibr_result, rel_res_true); F(ibr_result, reserved_bytes); F(ibr_result, slot); F(ibr_result, n_bodies);
+    F(ibr_server_stats, tuned_shapes);
+    return 0;
+}
+"""
+
+
+def test_server_struct_layouts_match_c(abi, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        t, m, v = line.split()
+        got[(t, m)] = int(v)
+    assert got[("ibr_request", "size")] == ctypes.sizeof(abi.Request)
+    assert got[("ibr_result", "size")] == ctypes.sizeof(abi.Result)
+    assert got[("ibr_server_stats", "size")] == ctypes.sizeof(abi.ServerStats)
+    for (t, m), v in got.items():
+        if m == "size":
+            continue
+        cls = {"ibr_request": abi.Request, "ibr_result": abi.Result, "ibr_server_stats": abi.ServerStats}[t]
+        assert getattr(cls, m).offset == v, (t, m)
+
+
+def test_device_memory_estimate_is_consistent(abi):
+    # host-only arithmetic: grows with the grid, the markers, the restart and
+    # the precision; the Krylov basis dominates large grids
+    e = abi.estimate_device_bytes
+    base = e(3, (64, 64, 64), [400])
+    assert e(3, (128, 128, 128), [400]) > 7 * base
+    assert e(3, (64, 64, 64), [800]) > base
+    assert e(3, (64, 64, 64), [400], precision=abi.FP64) > base
+    # ten more restart vectors: 2 x 10 FP64 system vectors (basis and Z)
+    len_ = 4 * 64 ** 3 + 3 * 400
+    d10 = e(3, (64, 64, 64), [400], restart=60) - base
+    assert abs(d10 - 2 * 10 * 8 * len_) < 0.05 * d10
+    # dense mobility blocks: (3 N)^2 entries in FP64 (built) + FP32 (inverse, work)
+    dm = e(2, (64, 64), [2000]) - e(2, (64, 64), [1000])
+    assert dm > 0
+    assert e(2, (64, 64), [2000]) - e(2, (64, 64), [1000, 1000]) > 0  # one block of 2N costs more than two of N
+    with pytest.raises(abi.IbrError):
+        e(4, (8, 8), [1])
+
+
+def test_server_create_without_gpu_fails_cleanly(abi):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(abi.IbrError) as ex:
+        abi.Server(slots=2, budget_bytes=1 << 30)
+    assert ex.value.code == abi.ECUDA
+    assert abi._lib.ibr_server_create(None, 1, 1, 0) == abi.EINVAL
+    assert abi._lib.ibr_server_destroy(None) == abi.OK

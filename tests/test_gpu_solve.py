@@ -108,7 +108,8 @@ def test_mixed_at_benchmark_tolerance(abi):
         assert rel_err(a, b) < 1e-7
 
 
-@pytest.mark.parametrize("kw", [dict(n_s=1), dict(n_s=4), dict(variant=1), dict(restart=20), dict(mg_pre=1, mg_post=1)])
+@pytest.mark.parametrize("kw", [dict(n_s=1), dict(n_s=4), dict(variant=1), dict(restart=20), dict(mg_pre=1, mg_post=1),
+                                dict(mob_model=4)])
 def test_preconditioner_choice_does_not_change_solution(abi, kw):
     # Sec. V.A: the preconditioner changes iteration counts, never the answer
     wl = CASES[2]
