@@ -270,13 +270,25 @@ int ibr_op_rigid_T(ibr_grid* g, const double* lam, double* FT);
 int ibr_op_mtilde(ibr_grid* g, int body, double* out);
 
 /* out = M~^-1 rhs (block diagonal over bodies, [N*dim]) with the factorised
- * M~ in the grid's preconditioner precision. */
+ * M~ in the grid's preconditioner precision.  The mixed path factorises on the
+ * tensor cores: blocked Cholesky (128-blocks), triangular inverse and
+ * M~^-1 = L^-T L^-1, their products in split TF32 (ibr_op_gemm_tf32x3). */
 int ibr_op_mtilde_solve(ibr_grid* g, const double* rhs, double* out);
 
 /* One application z = P_S^-1 r of the Stokes preconditioner (Sec. V.B,
  * Eq. P1_practical) in the preconditioner precision, r and z of length
  * (dim+1)*cells (velocity then pressure). */
 int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
+
+/* C = beta C + alpha A B^T on the tensor cores: the dense product of the
+ * mixed-precision M~ factorisation (Sec. V.C), exposed for parity checks.
+ * A [M][lda], B [N][ldb], C [M][ldc] row-major FP32 device arrays (A and B
+ * 16-byte aligned, lda and ldb multiples of 4); M and N multiples of 128, K
+ * of 32 (else IBR_EINVAL).  Each operand is split into two TF32 parts, the
+ * three leading products are accumulated in FP32 (close to FP32 accuracy).
+ * Issued on cuda_stream (NULL: legacy default stream) and waited for. */
+int ibr_op_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                       float alpha, float beta, void* cuda_stream);
 
 /* N = div(v v) (the advection term of ibr_advance: centred flux form, the
  * wall extension with the wall data), v and N device arrays of dim face

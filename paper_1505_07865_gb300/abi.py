@@ -175,6 +175,8 @@ _SIGS = {
     "ibr_op_mtilde_solve": (ctypes.c_int, [_P, _P, _P]),
     "ibr_op_stokes_pc": (ctypes.c_int, [_P, _P, _P]),
     "ibr_op_advect": (ctypes.c_int, [_P, _P, _P]),
+    "ibr_op_gemm_tf32x3": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int,
+                                          _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
     "ibr_op_vcycle": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_int]),
     "ibr_destroy_grid": (ctypes.c_int, [_P]),
     "ibr_last_error": (ctypes.c_char_p, []),
@@ -389,6 +391,19 @@ def op_mtilde_solve(grid, rhs, out):
 
 def op_advect(grid, v, N):
     _check(_lib.ibr_op_advect(grid, _dev(v), _dev(N)))
+
+
+def op_gemm_tf32x3(A, B, C, alpha=1.0, beta=0.0, stream=None):
+    """C = beta C + alpha A B^T on the tensor cores; A [M, K], B [N, K], C [M, N]
+    contiguous float32 CUDA tensors (row strides may exceed the widths)."""
+    for t in (A, B, C):
+        if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != "torch.float32" or t.stride(1) != 1:
+            raise TypeError("expected float32 CUDA tensors with unit column stride")
+    M, K = A.shape
+    N = B.shape[0]
+    s = None if stream is None else _P(int(stream))
+    _check(_lib.ibr_op_gemm_tf32x3(M, N, K, _P(A.data_ptr()), A.stride(0), _P(B.data_ptr()), B.stride(0),
+                                   _P(C.data_ptr()), C.stride(0), float(alpha), float(beta), s))
 
 
 def op_stokes_pc(grid, r, z):

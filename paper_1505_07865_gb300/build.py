@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibrigid.so")
-SOURCES = ["stencil.cu", "blas.cu", "ib.cu", "dense.cu", "solver.cu", "prof.cu", "noalloc.cu", "advect.cu", "server.cu"]
+SOURCES = ["stencil.cu", "blas.cu", "ib.cu", "dense.cu", "solver.cu", "prof.cu", "noalloc.cu", "advect.cu", "server.cu", "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -51,7 +51,7 @@ enum KernelId {
     KID_STOKES, KID_RBGS, KID_RESTRICT, KID_PROLONG, KID_COARSE, KID_PS_DIV, KID_PS_FINISH,
     KID_AXPBY, KID_SCALE, KID_CONVERT, KID_MDOT, KID_UPD_MDOT, KID_UPD_NORM, KID_NORM2, KID_COMBINE,
     KID_BLOCK_MEANS, KID_SUB_MEANS, KID_SMALL, KID_SPREAD, KID_INTERP, KID_LAMSUM, KID_RIGID_K,
-    KID_RIGID_KT, KID_MARKERS, KID_MTILDE, KID_SPD_INV, KID_GEMV, KID_ADVECT, KID_COUNT
+    KID_RIGID_KT, KID_MARKERS, KID_MTILDE, KID_SPD_INV, KID_GEMV, KID_ADVECT, KID_TC_GEMM, KID_COUNT
 };
 // records CUDA events around the launches in its scope when profiling is on;
 // bytes = the algorithmic bytes those launches move
@@ -346,6 +346,16 @@ template <typename T>
 void spd_inverse(int n, T* M, T* work, int* info_dev, double min_pivot, cudaStream_t s);
 template <typename Ti, typename To>
 void mat_convert(long long n, const Ti* a, To* b, cudaStream_t s);
+// tc_gemm.cu -- tensor-core (tcgen05, split TF32) dense products:
+// C = beta C + alpha A B^T, A [M][K], B [N][K] row-major FP32; M, N multiples
+// of 128, K of 32; lower_only: the 128 x 128 tiles above the diagonal are
+// not computed; err_dev[0] = 1 if a wait for the tensor cores timed out
+void gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, float alpha,
+                 float beta, bool lower_only, int* err_dev, cudaStream_t s);
+// M (n x n SPD FP32) -> M^-1 with the tensor-core products (blocked Cholesky,
+// triangular inverse, X^T X); info_dev as in spd_inverse; pad: the diagonal
+// of the identity block that pads n to a multiple of 128
+void spd_inverse_tc(int n, float* M, int* info_dev, double min_pivot, double pad, int* err_dev, cudaStream_t s);
 template <typename T>
 void add_diag(int n, T* M, double delta, cudaStream_t s);   // M += delta I
 // out[r] = sum_c Minv_b[r][c] rhs[c] for each body block (offsets in elements)

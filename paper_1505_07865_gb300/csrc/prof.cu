@@ -38,7 +38,7 @@ static const char* kNames[KID_COUNT] = {
     "ps_divergence", "ps_finish", "vec_axpby", "vec_scale_copy", "vec_convert", "krylov_mdot",
     "krylov_update_mdot", "krylov_update_norm2", "krylov_norm2", "krylov_combine", "block_means",
     "subtract_means", "krylov_small", "spread_gather", "interp", "lam_sum", "rigid_K", "rigid_KT",
-    "markers_setup", "mtilde_build", "spd_inverse", "blockdiag_gemv", "advect",
+    "markers_setup", "mtilde_build", "spd_inverse", "blockdiag_gemv", "advect", "tc_gemm_tf32x3",
 };
 
 // per-thread count as well: a graph capture counts only its own thread's launches

@@ -953,8 +953,9 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
             mtilde_build(d, G->bodies[bi].N, md.rel + (long long)bstart[bi] * d, mp, G->Mbuild + G->moff[bi], s);
         fself = mob_self(mp);
     }
-    if (!G->info_dev) G->info_dev = dalloc<int>(1);
-    IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, sizeof(int), s));
+    // info_dev[0]: failed pivot, info_dev[1]: tensor-core time-out flag
+    if (!G->info_dev) G->info_dev = dalloc<int>(2);
+    IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, 2 * sizeof(int), s));
     // a pivot below this fraction of the self-mobility means M~ is singular
     // to working precision (e.g. coincident markers)
     if (!(fself > 0.0))
@@ -967,6 +968,12 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     // from 1e-3 f(0): the shift damps the spurious small/negative modes the way
     // the paper's eigenvalue filtering drops them.
     G->mob_shift.assign(nblk, 0.0);
+    // the mixed path factorises on the tensor cores (split TF32); IBR_DENSE=cuda
+    // selects the CUDA-core FP32 tiles instead (for comparison)
+    static const bool dense_cuda = [] {
+        const char* e = std::getenv("IBR_DENSE");
+        return e && std::strcmp(e, "cuda") == 0;
+    }();
     auto factor_all = [&](auto* Minv, auto* work, double min_piv) {
         using TT = std::remove_pointer_t<decltype(Minv)>;
         for (int bi = 0; bi < nblk; ++bi) {
@@ -975,12 +982,20 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
             for (int attempt = 0;; ++attempt) {
                 mat_convert<double, TT>(G->moff[bi + 1] - G->moff[bi], G->Mbuild + G->moff[bi], Minv + G->moff[bi], s);
                 if (delta > 0.0) add_diag<TT>(nb, Minv + G->moff[bi], delta, s);
-                IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, sizeof(int), s));
-                spd_inverse<TT>(nb, Minv + G->moff[bi], work, G->info_dev, min_piv, s);
-                int info = 0;
-                IBR_CUDA_TRY(cudaMemcpyAsync(&info, G->info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+                IBR_CUDA_TRY(cudaMemsetAsync(G->info_dev, 0, 2 * sizeof(int), s));
+                if constexpr (std::is_same<TT, float>::value) {
+                    if (!dense_cuda)
+                        spd_inverse_tc(nb, Minv + G->moff[bi], G->info_dev, min_piv, fself, G->info_dev + 1, s);
+                    else
+                        spd_inverse<TT>(nb, Minv + G->moff[bi], work, G->info_dev, min_piv, s);
+                } else {
+                    spd_inverse<TT>(nb, Minv + G->moff[bi], work, G->info_dev, min_piv, s);
+                }
+                int info[2] = {0, 0};
+                IBR_CUDA_TRY(cudaMemcpyAsync(info, G->info_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
                 IBR_CUDA_TRY(cudaStreamSynchronize(s));
-                if (info == 0) break;
+                if (info[1]) throw Error{IBR_ECUDA, "a tensor-core product timed out waiting for its MMAs"};
+                if (info[0] == 0) break;
                 if (attempt >= 40)
                     throw Error{IBR_ENUMERIC, "mobility block " + std::to_string(bi) +
                                                   " could not be made positive definite"};
@@ -996,9 +1011,9 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
         cudaFree(work);
     } else {
         G->Minv32 = dalloc<float>(mtot);
-        float* work = dalloc<float>(maxblk);
+        float* work = dense_cuda ? dalloc<float>(maxblk) : nullptr;  // the tensor-core path has its own
         factor_all(G->Minv32, work, min_piv32);
-        cudaFree(work);
+        if (work) cudaFree(work);
     }
     G->FT = dalloc<double>((size_t)B * (d + G->rot()));
     G->bfree_dev = dalloc<int>(B);
@@ -1407,8 +1422,15 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
              3 * pg(8.0 * nc);
         if (dN <= PAIR_FULL_MAX) blk2 = blkmax = dN * dN;
     }
-    // mobility: built (FP64) + factorised inverse (precision) + work block
-    t += pg(8.0 * blk2) + pg(e * blk2) + pg(e * blkmax);
+    // mobility: built (FP64) + factorised inverse (precision) + work: the FP64
+    // path's work block, or the tensor-core path's two padded blocks
+    t += pg(8.0 * blk2) + pg(e * blk2);
+    if (precision == IBR_FP64) {
+        t += pg(e * blkmax);
+    } else {
+        const double np = std::ceil(std::sqrt(blkmax) / 128.0) * 128.0;
+        t += 2 * pg(4.0 * np * np) + pg(4.0 * np * 128.0) + pg(4.0 * np * 128.0);
+    }
     return (long long)(t + 16.0 * 1048576.0);
 }
 
@@ -1890,6 +1912,29 @@ int ibr_op_vcycle(ibr_grid* G, double sigma, double kappa, const double* f, doub
             for (int i = 0; i < k; ++i) pc->mg.vcycle(pc->xs, pc->rs, 1, FLD_P, sigma, kappa, false, pc->pre, pc->post, s);
             vec_convert<float, double>(n, pc->xs, u, s);
         }
+    });
+}
+
+int ibr_op_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                       float alpha, float beta, void* cuda_stream) {
+    return run_guarded("ibr_op_gemm_tf32x3", [&] {
+        require(A && B && C, "A, B, C must be non-NULL");
+        require(M >= 0 && N >= 0 && K >= 0 && lda >= K && ldb >= K && ldc >= N, "bad sizes");
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        int* err = nullptr;
+        IBR_CUDA_TRY(cudaMallocAsync(&err, sizeof(int), s));
+        IBR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+        int herr = 0;
+        try {
+            gemm_tf32x3(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, false, err, s);
+            IBR_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            IBR_CUDA_TRY(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaFreeAsync(err, s);
+            throw;
+        }
+        IBR_CUDA_TRY(cudaFreeAsync(err, s));
+        if (herr) throw Error{IBR_ECUDA, "a tensor-core product timed out waiting for its MMAs"};
     });
 }
 
