@@ -284,7 +284,7 @@ int ibr_op_stokes_pc(ibr_grid* g, const double* r, double* z);
  * mixed-precision M~ factorisation (Sec. V.C), exposed for parity checks.
  * A [M][lda], B [N][ldb], C [M][ldc] row-major FP32 device arrays (A and B
  * 16-byte aligned, lda and ldb multiples of 4); M and N multiples of 128, K
- * of 32 (else IBR_EINVAL).  Each operand is split into two TF32 parts, the
+ * a positive multiple of 32 (else IBR_EINVAL).  Each operand is split into two TF32 parts, the
  * three leading products are accumulated in FP32 (close to FP32 accuracy).
  * Issued on cuda_stream (NULL: legacy default stream) and waited for. */
 int ibr_op_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
@@ -433,15 +433,17 @@ int ibr_server_destroy(ibr_server* s);
  * was loaded.  ibr_profile_enable(1): from then on every launch is bracketed
  * by CUDA events on its own stream; ibr_profile_read(idx, ...) returns, for
  * entry idx (IBR_EINVAL past the end), a kernel-class name, launches, summed
- * event time in ms and summed algorithmic bytes (each array read or written
- * once); the first half of the entries count every launch of a class, the
+ * event time in ms, summed algorithmic bytes (each array read or written
+ * once) and summed tensor-core FLOPs (executed TF32 products; 0 for the
+ * other classes; any output may be NULL); the first half of the entries count every launch of a class, the
  * second half ("<name>@large") only its launches that move >= 32 MiB.  It
  * synchronises on the recorded events.  ibr_profile_reset clears the sums.
  * While profiling is on the preconditioner runs without CUDA graphs. */
 long long ibr_launch_count(void);
 int ibr_profile_enable(int on);
 int ibr_profile_reset(void);
-int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes);
+int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes,
+                     double* flops);
 
 /* Destroys the grid and frees its device memory. NULL is accepted. */
 int ibr_destroy_grid(ibr_grid* g);

@@ -194,7 +194,7 @@ _SIGS = {
     "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ibr_profile_reset": (ctypes.c_int, []),
     "ibr_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
-                                        ctypes.POINTER(ctypes.c_longlong), _D, _D]),
+                                        ctypes.POINTER(ctypes.c_longlong), _D, _D, _D]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -440,9 +440,9 @@ def profile_reset():
     _check(_lib.ibr_profile_reset())
 
 
-def profile_read():
-    """{kernel class: (launches, total_ms, total_algorithmic_bytes)} for every
-    class with at least one timed launch."""
+def profile_read(with_flops=False):
+    """{kernel class: (launches, total_ms, total_algorithmic_bytes[, tensor_flops])}
+    for every class with at least one timed launch."""
     out = {}
     i = 0
     buf = ctypes.create_string_buffer(64)
@@ -450,10 +450,12 @@ def profile_read():
         n = ctypes.c_longlong()
         ms = ctypes.c_double()
         by = ctypes.c_double()
-        if _lib.ibr_profile_read(i, buf, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)) != OK:
+        fl = ctypes.c_double()
+        if _lib.ibr_profile_read(i, buf, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                 ctypes.byref(fl)) != OK:
             break
         if n.value:
-            out[buf.value.decode()] = (n.value, ms.value, by.value)
+            out[buf.value.decode()] = (n.value, ms.value, by.value) + ((fl.value,) if with_flops else ())
         i += 1
     return out
 

@@ -54,10 +54,11 @@ enum KernelId {
     KID_RIGID_KT, KID_MARKERS, KID_MTILDE, KID_SPD_INV, KID_GEMV, KID_ADVECT, KID_TC_GEMM, KID_COUNT
 };
 // records CUDA events around the launches in its scope when profiling is on;
-// bytes = the algorithmic bytes those launches move
+// bytes = the algorithmic bytes those launches move, flops = the
+// floating-point operations they execute (tensor-core products; 0 elsewhere)
 class ProfScope {
   public:
-    ProfScope(int kid, cudaStream_t s, double bytes);
+    ProfScope(int kid, cudaStream_t s, double bytes, double flops = 0.0);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;
@@ -65,7 +66,7 @@ class ProfScope {
   private:
     int kid_;
     cudaStream_t s_;
-    double bytes_;
+    double bytes_, flops_;
     void* a_;
 };
 

@@ -18,12 +18,13 @@ static bool g_prof = false;
 struct Pending {
     int kid;
     cudaEvent_t a, b;
-    double bytes;
+    double bytes, flops;
 };
 struct Acc {
     long long launches = 0;
     double ms = 0.0;
     double bytes = 0.0;
+    double flops = 0.0;
 };
 static std::mutex g_mu;
 static std::vector<Pending> g_pending;
@@ -65,7 +66,8 @@ static cudaEvent_t get_event() {
     return e;
 }
 
-ProfScope::ProfScope(int kid, cudaStream_t s, double bytes) : kid_(kid), s_(s), bytes_(bytes), a_(nullptr) {
+ProfScope::ProfScope(int kid, cudaStream_t s, double bytes, double flops)
+    : kid_(kid), s_(s), bytes_(bytes), flops_(flops), a_(nullptr) {
     if (!g_prof) return;
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = get_event();
@@ -78,7 +80,7 @@ ProfScope::~ProfScope() {
     cudaEvent_t b = get_event();
     if (!b) return;
     cudaEventRecord(b, s_);
-    g_pending.push_back({kid_, (cudaEvent_t)a_, b, bytes_});
+    g_pending.push_back({kid_, (cudaEvent_t)a_, b, bytes_, flops_});
 }
 
 static void drain() {
@@ -92,6 +94,7 @@ static void drain() {
             a.launches++;
             a.ms += ms;
             a.bytes += p.bytes;
+            a.flops += p.flops;
         }
         g_free.push_back(p.a);
         g_free.push_back(p.b);
@@ -116,7 +119,8 @@ int ibr_profile_reset(void) {
     return IBR_OK;
 }
 
-int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes) {
+int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes,
+                     double* flops) {
     if (idx < 0 || idx >= 2 * ibr::KID_COUNT) return IBR_EINVAL;
     std::lock_guard<std::mutex> lk(ibr::g_mu);
     ibr::drain();
@@ -130,6 +134,7 @@ int ibr_profile_read(int idx, char* name, int name_len, long long* launches, dou
     if (launches) *launches = a.launches;
     if (ms) *ms = a.ms;
     if (bytes) *bytes = a.bytes;
+    if (flops) *flops = a.flops;
     return IBR_OK;
 }
 

@@ -5,14 +5,17 @@
 // gemm_tf32x3: C = beta C + alpha A B^T for FP32 row-major A [M][K], B [N][K]
 // (both K contiguous).  Each operand is split into a TF32 high part and a TF32
 // remainder, x = hi + lo, and the three products hi.hi + hi.lo + lo.hi are
-// accumulated in FP32 (split-precision TF32, close to FP32 accuracy).  One
-// CTA of 128 threads computes a 128 x 128 tile of C: the threads stage 128 x
-// 32 slices of A and B (hi and lo) into shared memory in the canonical
-// K-major no-swizzle layout (8-row x 16-byte core matrices), double
-// buffered; one thread issues tcgen05.mma (kind::tf32, M = N = 128, K = 8)
-// into a 128-column TMEM accumulator and commits each slice to an mbarrier;
-// the epilogue reads the accumulator with tcgen05.ld.  Every mbarrier wait is
-// bounded: on time-out the kernel records an error and stops issuing work.
+// accumulated in FP32 (split-precision TF32, close to FP32 accuracy).  A pack
+// pass writes the hi and lo parts in 128 x 32 slices already laid out as the
+// tensor cores read them from shared memory (canonical K-major, no swizzle:
+// 8-row x 16-byte core matrices); one CTA per 128 x 128 tile of C then runs a
+// producer / consumer pipeline over three shared-memory stages: one thread
+// moves slices with bulk asynchronous copies (cp.async.bulk, completion counted
+// on an mbarrier), one thread issues tcgen05.mma (kind::tf32, M = N = 128,
+// K = 8) into a 128-column TMEM accumulator and commits each slice back to the
+// producer; the epilogue reads the accumulator with tcgen05.ld.  Every
+// mbarrier wait is bounded: on time-out the kernel records an error and stops
+// issuing work.
 #include <cstdint>
 
 #include "ibr_internal.cuh"
@@ -22,10 +25,11 @@ namespace {
 
 constexpr int GT = 128;                   // tile rows / columns
 constexpr int GK = 32;                    // K slice per stage
+constexpr int NSTAGE = 3;                 // slices in flight
 constexpr int SLICE_BYTES = GT * GK * 4;  // one 128 x 32 FP32 slice: 16 KB
 constexpr int STAGE_BYTES = 4 * SLICE_BYTES;  // A hi, A lo, B hi, B lo
-constexpr int GEMM_SMEM = 2 * STAGE_BYTES + 1024;
-constexpr long long WAIT_LIMIT = 1LL << 26;
+constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 256;
+constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ULL;  // 4 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -72,9 +76,16 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// bounded wait for the phase with the given parity; false on time-out
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase with the given parity; false after WAIT_LIMIT_NS
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -84,52 +95,69 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
             : "r"(mbar), "r"(parity)
             : "memory");
         if (ok) return true;
-    }
-    return false;
-}
-
-// load a 128 x 32 slice of a row-major FP32 matrix (rows r0.., columns k0..)
-// and store its TF32 high and low parts; thread t handles 8 of the 1024
-// 16-byte chunks: chunk q -> row (q & 7) + 8 (q >> 6), chunk column (q >> 3) & 7
-// (8 consecutive threads: 8 rows of one chunk column, conflict-free stores)
-__device__ __forceinline__ void stage_slice(const float* __restrict__ X, int ld, int r0, int k0, uint8_t* hi,
-                                            uint8_t* lo) {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int q = i * GT + t;
-        const int r = (q & 7) + 8 * (q >> 6);
-        const int c = (q >> 3) & 7;
-        const float4 v = *reinterpret_cast<const float4*>(X + (long long)(r0 + r) * ld + k0 + 4 * c);
-        float4 h, l;
-        h.x = tf32_round(v.x);
-        h.y = tf32_round(v.y);
-        h.z = tf32_round(v.z);
-        h.w = tf32_round(v.w);
-        l.x = tf32_round(v.x - h.x);
-        l.y = tf32_round(v.y - h.y);
-        l.z = tf32_round(v.z - h.z);
-        l.w = tf32_round(v.w - h.w);
-        const uint32_t off = slice_off(r, 4 * c);
-        *reinterpret_cast<float4*>(hi + off) = h;
-        *reinterpret_cast<float4*>(lo + off) = l;
+        if ((it & 255) == 255 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
     }
 }
 
-// C may overlap A (the in-place panel product): a CTA reads all of its A rows
-// before it writes its C tile, and no other CTA reads them
-__global__ void __launch_bounds__(GT) k_gemm_tf32x3(int K, const float* A, int lda,
-                                                    const float* __restrict__ B, int ldb, float* C, int ldc,
-                                                    float alpha, float beta, int lower_only, int* __restrict__ err) {
+// Operand packing: the TF32 high and low parts of a row-major FP32 matrix
+// (rows a multiple of 128, K a multiple of 32), each 128 x 32 slice stored as
+// one contiguous 16 KB block already in the canonical shared-memory layout
+// (slice (mt, kt) at ((mt * K / 32) + kt) * 4096 floats), so that the product
+// kernel moves whole slices with one bulk copy each.
+__global__ void k_pack_tf32(const float* __restrict__ X, int ld, int rows, int K, float* __restrict__ hi,
+                            float* __restrict__ lo) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // 16-byte chunk
+    const int kq = K / 4;
+    if (q >= (long long)rows * kq) return;
+    const int r = (int)(q / kq), c4 = (int)(q % kq);
+    const float4 v = *reinterpret_cast<const float4*>(X + (long long)r * ld + 4 * c4);
+    float4 h, l;
+    h.x = tf32_round(v.x);
+    h.y = tf32_round(v.y);
+    h.z = tf32_round(v.z);
+    h.w = tf32_round(v.w);
+    l.x = tf32_round(v.x - h.x);
+    l.y = tf32_round(v.y - h.y);
+    l.z = tf32_round(v.z - h.z);
+    l.w = tf32_round(v.w - h.w);
+    const long long slice = (long long)(r / GT) * (K / GK) + (4 * c4) / GK;
+    const long long off = slice * (GT * GK) + slice_off(r % GT, (4 * c4) % GK) / 4;
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// One CTA per 128 x 128 tile of C.  Thread 32 (producer) fills a free stage
+// with the four slices of K slice kc (bulk copies, completion counted in
+// bytes on full[s]); thread 0 (consumer) waits for full[s], issues the 12
+// MMAs of the slice and commits them to empty[s]; after the last slice a
+// commit to done releases the epilogue (all four warps read their TMEM lane
+// quarter).  Pa*/Pb*: packed operands; mt, nt: tile row / column.
+__global__ void __launch_bounds__(GT) k_gemm_tf32x3(int K, const float* __restrict__ Pah,
+                                                    const float* __restrict__ Pal, const float* __restrict__ Pbh,
+                                                    const float* __restrict__ Pbl, float* C, int ldc, float alpha,
+                                                    float beta, int lower_only, int* __restrict__ err) {
     const int tm = blockIdx.y, tn = blockIdx.x;
     if (lower_only && tn > tm) return;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* stage0 = smem;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE_BYTES + 64);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+    uint64_t* empty = full + NSTAGE;
+    uint64_t* done = empty + NSTAGE;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int fail;
     const int t = threadIdx.x, warp = t >> 5;
     if (t == 0) {
-        for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        fail = 0;
+        for (int s = 0; s < NSTAGE; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -141,26 +169,38 @@ __global__ void __launch_bounds__(GT) k_gemm_tf32x3(int K, const float* A, int l
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const int m0 = tm * GT, n0 = tn * GT;
     const int nk = K / GK;
-    bool ok = true;
-    for (int kc = 0; kc < nk; ++kc) {
-        const int s = kc & 1;
-        uint8_t* st = stage0 + s * STAGE_BYTES;
-        // the MMAs that last read this stage (slice kc - 2) must be done; the
-        // decision to go on is the same for every thread of the CTA
-        if (kc >= 2) ok = mbar_wait(smem_u32(&mbar[s]), ((kc - 2) >> 1) & 1);
-        if (!__syncthreads_and(ok ? 1 : 0)) {
-            ok = false;
-            break;
+    const long long a0 = (long long)tm * nk * (GT * GK), b0 = (long long)tn * nk * (GT * GK);
+    const uint32_t base = smem_u32(smem);
+    if (t == 32) {
+        // producer
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % NSTAGE;
+            if (kc >= NSTAGE && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((kc / NSTAGE - 1) & 1))) {
+                fail = 1;
+                break;
+            }
+            if (*(volatile int*)&fail) break;
+            const uint32_t fb = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES)
+                         : "memory");
+            const uint32_t st = base + s * STAGE_BYTES;
+            const long long so = (long long)kc * (GT * GK);
+            bulk_g2s(st, Pah + a0 + so, SLICE_BYTES, fb);
+            bulk_g2s(st + SLICE_BYTES, Pal + a0 + so, SLICE_BYTES, fb);
+            bulk_g2s(st + 2 * SLICE_BYTES, Pbh + b0 + so, SLICE_BYTES, fb);
+            bulk_g2s(st + 3 * SLICE_BYTES, Pbl + b0 + so, SLICE_BYTES, fb);
         }
-        stage_slice(A, lda, m0, kc * GK, st, st + SLICE_BYTES);
-        stage_slice(B, ldb, n0, kc * GK, st + 2 * SLICE_BYTES, st + 3 * SLICE_BYTES);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (t == 0) {
+    } else if (t == 0) {
+        // consumer: the MMA issuer
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % NSTAGE;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kc / NSTAGE) & 1))) {
+                fail = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + SLICE_BYTES;
+            const uint32_t a_hi = base + s * STAGE_BYTES, a_lo = a_hi + SLICE_BYTES;
             const uint32_t b_hi = a_hi + 2 * SLICE_BYTES, b_lo = a_hi + 3 * SLICE_BYTES;
 #pragma unroll
             for (int j = 0; j < GK / 8; ++j) {
@@ -172,18 +212,21 @@ __global__ void __launch_bounds__(GT) k_gemm_tf32x3(int K, const float* A, int l
                 mma_tf32(tmem, dah, dbl, 1u);
                 mma_tf32(tmem, dal, dbh, 1u);
             }
-            mma_commit(smem_u32(&mbar[s]));
+            mma_commit(smem_u32(&empty[s]));
         }
+        mma_commit(smem_u32(done));  // every MMA issued above
     }
-    // the last commit covers every MMA issued before it
-    if (ok && nk > 0) ok = mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1);
+    __syncthreads();
+    // the accumulator is final once done completes (bounded wait)
+    bool ok = !fail && nk > 0;
+    if (ok) ok = mbar_wait(smem_u32(done), 0);
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!ok && t == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        // warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane
-        const int row = m0 + warp * 32 + (t & 31);
-        float* Cr = C + (long long)row * ldc + n0;
+        // warp w reads TMEM lanes 32w..32w+31 = rows 32w + lane of the tile
+        const int row = tm * GT + warp * 32 + (t & 31);
+        float* Cr = C + (long long)row * ldc + tn * GT;
 #pragma unroll 1
         for (int c0 = 0; c0 < GT; c0 += 8) {
             uint32_t v[8];
@@ -211,45 +254,73 @@ __global__ void __launch_bounds__(GT) k_gemm_tf32x3(int K, const float* A, int l
 // Cholesky of the P x P diagonal block at (k, k) of A (ld) in shared memory:
 // A_kk = L L^T, L written back (lower, zeros above), Dinv = L^-1 (lower, P x
 // P row-major).  info = global pivot index + 1 if a pivot <= min_pivot.
-__global__ void __launch_bounds__(GT) k_diag_block(float* __restrict__ A, int ld, int k, float* __restrict__ Dinv,
-                                                   int* __restrict__ info, float min_pivot) {
+// 512 threads: thread (tx, ty) = (t % 32, t / 32) owns the elements (ty + 16a,
+// tx + 32b) of the 128 x 128 block for the rank-1 updates of both phases.
+constexpr int DB_THREADS = 512;
+__global__ void __launch_bounds__(DB_THREADS) k_diag_block(float* __restrict__ A, int ld, int k,
+                                                           float* __restrict__ Dinv, int* __restrict__ info,
+                                                           float min_pivot) {
     extern __shared__ __align__(16) float sm[];
-    float* L = sm;                   // [GT][GT + 1]
-    float* X = sm + GT * (GT + 1);   // [GT][GT + 1]
-    const int t = threadIdx.x;
+    constexpr int LD = GT + 1;
+    float* L = sm;             // [GT][GT + 1]
+    float* X = sm + GT * LD;   // [GT][GT + 1]
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     float* Akk = A + (long long)k * GT * ld + (long long)k * GT;
-    for (int r = 0; r < GT; ++r) L[r * (GT + 1) + t] = Akk[(long long)r * ld + t];
+    for (int e = t; e < GT * GT; e += DB_THREADS) {
+        const int r = e >> 7, c = e & (GT - 1);
+        L[r * LD + c] = Akk[(long long)r * ld + c];
+        X[r * LD + c] = r == c ? 1.0f : 0.0f;
+    }
     __syncthreads();
+    // right-looking Cholesky: pivot, column scale, rank-1 update of the rest
     for (int j = 0; j < GT; ++j) {
         if (t == 0) {
-            float dj = L[j * (GT + 1) + j];
+            float dj = L[j * LD + j];
             if (!(dj > min_pivot)) {
                 if (*info == 0) *info = k * GT + j + 1;
                 dj = fmaxf(fabsf(dj), min_pivot > 0.f ? min_pivot : 1e-30f);
             }
-            L[j * (GT + 1) + j] = sqrtf(dj);
+            L[j * LD + j] = sqrtf(dj);
         }
         __syncthreads();
-        const float djj = L[j * (GT + 1) + j];
-        if (t > j) L[t * (GT + 1) + j] /= djj;
+        const float djj = L[j * LD + j];
+        if (t > j && t < GT) L[t * LD + j] /= djj;
         __syncthreads();
-        // trailing update of column t (rows >= t) by column j
-        if (t > j) {
-            const float ltj = L[t * (GT + 1) + j];
-            for (int i = t; i < GT; ++i) L[i * (GT + 1) + t] -= L[i * (GT + 1) + j] * ltj;
+#pragma unroll
+        for (int a = 0; a < GT / 16; ++a) {
+            const int i = ty + 16 * a;
+            if (i <= j) continue;
+            const float lij = L[i * LD + j];
+#pragma unroll
+            for (int b = 0; b < GT / 32; ++b) {
+                const int c = tx + 32 * b;
+                if (c > j && c <= i) L[i * LD + c] -= lij * L[c * LD + j];
+            }
         }
         __syncthreads();
     }
-    // X = L^-1: thread t solves L x = e_t (column t of X) by forward substitution
-    for (int r = 0; r < GT; ++r) {
-        float s = (r == t) ? 1.0f : 0.0f;
-        for (int q = t; q < r; ++q) s -= L[r * (GT + 1) + q] * X[q * (GT + 1) + t];
-        X[r * (GT + 1) + t] = (r >= t) ? s / L[r * (GT + 1) + r] : 0.0f;
+    // X = L^-1 by forward elimination applied to the identity
+    for (int j = 0; j < GT; ++j) {
+        const float inv = 1.0f / L[j * LD + j];
+        if (t <= j) X[j * LD + t] *= inv;
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < GT / 16; ++a) {
+            const int i = ty + 16 * a;
+            if (i <= j) continue;
+            const float lij = L[i * LD + j];
+#pragma unroll
+            for (int b = 0; b < GT / 32; ++b) {
+                const int c = tx + 32 * b;
+                if (c <= j) X[i * LD + c] -= lij * X[j * LD + c];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int r = 0; r < GT; ++r) {
-        Akk[(long long)r * ld + t] = (t <= r) ? L[r * (GT + 1) + t] : 0.0f;
-        Dinv[r * GT + t] = X[r * (GT + 1) + t];
+    for (int e = t; e < GT * GT; e += DB_THREADS) {
+        const int r = e >> 7, c = e & (GT - 1);
+        Akk[(long long)r * ld + c] = c <= r ? L[r * LD + c] : 0.0f;
+        Dinv[r * GT + c] = c <= r ? X[r * LD + c] : 0.0f;
     }
 }
 
@@ -289,16 +360,39 @@ void set_attributes() {
 
 void gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, float alpha,
                  float beta, bool lower_only, int* err_dev, cudaStream_t s) {
-    if (M % GT || N % GT || K % GK || lda % 4 || ldb % 4)
-        throw Error{IBR_EINVAL, "gemm_tf32x3: M, N must be multiples of 128, K of 32, lda and ldb of 4"};
+    if (M % GT || N % GT || K % GK || K == 0 || lda % 4 || ldb % 4)
+        throw Error{IBR_EINVAL, "gemm_tf32x3: M, N must be multiples of 128, K a positive multiple of 32, lda and ldb "
+                                "multiples of 4"};
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
         throw Error{IBR_EINVAL, "gemm_tf32x3: A and B must be 16-byte aligned"};
     if (M == 0 || N == 0) return;
     set_attributes();
-    ProfScope ps(KID_TC_GEMM, s, 4.0 * ((double)M * K + (double)N * K + 2.0 * M * N));
-    dim3 grid(N / GT, M / GT);
-    k_gemm_tf32x3<<<grid, GT, GEMM_SMEM, s>>>(K, A, lda, B, ldb, C, ldc, alpha, beta, lower_only ? 1 : 0, err_dev);
-    IBR_CHECK_LAUNCH();
+    // pack A (and B unless it is the same matrix) into TF32 hi / lo slices
+    const bool same = A == B && lda == ldb && M == N;
+    const size_t ea = (size_t)M * K, eb = same ? 0 : (size_t)N * K;
+    float* pk = nullptr;
+    IBR_CUDA_TRY(cudaMallocAsync(&pk, (2 * ea + 2 * eb) * sizeof(float), s));
+    float *pah = pk, *pal = pk + ea, *pbh = same ? pah : pk + 2 * ea, *pbl = same ? pal : pk + 2 * ea + eb;
+    {
+        ProfScope ps(KID_TC_GEMM, s, 12.0 * (double)(ea + eb));
+        k_pack_tf32<<<grid_1d((long long)ea / 4, 256), 256, 0, s>>>(A, lda, M, K, pah, pal);
+        IBR_CHECK_LAUNCH();
+        if (!same) {
+            k_pack_tf32<<<grid_1d((long long)eb / 4, 256), 256, 0, s>>>(B, ldb, N, K, pbh, pbl);
+            IBR_CHECK_LAUNCH();
+        }
+    }
+    {
+        // executed tensor FLOPs: three TF32 products per output over the tiles computed
+        const double tiles = lower_only ? (double)(M / GT) * (M / GT + 1) / 2.0 : (double)(M / GT) * (N / GT);
+        ProfScope ps(KID_TC_GEMM, s, 8.0 * ((double)M * K + (double)N * K) + 4.0 * 2.0 * M * N,
+                     3.0 * 2.0 * tiles * GT * GT * (double)K);
+        dim3 grid(N / GT, M / GT);
+        k_gemm_tf32x3<<<grid, GT, GEMM_SMEM, s>>>(K, pah, pal, pbh, pbl, C, ldc, alpha, beta, lower_only ? 1 : 0,
+                                                  err_dev);
+        IBR_CHECK_LAUNCH();
+    }
+    IBR_CUDA_TRY(cudaFreeAsync(pk, s));
 }
 
 // M (n x n SPD, FP32, row-major) -> M^-1 on the tensor cores: padded to a
@@ -325,8 +419,8 @@ void spd_inverse_tc(int n, float* M, int* info_dev, double min_pivot, double pad
     for (int k = 0; k < nb; ++k) {
         {
             ProfScope ps(KID_SPD_INV, s, 4.0 * 3 * GT * GT);
-            k_diag_block<<<1, GT, 2 * GT * (GT + 1) * sizeof(float), s>>>(P, np, k, Dinv + (long long)k * GT * GT,
-                                                                          info_dev, (float)min_pivot);
+            k_diag_block<<<1, DB_THREADS, 2 * GT * (GT + 1) * sizeof(float), s>>>(
+                P, np, k, Dinv + (long long)k * GT * GT, info_dev, (float)min_pivot);
             IBR_CHECK_LAUNCH();
         }
         const int rest = np - (k + 1) * GT;
