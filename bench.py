@@ -120,25 +120,21 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def source_sha():
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1505_07865_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
-    return h.hexdigest()[:16]
+def file_sha(name):
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_1505_07865_gb300", "csrc", name), "rb").read()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel, launch_bytes):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured from the current sources (else None)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    source file that holds the kernel is unchanged since the capture (else None)."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
     except (OSError, ValueError):
         return None
-    if t.get("source_sha") != source_sha():
-        return None
     k = t.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    if k is None or k.get("source_sha") != file_sha(k.get("source_file", "")):
+        return None
+    return k.get("dram_bytes_per_launch")
 
 
 def cpu_oracle_sample(seconds_budget=20.0):

@@ -254,73 +254,134 @@ __global__ void __launch_bounds__(GT) k_gemm_tf32x3(int K, const float* __restri
 // Cholesky of the P x P diagonal block at (k, k) of A (ld) in shared memory:
 // A_kk = L L^T, L written back (lower, zeros above), Dinv = L^-1 (lower, P x
 // P row-major).  info = global pivot index + 1 if a pivot <= min_pivot.
-// 512 threads: thread (tx, ty) = (t % 32, t / 32) owns the elements (ty + 16a,
-// tx + 32b) of the 128 x 128 block for the rank-1 updates of both phases.
+// Blocked by 32 (P = 4 x 32): warp 0 factors and inverts each 32 x 32
+// diagonal block in registers (lane i holds row i; values move by shuffles);
+// the 16 warps then form the panel below it (A_ik W_k^T, W_k = L_kk^-1) and the
+// trailing update; finally X = L^-1 block row by block row,
+// X_ik = -W_i sum_{j=k}^{i-1} L_ij X_jk.
 constexpr int DB_THREADS = 512;
+constexpr int DB_LD = GT + 1;
+constexpr int DB_SMEM = (2 * GT * DB_LD + 4 * 32 * 33 + 32 * 97) * (int)sizeof(float);
+
 __global__ void __launch_bounds__(DB_THREADS) k_diag_block(float* __restrict__ A, int ld, int k,
                                                            float* __restrict__ Dinv, int* __restrict__ info,
                                                            float min_pivot) {
     extern __shared__ __align__(16) float sm[];
-    constexpr int LD = GT + 1;
-    float* L = sm;             // [GT][GT + 1]
-    float* X = sm + GT * LD;   // [GT][GT + 1]
-    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    float* L = sm;                    // [GT][DB_LD]
+    float* X = L + GT * DB_LD;        // [GT][DB_LD]
+    float* W = X + GT * DB_LD;        // [4][32][33]: inverses of the 32 x 32 diagonal blocks
+    float* T = W + 4 * 32 * 33;       // [32][97]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned FULL = 0xffffffffu;
     float* Akk = A + (long long)k * GT * ld + (long long)k * GT;
     for (int e = t; e < GT * GT; e += DB_THREADS) {
         const int r = e >> 7, c = e & (GT - 1);
-        L[r * LD + c] = Akk[(long long)r * ld + c];
-        X[r * LD + c] = r == c ? 1.0f : 0.0f;
+        L[r * DB_LD + c] = Akk[(long long)r * ld + c];
+        X[r * DB_LD + c] = 0.0f;
     }
     __syncthreads();
-    // right-looking Cholesky: pivot, column scale, rank-1 update of the rest
-    for (int j = 0; j < GT; ++j) {
-        if (t == 0) {
-            float dj = L[j * LD + j];
-            if (!(dj > min_pivot)) {
-                if (*info == 0) *info = k * GT + j + 1;
-                dj = fmaxf(fabsf(dj), min_pivot > 0.f ? min_pivot : 1e-30f);
+    const float floor_piv = min_pivot > 0.f ? min_pivot : 1e-30f;
+    for (int kb = 0; kb < 4; ++kb) {
+        const int o = kb * 32;
+        if (warp == 0) {
+            float r[32], x[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) r[c] = L[(o + lane) * DB_LD + o + c];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                float djj = __shfl_sync(FULL, r[j], j);
+                if (!(djj > min_pivot)) {
+                    if (lane == j && *info == 0) *info = k * GT + o + j + 1;
+                    djj = fmaxf(fabsf(djj), floor_piv);
+                }
+                const float sq = sqrtf(djj);
+                r[j] = lane == j ? sq : (lane > j ? r[j] / sq : r[j]);
+#pragma unroll
+                for (int c = j + 1; c < 32; ++c) {
+                    const float lcj = __shfl_sync(FULL, r[j], c);
+                    if (lane >= c) r[c] -= r[j] * lcj;
+                }
             }
-            L[j * LD + j] = sqrtf(dj);
+            // column `lane` of the inverse by forward substitution
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) {
+                float s = lane == rr ? 1.0f : 0.0f;
+#pragma unroll
+                for (int q = 0; q < rr; ++q) s -= __shfl_sync(FULL, r[q], rr) * x[q];
+                const float lrr = __shfl_sync(FULL, r[rr], rr);
+                x[rr] = rr >= lane ? s / lrr : 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                L[(o + lane) * DB_LD + o + c] = c <= lane ? r[c] : 0.0f;
+                W[(kb * 32 + c) * 33 + lane] = x[c];
+                X[(o + c) * DB_LD + o + lane] = x[c];
+            }
         }
         __syncthreads();
-        const float djj = L[j * LD + j];
-        if (t > j && t < GT) L[t * LD + j] /= djj;
-        __syncthreads();
+        const int R0 = o + 32;
+        if (R0 < GT) {
+            // panel: L[r][o + c] = sum_{q <= c} A[r][o + q] W_kb[c][q], rows r >= R0
+            float pv[(GT - 32) * 32 / DB_THREADS];
+            const int ne = (GT - R0) * 32;
 #pragma unroll
-        for (int a = 0; a < GT / 16; ++a) {
-            const int i = ty + 16 * a;
-            if (i <= j) continue;
-            const float lij = L[i * LD + j];
-#pragma unroll
-            for (int b = 0; b < GT / 32; ++b) {
-                const int c = tx + 32 * b;
-                if (c > j && c <= i) L[i * LD + c] -= lij * L[c * LD + j];
+            for (int u = 0; u < (GT - 32) * 32 / DB_THREADS; ++u) {
+                const int e = t + u * DB_THREADS;
+                float acc = 0.0f;
+                if (e < ne) {
+                    const int r = R0 + (e >> 5), c = e & 31;
+                    for (int q = 0; q <= c; ++q) acc += L[r * DB_LD + o + q] * W[(kb * 32 + c) * 33 + q];
+                }
+                pv[u] = acc;
             }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < (GT - 32) * 32 / DB_THREADS; ++u) {
+                const int e = t + u * DB_THREADS;
+                if (e < ne) L[(R0 + (e >> 5)) * DB_LD + o + (e & 31)] = pv[u];
+            }
+            __syncthreads();
+            // trailing update of the lower part at rows, columns >= R0
+            const int tx = lane, ty = warp;
+#pragma unroll
+            for (int a = 0; a < GT / 16; ++a) {
+                const int i = ty + 16 * a;
+                if (i < R0) continue;
+#pragma unroll
+                for (int b = 0; b < GT / 32; ++b) {
+                    const int c = tx + 32 * b;
+                    if (c < R0 || c > i) continue;
+                    float acc = 0.0f;
+#pragma unroll 8
+                    for (int q = 0; q < 32; ++q) acc += L[i * DB_LD + o + q] * L[c * DB_LD + o + q];
+                    L[i * DB_LD + c] -= acc;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    // X = L^-1 by forward elimination applied to the identity
-    for (int j = 0; j < GT; ++j) {
-        const float inv = 1.0f / L[j * LD + j];
-        if (t <= j) X[j * LD + t] *= inv;
+    // X = L^-1 by block rows: T = sum_j L_ij X_j. (columns < 32 i), X_i. = -W_i T
+    for (int ib = 1; ib < 4; ++ib) {
+        const int o = ib * 32, nc = ib * 32;
+        for (int e = t; e < 32 * nc; e += DB_THREADS) {
+            const int q = e / nc, col = e % nc;
+            float acc = 0.0f;
+            for (int m = (col >> 5) << 5; m < o; ++m) acc += L[(o + q) * DB_LD + m] * X[m * DB_LD + col];
+            T[q * 97 + col] = acc;
+        }
         __syncthreads();
-#pragma unroll
-        for (int a = 0; a < GT / 16; ++a) {
-            const int i = ty + 16 * a;
-            if (i <= j) continue;
-            const float lij = L[i * LD + j];
-#pragma unroll
-            for (int b = 0; b < GT / 32; ++b) {
-                const int c = tx + 32 * b;
-                if (c <= j) X[i * LD + c] -= lij * X[j * LD + c];
-            }
+        for (int e = t; e < 32 * nc; e += DB_THREADS) {
+            const int q = e / nc, col = e % nc;
+            float acc = 0.0f;
+            for (int p = 0; p <= q; ++p) acc += W[(ib * 32 + q) * 33 + p] * T[p * 97 + col];
+            X[(o + q) * DB_LD + col] = -acc;
         }
         __syncthreads();
     }
     for (int e = t; e < GT * GT; e += DB_THREADS) {
         const int r = e >> 7, c = e & (GT - 1);
-        Akk[(long long)r * ld + c] = c <= r ? L[r * LD + c] : 0.0f;
-        Dinv[r * GT + c] = c <= r ? X[r * LD + c] : 0.0f;
+        Akk[(long long)r * ld + c] = c <= r ? L[r * DB_LD + c] : 0.0f;
+        Dinv[r * GT + c] = c <= r ? X[r * DB_LD + c] : 0.0f;
     }
 }
 
@@ -349,8 +410,7 @@ __global__ void k_sym_out(int n, int np, const float* __restrict__ P, float* __r
 void set_attributes() {
     static const bool done = [] {
         IBR_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
-        IBR_CUDA_TRY(cudaFuncSetAttribute(k_diag_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(2 * GT * (GT + 1) * sizeof(float))));
+        IBR_CUDA_TRY(cudaFuncSetAttribute(k_diag_block, cudaFuncAttributeMaxDynamicSharedMemorySize, DB_SMEM));
         return true;
     }();
     (void)done;
@@ -419,7 +479,7 @@ void spd_inverse_tc(int n, float* M, int* info_dev, double min_pivot, double pad
     for (int k = 0; k < nb; ++k) {
         {
             ProfScope ps(KID_SPD_INV, s, 4.0 * 3 * GT * GT);
-            k_diag_block<<<1, DB_THREADS, 2 * GT * (GT + 1) * sizeof(float), s>>>(
+            k_diag_block<<<1, DB_THREADS, DB_SMEM, s>>>(
                 P, np, k, Dinv + (long long)k * GT * GT, info_dev, (float)min_pivot);
             IBR_CHECK_LAUNCH();
         }
