@@ -441,6 +441,8 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(launches),
         "roofline": roof,
         "tensor_roofline": tensor_roof,
+        "smoother_tiles": [{"level": list(t[:3]), "fields": t[3], "bytes": t[4], "block": [32, t[5]], "kz": t[6]}
+                           for t in abi.tuned_smoother_tiles()],
         "kernel_breakdown": breakdown,
         "clocks": clk,
         "cpu_baseline": cpu,

@@ -445,6 +445,15 @@ int ibr_profile_reset(void);
 int ibr_profile_read(int idx, char* name, int name_len, long long* launches, double* ms, double* bytes,
                      double* flops);
 
+/* The smoother tiles picked by the library's autotuner: the red-black half
+ * sweep of a periodic 3-D multigrid level runs 32 x by threads per block,
+ * each on a column of kz cells; the first multigrid set-up of each level
+ * shape times the candidates (by in {4, 8}, kz in {2..32}) on scratch arrays
+ * and keeps the fastest (IBR_TUNE=0 in the environment: a fixed heuristic).
+ * Entry idx: shape_c_esz[5] = n0, n1, n2, stacked fields, element bytes; by;
+ * kz (any pointer may be NULL).  IBR_EINVAL past the last entry. */
+int ibr_tuned_smoother_tile(int idx, int* shape_c_esz, int* by, int* kz);
+
 /* Destroys the grid and frees its device memory. NULL is accepted. */
 int ibr_destroy_grid(ibr_grid* g);
 

@@ -190,6 +190,7 @@ _SIGS = {
                                        _D, _D]),
     "ibr_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "ibr_server_destroy": (ctypes.c_int, [_P]),
+    "ibr_tuned_smoother_tile": (ctypes.c_int, [ctypes.c_int, _I, _I, _I]),
     "ibr_launch_count": (ctypes.c_longlong, []),
     "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ibr_profile_reset": (ctypes.c_int, []),
@@ -560,3 +561,15 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def tuned_smoother_tiles():
+    """[(n0, n1, n2, stacked fields, element bytes, by, kz)] picked by the smoother autotuner."""
+    out = []
+    i = 0
+    v = (ctypes.c_int * 5)()
+    by, kz = ctypes.c_int(), ctypes.c_int()
+    while _lib.ibr_tuned_smoother_tile(i, v, ctypes.byref(by), ctypes.byref(kz)) == OK:
+        out.append(tuple(v) + (by.value, kz.value))
+        i += 1
+    return out

@@ -151,6 +151,12 @@ inline int mg_coarse_sweeps(const Geo& g) {
 // raises the shared-memory limit of the tail kernel (call outside stream capture)
 template <typename T>
 void mg_set_attributes();
+// times the half-sweep tiles of a periodic 3-D level (C stacked fields) once
+// per level shape and keeps the fastest (no-op elsewhere and during capture)
+template <typename T>
+void mg_tune_smoother(const Geo& g, int C, cudaStream_t s);
+// tuned tile idx: n0, n1, n2, C, element size, by, kz (false past the end)
+bool tuned_tile(int idx, int* out7);
 // q = -D y - hd ; (P_S middle factor, Sec. V.B)
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s);

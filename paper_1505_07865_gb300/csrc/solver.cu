@@ -245,6 +245,11 @@ struct PC {
         long long nS = G->nS;
         mg.init(G->geo, G->d);
         mg_set_attributes<T>();
+        // smoother tiles of the levels (d stacked velocity components, and the pressure)
+        for (const Geo& lg : mg.lev) {
+            mg_tune_smoother<T>(lg, G->d, G->stream);
+            mg_tune_smoother<T>(lg, 1, G->stream);
+        }
         Vi = dalloc<T>((size_t)(ns + 1) * nS);
         Zi = dalloc<T>((size_t)ns * nS);
         w = dalloc<T>(nS);
@@ -1935,6 +1940,17 @@ int ibr_op_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float
         }
         IBR_CUDA_TRY(cudaFreeAsync(err, s));
         if (herr) throw Error{IBR_ECUDA, "a tensor-core product timed out waiting for its MMAs"};
+    });
+}
+
+int ibr_tuned_smoother_tile(int idx, int* shape_c_esz, int* by, int* kz) {
+    return run_guarded("ibr_tuned_smoother_tile", [&] {
+        int v[7];
+        require(tuned_tile(idx, v), "no tuned tile with this index");
+        if (shape_c_esz)
+            for (int q = 0; q < 5; ++q) shape_c_esz[q] = v[q];
+        if (by) *by = v[5];
+        if (kz) *kz = v[6];
     });
 }
 

@@ -13,6 +13,11 @@
 // instances are the plain wrapped stencils.  Boundary data enters only the
 // right-hand side (wall_lift).
 #include <algorithm>
+#include <array>
+#include <cstdlib>
+#include <iterator>
+#include <map>
+#include <mutex>
 
 #include "ibr_internal.cuh"
 
@@ -447,11 +452,12 @@ __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __rest
 // cells along z at fixed (ih, j): the y wrap and the block decomposition
 // are paid once per column, the cells of a column are independent (one
 // colour) so their loads overlap.  Same arithmetic and summation order as
-// rbgs_cell, so the result is bitwise that of k_rbgs.
+// rbgs_cell, so the result is bitwise that of k_rbgs, whatever the tile
+// (32 x by threads, kz cells each; picked per level shape by the tuner).
 template <typename T>
 __global__ void __launch_bounds__(256) k_rbgs_col(T* __restrict__ u, const T* __restrict__ f, Geo g, int nkb, int kz,
                                                   T kh2, T inv_diag, int color, int zero_init) {
-    const int ih = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int ih = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     const int cmp = blockIdx.z / nkb, kb = blockIdx.z - cmp * nkb;
     if (ih >= (g.n0 >> 1) || j >= g.n1) return;
     const long long off = (long long)cmp * g.ncell;
@@ -760,6 +766,105 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
     IBR_CHECK_LAUNCH();
 }
 
+// Tile autotuner of the periodic 3-D column smoother: per level shape (n0,
+// n1, n2, C, element size) the block height by (of 32 x by threads) and the
+// column length kz with the shortest measured half sweep.  Tuning runs once
+// per shape and process, on scratch arrays (the result does not depend on
+// the tile), outside stream capture (from the multigrid set-up); until a
+// shape is tuned, or with IBR_TUNE=0, the fixed heuristic tile is used.
+struct ColTile {
+    int by, kz;
+};
+std::mutex g_tile_mu;
+std::map<std::array<long long, 5>, ColTile> g_tiles;
+
+ColTile col_tile_heuristic(const Geo& g, int C) {
+    // columns of kz cells; kz shrinks on small levels to keep ~1.5e5 threads busy
+    const long long cells = (long long)(g.n0 >> 1) * g.n1 * g.n2 * C;
+    return ColTile{BY, (int)std::min<long long>(8, std::max<long long>(1, cells / 150000))};
+}
+
+ColTile col_tile(const Geo& g, int C, size_t esz) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tiles.find({g.n0, g.n1, g.n2, C, (long long)esz});
+    return it != g_tiles.end() ? it->second : col_tile_heuristic(g, C);
+}
+
+template <typename T>
+void launch_col(const Geo& g, T* u, const T* f, int C, ColTile t, T kh2, T inv, int color, int zi, cudaStream_t s) {
+    const int nkb = (g.n2 + t.kz - 1) / t.kz;
+    dim3 gc(((g.n0 >> 1) + 31) / 32, (g.n1 + t.by - 1) / t.by, nkb * C), blk(32, t.by);
+    k_rbgs_col<T><<<gc, blk, 0, s>>>(u, f, g, nkb, t.kz, kh2, inv, color, zi);
+}
+
+template <typename T>
+void mg_tune_smoother(const Geo& g, int C, cudaStream_t s) {
+    if (g.d != 3 || g.wall) return;
+    const long long cells = (long long)(g.n0 >> 1) * g.n1 * g.n2 * C;
+    if (cells < (1LL << 17)) return;  // small levels: latency-bound, the heuristic is fine
+    static const bool off = [] {
+        const char* e = std::getenv("IBR_TUNE");
+        return e && e[0] == '0';
+    }();
+    if (off) return;
+    const std::array<long long, 5> key = {g.n0, g.n1, g.n2, C, (long long)sizeof(T)};
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        if (g_tiles.count(key)) return;
+    }
+    cudaStreamCaptureStatus cs;
+    IBR_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return;
+    const size_t n = (size_t)C * g.ncell;
+    T *u = nullptr, *f = nullptr;
+    IBR_CUDA_TRY(cudaMallocAsync(&u, n * sizeof(T), s));
+    IBR_CUDA_TRY(cudaMallocAsync(&f, n * sizeof(T), s));
+    IBR_CUDA_TRY(cudaMemsetAsync(u, 0, n * sizeof(T), s));
+    IBR_CUDA_TRY(cudaMemsetAsync(f, 0, n * sizeof(T), s));
+    cudaEvent_t e0, e1;
+    IBR_CUDA_TRY(cudaEventCreate(&e0));
+    IBR_CUDA_TRY(cudaEventCreate(&e1));
+    const T kh2 = (T)1, inv = (T)(1.0 / 6.0);
+    ColTile best = col_tile_heuristic(g, C);
+    float best_ms = 1e30f;
+    const int bys[] = {4, 8};  // 32 x by threads within the kernel's launch bound of 256
+    const int kzs[] = {2, 4, 6, 8, 11, 16, 22, 32};
+    for (int by : bys)
+        for (int kz : kzs) {
+            if (kz > g.n2) continue;
+            const ColTile t{by, kz};
+            for (int r = 0; r < 2; ++r) launch_col<T>(g, u, f, C, t, kh2, inv, r & 1, 0, s);
+            IBR_CUDA_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < 6; ++r) launch_col<T>(g, u, f, C, t, kh2, inv, r & 1, 0, s);
+            IBR_CUDA_TRY(cudaEventRecord(e1, s));
+            IBR_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            IBR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    IBR_CUDA_TRY(cudaGetLastError());
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    IBR_CUDA_TRY(cudaFreeAsync(u, s));
+    IBR_CUDA_TRY(cudaFreeAsync(f, s));
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tiles[key] = best;
+}
+
+bool tuned_tile(int idx, int* out7) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    if (idx < 0 || idx >= (int)g_tiles.size()) return false;
+    auto it = g_tiles.begin();
+    std::advance(it, idx);
+    for (int q = 0; q < 5; ++q) out7[q] = (int)it->first[q];
+    out7[5] = it->second.by;
+    out7[6] = it->second.kz;
+    return true;
+}
+
 template <typename T>
 void mg_smooth(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, double kappa, int color,
                bool zero_init, cudaStream_t s) {
@@ -774,12 +879,7 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, do
         if (g.wall) {
             k_rbgs<3, true, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
         } else {
-            // columns of kz cells; kz shrinks on small levels to keep ~1.5e5 threads busy
-            const long long cells = (long long)(g.n0 >> 1) * g.n1 * g.n2 * C;
-            int kz = (int)std::min<long long>(8, std::max<long long>(1, cells / 150000));
-            const int nkb = (g.n2 + kz - 1) / kz;
-            dim3 gc(((g.n0 >> 1) + BX - 1) / BX, (g.n1 + BY - 1) / BY, nkb * C);
-            k_rbgs_col<T><<<gc, blk, 0, s>>>(u, f, g, nkb, kz, kh2, inv, color, zi);
+            launch_col<T>(g, u, f, C, col_tile(g, C, sizeof(T)), kh2, inv, color, zi, s);
         }
     } else {
         T inv = rbgs_inv_diag<2, T>(sg, kh2);
@@ -990,6 +1090,7 @@ void wall_lift(const Geo& g, int a, int side, const double* data, double* b, dou
     template void mg_prolong_correct<T>(const Geo&, const Geo&, T*, const T*, int, int, cudaStream_t);    \
     template void mg_coarse_solve<T>(const Geo&, T*, const T*, int, int, double, double, int, cudaStream_t); \
     template void mg_set_attributes<T>();                                                                   \
+    template void mg_tune_smoother<T>(const Geo&, int, cudaStream_t);                                       \
     template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, int, double, double, bool, \
                                int, int, int, cudaStream_t);                                                \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \

@@ -158,9 +158,11 @@ def test_mtilde_solve_inverts(abi, prec, tol):
         abi.destroy_grid(G)
 
 
-@pytest.mark.parametrize("n,sigma", [((64, 64), 0.0), ((48, 32), 5e3), ((32, 32, 32), 0.0), ((24, 16, 32), 1e4)])
+@pytest.mark.parametrize("n,sigma", [((64, 64), 0.0), ((48, 32), 5e3), ((32, 32, 32), 0.0), ((24, 16, 32), 1e4),
+                                     ((96, 64, 64), 0.0)])
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
 def test_vcycle_converges_to_exact_solution(abi, n, sigma, prec):
+    # (96, 64, 64): a level large enough for the smoother's tile autotuner
     d = len(n)
     L = [v / n[0] for v in n]
     wl = Workload("mg", n, tuple(L), bodies=[Body(np.array(L) * 0.5, np.zeros((1, d)) + 0.01, np.zeros(d + (1 if d == 2 else 3)))])
@@ -187,3 +189,22 @@ def test_vcycle_converges_to_exact_solution(abi, n, sigma, prec):
         assert rate < 0.35 or errs[-1] < floor * 10, (errs, rate)
     finally:
         abi.destroy_grid(G)
+
+
+def test_smoother_tiles_are_tuned_candidates(abi):
+    # after a 3-D solve whose finest level is large enough, the tuner has picked
+    # a tile for it from its candidate sets; the half sweep is the same for any
+    # tile (the cells of one colour are independent), which the V-cycle test on
+    # the (96, 64, 64) grid checks against the exact solution
+    wl = Workload("tune", (64, 64, 64), (1.0, 1.0, 1.0),
+                  bodies=[Body(np.array([0.5, 0.5, 0.5]), sphere_markers(0.2, 120), np.ones(6))], tol=1e-8)
+    G = gpu_grid(abi, wl, abi.MIXED)
+    try:
+        abi.solve_coupled(G, wl.UO(), opts=abi.solve_opts_default())
+    finally:
+        abi.destroy_grid(G)
+    tiles = abi.tuned_smoother_tiles()
+    mine = [t for t in tiles if t[:3] == (64, 64, 64) and t[4] == 4]
+    assert {t[3] for t in mine} == {1, 3}
+    for t in mine:
+        assert t[5] in (4, 8) and t[6] in (2, 4, 6, 8, 11, 16, 22, 32)
