@@ -249,6 +249,25 @@ def dense_leg(abi, torch, stream, pk):
     return out
 
 
+def replica_max(dist, x, device):
+    """The largest value of x over all ranks (the slowest replica's timed
+    region); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(dist, world, steps, local_ms, device):
+    """Whole-job throughput of `world` replicas that each ran `steps` units in
+    local_ms: all units over the slowest replica's time; (max ms, units/s)."""
+    ms = replica_max(dist, local_ms, device)
+    return ms, world * steps / (ms / 1000.0)
+
+
 def make_grid(abi, torch, wl, precision, stream):
     body = wl.bodies[0]
     G = abi.create_grid(3, wl.n, wl.L, eta=wl.eta, precision=precision, stream=stream.cuda_stream)
@@ -313,11 +332,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(dist, x, "cuda")
 
     # ---- mixed precision (the flagship path), device-resident inputs -------
     G = make_grid(abi, torch, wl, abi.MIXED, stream)
@@ -327,8 +342,7 @@ def run_ours(args, world, rank, local):
     total_ms, per, infos, launches = timed_solves(abi, torch, G, wl, stream, UOs, args.warmup, args.steps)
     clk = clocks.stop()
     barrier()
-    total_ms = max_over_ranks(total_ms)
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms, value = replica_throughput(dist, world, args.steps, total_ms, "cuda")
     if args.quick:
         abi.destroy_grid(G)
         if rank == 0:
