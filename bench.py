@@ -698,6 +698,21 @@ def run_serve(args):
         _run_batch_once(abi, S, wreq, abi.MIXED, mo)
         s1, _ = _run_batch_once(abi, S, sample, abi.MIXED, mo)
     errs = [float(np.linalg.norm(m["lam"] - f["lam"]) / np.linalg.norm(f["lam"])) for m, f in zip(out, o64)]
+    # where a large request's time goes: the request with the most markers of
+    # the sample, solved alone with every launch timed (graphs off)
+    big = max(sample, key=lambda r: r.N)
+    with abi.Server(slots=1, budget_bytes=budget) as S:
+        abi.profile_reset()
+        abi.profile_enable(True)
+        pb = S.poll(_server_submit(S, big, abi.MIXED, opts=mo))
+        abi.profile_enable(False)
+        prof = abi.profile_read()
+        abi.profile_reset()
+    top = sorted(((k, v) for k, v in prof.items() if not k.endswith("@large")), key=lambda kv: -kv[1][1])[:10]
+    big_profile = {"request": {"n": big.n[0], "bodies": len(big.rels), "markers": big.N,
+                               "largest_body": max(r.shape[0] for r in big.rels)},
+                   "iters": pb["iters"], "ms_setup": pb["ms_setup"], "ms_solve": pb["ms_solve"],
+                   "kernels_ms": {k: round(v[1], 2) for k, v in top}}
     res = {"metric": "served 3-D rigid-body IB solves/s at rel. residual 1e-8; p50/p99 ms",
            "value": value, "unit": "solves/s", "n_gpus": 1, "steps": len(out), "warmup": len(wreq),
            "ms_per_step": 1000.0 / value, "higher_is_better": True, "dtype": "f64+f32 (mixed)", "data": "synthetic",
@@ -714,6 +729,8 @@ def run_serve(args):
            "iters_per_solve": float(np.mean([m["iters"] for m in out])),
            "all_ok": all(m["status"] == 0 for m in out),
            "max_rel_err_lambda_vs_fp64_gpu_sample": max(errs),
+           "iters_by_request": [[r.n[0], len(r.rels), r.N, m["iters"]] for r, m in zip(reqs, out)],
+           "largest_request_profile": big_profile,
            "server": st, "gpu_launches": int(launches), "clocks": clk}
     print(json.dumps(res), flush=True)
 

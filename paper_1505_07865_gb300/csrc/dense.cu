@@ -5,6 +5,8 @@
 // The factorisation is a blocked right-looking Cholesky on 32x32 tiles
 // (diagonal tile factor + inverse in shared memory, panel = A_ik X_kk^T,
 // trailing rank-32 update), then X = L^-1 tile by tile, then M^-1 = X^T X.
+#include <type_traits>
+
 #include "ibr_internal.cuh"
 
 namespace ibr {
@@ -226,16 +228,17 @@ __device__ __forceinline__ void pair_window(const Geo& g, const double* p, int a
     }
 }
 
+// one thread per unordered pair (i <= j; 16 x 16 blocks, those wholly below
+// the diagonal exit): it forms M~_ij and writes it and its transpose M~_ji
 template <int D>
-__global__ void k_pair_mtilde(Geo g, int nr, const double* __restrict__ q, int S, const double* __restrict__ x0,
-                              const float* __restrict__ tab, double* __restrict__ M) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)nr * nr) return;
-    const int i = (int)(t / nr), j = (int)(t % nr);
+__global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double* __restrict__ q, int S,
+                                                     const double* __restrict__ x0, const float* __restrict__ tab,
+                                                     double* __restrict__ M) {
+    if (blockIdx.x < blockIdx.y) return;
+    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    if (i >= nr || j >= nr || j < i) return;
     const int ns[3] = {g.n0, g.n1, g.n2};
-    // acc[0]: sum_s T_s(q_i - q_j);  acc[1]: sum_s T_s(q_j - q_i)^T.  Thread
-    // (j, i) computes the same two sums transposed and swapped, and their sum
-    // does not depend on the order: the block is exactly symmetric
+    // acc[0]: sum_s T_s(q_i - q_j);  acc[1]: sum_s T_s(q_j - q_i)^T
     double acc[2][D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -293,7 +296,11 @@ __global__ void k_pair_mtilde(Geo g, int nr, const double* __restrict__ q, int S
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b) M[((long long)i * D + a) * ld + (long long)j * D + b] = sc * (acc[0][a][b] + acc[1][a][b]);
+        for (int b = 0; b < D; ++b) {
+            const double v = sc * (acc[0][a][b] + acc[1][a][b]);
+            M[((long long)i * D + a) * ld + (long long)j * D + b] = v;
+            M[((long long)j * D + b) * ld + (long long)i * D + a] = v;  // exactly symmetric
+        }
 }
 
 template <int D>
@@ -344,7 +351,25 @@ __global__ void k_bd_gemv(int B, const long long* __restrict__ moff, const int* 
     int row = warp - r0;
     const T* Mr = M + moff[b] + (long long)row * nr;
     double acc = 0.0;
-    for (int c = lane; c < nr; c += 32) acc += (double)Mr[c] * (double)rhs[r0 + c];
+    if (std::is_same<T, float>::value && std::is_same<Tv, float>::value) {
+        // FP32 path: per-lane FP32 sums (FP64 arithmetic runs at a small
+        // fraction of the FP32 rate on this part), combined in FP64 across
+        // lanes; four independent partial sums per lane
+        const float* Mf = reinterpret_cast<const float*>(Mr);
+        const float* xf = reinterpret_cast<const float*>(rhs) + r0;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int c = lane;
+        for (; c + 96 < nr; c += 128) {
+            a0 = fmaf(Mf[c], xf[c], a0);
+            a1 = fmaf(Mf[c + 32], xf[c + 32], a1);
+            a2 = fmaf(Mf[c + 64], xf[c + 64], a2);
+            a3 = fmaf(Mf[c + 96], xf[c + 96], a3);
+        }
+        for (; c < nr; c += 32) a0 = fmaf(Mf[c], xf[c], a0);
+        acc = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+    } else {
+        for (int c = lane; c < nr; c += 32) acc += (double)Mr[c] * (double)rhs[r0 + c];
+    }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) out[warp] = (Tv)acc;
 }
@@ -365,10 +390,12 @@ void pair_mtilde(const Geo& g, int nr, const double* q, int S, const double* x0,
                  cudaStream_t s) {
     const long long n = (long long)nr * nr;
     ProfScope ps(KID_MTILDE, s, (double)n * g.d * g.d * 8);
+    const int nt = (nr + 15) / 16;
+    dim3 grid(nt, nt), blk(16, 16);
     if (g.d == 3)
-        k_pair_mtilde<3><<<grid_1d(n, 128), 128, 0, s>>>(g, nr, q, S, x0, tab, M);
+        k_pair_mtilde<3><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
     else
-        k_pair_mtilde<2><<<grid_1d(n, 128), 128, 0, s>>>(g, nr, q, S, x0, tab, M);
+        k_pair_mtilde<2><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
     IBR_CHECK_LAUNCH();
 }
 

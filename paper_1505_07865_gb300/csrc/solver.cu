@@ -131,7 +131,16 @@ struct Body {
 // of its solves, largest d N of one dense block for all markers
 constexpr int PAIR_S = 2;
 constexpr int PAIR_NS = 8;
-constexpr long long PAIR_FULL_MAX = 6144;
+constexpr long long PAIR_FULL_MAX_DEFAULT = 6144;
+// IBR_PAIR_FULL_MAX in the environment overrides the single-block limit
+long long pair_full_max() {
+    static const long long v = [] {
+        const char* e = std::getenv("IBR_PAIR_FULL_MAX");
+        const long long x = e ? std::atoll(e) : 0;
+        return x > 0 ? x : PAIR_FULL_MAX_DEFAULT;
+    }();
+    return v;
+}
 
 template <typename T>
 struct PC;
@@ -917,7 +926,7 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     const bool true_mob = o.mob_model == IBR_MOB_TRUE;
     const bool pair_mob = o.mob_model == IBR_MOB_PAIR;
     require(!(pair_mob && G->walls()), "IBR_MOB_PAIR needs a periodic grid");
-    const bool one_block = true_mob || (pair_mob && (long long)N * d <= PAIR_FULL_MAX);
+    const bool one_block = true_mob || (pair_mob && (long long)N * d <= pair_full_max());
     G->nblk = one_block ? 1 : B;
     const int nblk = G->nblk;
     G->moff.assign(nblk + 1, 0);
@@ -1425,7 +1434,7 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
         }
         t += mg64 + pg(8.0 * (PAIR_NS + 1) * nS) + pg(8.0 * PAIR_NS * nS) + 8 * pg(8.0 * nS) + pg(8.0 * d * nc) +
              3 * pg(8.0 * nc);
-        if (dN <= PAIR_FULL_MAX) blk2 = blkmax = dN * dN;
+        if (dN <= (double)pair_full_max()) blk2 = blkmax = dN * dN;
     }
     // mobility: built (FP64) + factorised inverse (precision) + work: the FP64
     // path's work block, or the tensor-core path's two padded blocks
@@ -1433,8 +1442,10 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
     if (precision == IBR_FP64) {
         t += pg(e * blkmax);
     } else {
+        // padded block, X^T, the panel product, the diagonal inverses, and the
+        // packed TF32 hi / lo operands of the largest product
         const double np = std::ceil(std::sqrt(blkmax) / 128.0) * 128.0;
-        t += 2 * pg(4.0 * np * np) + pg(4.0 * np * 128.0) + pg(4.0 * np * 128.0);
+        t += 2 * pg(4.0 * np * np) + pg(4.0 * np * 128.0) + pg(4.0 * np * 128.0) + pg(8.0 * np * np);
     }
     return (long long)(t + 16.0 * 1048576.0);
 }
