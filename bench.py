@@ -61,6 +61,8 @@ def parse():
                     help="batch / serve: approximate mobility (pair: the grid's tabulated pair mobility; auto: the "
                          "analytic forms)")
     ap.add_argument("--re", type=float, default=10.0, help="Reynolds number of the nozzle workload")
+    ap.add_argument("--n-s", type=int, default=0, help="inner iterations N_s (0: the library's automatic choice)")
+    ap.add_argument("--mg", default="2,2", help="pre,post multigrid sweeps per level")
     return ap.parse_args()
 
 
@@ -276,10 +278,16 @@ def make_grid(abi, torch, wl, precision, stream):
     return G
 
 
+SCHEDULE = {"n_s": 0, "mg_pre": 2, "mg_post": 2}
+
+
 def timed_solves(abi, torch, G, wl, stream, UOs, warmup, steps, e2e=False, host_bufs=None, mob_model=0):
     opts = abi.solve_opts_default()
     opts.tol = TOL
     opts.mob_model = mob_model
+    opts.n_s = SCHEDULE["n_s"]
+    opts.mg_pre = SCHEDULE["mg_pre"]
+    opts.mg_post = SCHEDULE["mg_post"]
     rel = wl.bodies[0].rel
     infos = []
 
@@ -348,6 +356,7 @@ def run_ours(args, world, rank, local):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "quick": True,
+                              "schedule": dict(SCHEDULE),
                               "iters_per_solve": float(np.mean([i.iters for i in infos])),
                               "gpu_launches": int(launches)}), flush=True)
         if dist is not None:
@@ -434,7 +443,8 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tol": TOL, "precision": "mixed", "restart": 50, "n_s": 2,
+        "config": {"workload": WORKLOAD, "tol": TOL, "precision": "mixed", "restart": 50,
+                   "n_s": SCHEDULE["n_s"] or 2, "mg_sweeps": [SCHEDULE["mg_pre"], SCHEDULE["mg_post"]],
                    "preconditioner": "lower-triangular Schur", "setup_in_step": True,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (FP64 system vector 67 MB, Krylov basis > 1 GB)"},
@@ -737,6 +747,8 @@ def run_serve(args):
 
 def main():
     args = parse()
+    pre, post = (int(x) for x in args.mg.split(","))
+    SCHEDULE.update(n_s=args.n_s, mg_pre=pre, mg_post=post)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
