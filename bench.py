@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--re", type=float, default=10.0, help="Reynolds number of the nozzle workload")
     ap.add_argument("--n-s", type=int, default=0, help="inner iterations N_s (0: the library's automatic choice)")
     ap.add_argument("--mg", default="2,2", help="pre,post multigrid sweeps per level")
+    ap.add_argument("--restart", type=int, default=50, help="FGMRES restart length")
     return ap.parse_args()
 
 
@@ -278,7 +279,7 @@ def make_grid(abi, torch, wl, precision, stream):
     return G
 
 
-SCHEDULE = {"n_s": 0, "mg_pre": 2, "mg_post": 2}
+SCHEDULE = {"n_s": 0, "mg_pre": 2, "mg_post": 2, "restart": 50}
 
 
 def timed_solves(abi, torch, G, wl, stream, UOs, warmup, steps, e2e=False, host_bufs=None, mob_model=0):
@@ -288,6 +289,7 @@ def timed_solves(abi, torch, G, wl, stream, UOs, warmup, steps, e2e=False, host_
     opts.n_s = SCHEDULE["n_s"]
     opts.mg_pre = SCHEDULE["mg_pre"]
     opts.mg_post = SCHEDULE["mg_post"]
+    opts.restart = SCHEDULE["restart"]
     rel = wl.bodies[0].rel
     infos = []
 
@@ -443,7 +445,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tol": TOL, "precision": "mixed", "restart": 50,
+        "config": {"workload": WORKLOAD, "tol": TOL, "precision": "mixed", "restart": SCHEDULE["restart"],
                    "n_s": SCHEDULE["n_s"] or 2, "mg_sweeps": [SCHEDULE["mg_pre"], SCHEDULE["mg_post"]],
                    "preconditioner": "lower-triangular Schur", "setup_in_step": True,
                    "parallelism": f"replicas x{world}",
@@ -550,6 +552,7 @@ def _mob_opts(abi, args):
     o = abi.solve_opts_default()
     o.tol = TOL
     o.mob_model = abi.MOB_PAIR if args.mob == "pair" else abi.MOB_AUTO
+    o.restart = args.restart
     return o
 
 
@@ -729,7 +732,7 @@ def run_serve(args):
            "config": {"workload": f"Poisson arrivals at {args.rate:g}/s, n~U{{64,96,128,192}}^3, 1-16 spheres / "
                                   "prolate ellipsoids (aspect U[1,3], b U[0.05,0.12]), markers <= 2.2h, U~N(0,1)",
                       "requests": len(out), "slots": args.slots, "budget_bytes": budget, "autotune": args.autotune,
-                      "mobility": args.mob},
+                      "mobility": args.mob, "restart": args.restart},
            "p50_ms": p50, "p99_ms": p99, "stream_wall_s": wall,
            "mean_queue_ms": float(np.mean([m["t_start_ms"] - m["t_submit_ms"] for m in out])),
            "mean_run_ms": float(np.mean([m["t_end_ms"] - m["t_start_ms"] for m in out])),
@@ -748,7 +751,7 @@ def run_serve(args):
 def main():
     args = parse()
     pre, post = (int(x) for x in args.mg.split(","))
-    SCHEDULE.update(n_s=args.n_s, mg_pre=pre, mg_post=post)
+    SCHEDULE.update(n_s=args.n_s, mg_pre=pre, mg_post=post, restart=args.restart)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -235,3 +235,49 @@ def test_many_requests_complete(abi):
     for i in range(k):
         for j in (i + k, i + 2 * k, i + 3 * k):
             assert np.array_equal(out[i]["lam"], out[j]["lam"])
+
+
+def test_malformed_requests_are_rejected_at_submit(abi):
+    r = _mix()[0]
+    with abi.Server(slots=1, budget_bytes=1 << 30) as S:
+        with pytest.raises(abi.IbrError) as e:
+            S.submit((31, 32), (1.0, 1.0), r.centers, r.rels, r.UO)  # odd cell count
+        assert e.value.code == abi.EINVAL
+        with pytest.raises(abi.IbrError) as e:
+            S.submit(r.n, r.L, r.centers, r.rels, r.UO, eta=0.0)
+        assert e.value.code == abi.EINVAL
+        assert S.stats()["submitted"] == 0
+
+
+def test_free_body_and_precisions_through_the_engine(abi):
+    # a free body (given force and torque) and FP64 / mixed requests of the same
+    # shape in one engine: each result equals the direct solve of that request
+    rng = np.random.default_rng(17)
+    n = 32
+    h = 1.0 / n
+    cs = [np.array([0.3, 0.5]), np.array([0.7, 0.52])]
+    rels = [disk_markers(3.5 * h, h), disk_markers(3.0 * h, h)]
+    UO = rng.standard_normal((2, 3))
+    req = Request((n, n), cs, [np.array([1.0, 0, 0, 0])] * 2, rels, UO)
+    kin = [abi.PRESCRIBED, abi.FREE]
+    direct = {}
+    for prec in (abi.MIXED, abi.FP64):
+        G = abi.create_grid(2, (n, n), (1.0, 1.0), precision=prec)
+        try:
+            for c, rel, k in zip(cs, rels, kin):
+                b = abi.add_body(G, c, kinematics=k)
+                abi.set_markers(G, b, rel)
+            abi.solve_coupled(G, UO, opts=_opts(abi))
+            direct[prec] = abi.get_forces(G, 2)
+        finally:
+            abi.destroy_grid(G)
+    with abi.Server(slots=2, budget_bytes=4 << 30) as S:
+        ts = {prec: S.submit(req.n, req.L, cs, rels, UO, precision=prec, kinematics=kin, opts=_opts(abi))
+              for prec in (abi.MIXED, abi.FP64)}
+        out = {prec: S.poll(t) for prec, t in ts.items()}
+    for prec in (abi.MIXED, abi.FP64):
+        assert out[prec]["status"] == abi.OK
+        assert np.array_equal(out[prec]["lam"], direct[prec][0])
+        assert np.array_equal(out[prec]["ft"], direct[prec][1])
+    # the free body's load is balanced: K^T Lambda equals the applied force/torque
+    assert np.allclose(out[abi.FP64]["ft"][1], UO[1], rtol=1e-8, atol=1e-10)
