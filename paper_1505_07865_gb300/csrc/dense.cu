@@ -230,6 +230,29 @@ __device__ __forceinline__ void pair_window(const Geo& g, const double* p, int a
 
 // one thread per unordered pair (i <= j; 16 x 16 blocks, those wholly below
 // the diagonal exit): it forms M~_ij and writes it and its transpose M~_ji
+// the same window with FP32 weights (the table is FP32): the position and
+// its offset from the window's first node stay FP64, the kernel value and the
+// 4^d-cell sums of the M~ build run on the FP32 pipe
+__device__ __forceinline__ float peskin4f(float r) {
+    r = fabsf(r);
+    if (r < 1.0f) return 0.125f * (3.0f - 2.0f * r + sqrtf(1.0f + 4.0f * r - 4.0f * r * r));
+    if (r < 2.0f) return 0.125f * (5.0f - 2.0f * r - sqrtf(fmaxf(-7.0f + 12.0f * r - 4.0f * r * r, 0.0f)));
+    return 0.0f;
+}
+
+template <int D>
+__device__ __forceinline__ void pair_window_f(const Geo& g, const double* p, int al, int* j0, float (*w)[4]) {
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const double sb = p[b] / g.h - (al == b ? 0.0 : 0.5);
+        const double fl = floor(sb);
+        j0[b] = (int)fl - 1;
+        const float fr = (float)(sb - fl);  // in [0, 1)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) w[b][m] = peskin4f(fr + 1.0f - (float)m);
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double* __restrict__ q, int S,
                                                      const double* __restrict__ x0, const float* __restrict__ tab,
@@ -260,14 +283,14 @@ __global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double
 #pragma unroll
             for (int al = 0; al < D; ++al) {
                 int j0[D];
-                double w[D][4];
-                pair_window<D>(g, p, al, j0, w);
-                double sum[D];
+                float w[D][4];
+                pair_window_f<D>(g, p, al, j0, w);
+                float sum[D];
 #pragma unroll
-                for (int be = 0; be < D; ++be) sum[be] = 0.0;
+                for (int be = 0; be < D; ++be) sum[be] = 0.0f;
                 for (int c = 0; c < (1 << (2 * D)); ++c) {
                     long long cell = 0, stride = 1;
-                    double wt = 1.0;
+                    float wt = 1.0f;
 #pragma unroll
                     for (int b = 0; b < D; ++b) {
                         const int m = (c >> (2 * b)) & 3;
@@ -279,14 +302,14 @@ __global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double
                     }
 #pragma unroll
                     for (int be = 0; be < D; ++be)
-                        sum[be] += wt * (double)tab[((long long)(s * D + be) * D + al) * g.ncell + cell];
+                        sum[be] = fmaf(wt, tab[((long long)(s * D + be) * D + al) * g.ncell + cell], sum[be]);
                 }
 #pragma unroll
                 for (int be = 0; be < D; ++be) {
                     if (tr == 0)
-                        acc[0][al][be] += sum[be];
+                        acc[0][al][be] += (double)sum[be];
                     else
-                        acc[1][be][al] += sum[be];
+                        acc[1][be][al] += (double)sum[be];
                 }
             }
         }

@@ -2,8 +2,11 @@
 tabulated pair mobility (periodic grids).
 
   - the dense M~ block the library builds equals the oracle's
-    pair_table_mtilde (same source points) to the precision of the FP32
-    table (2e-6 of the largest entry), one block coupling all bodies;
+    pair_table_mtilde (same source points) to the precision of its FP32
+    arithmetic: an FP32 table, FP32 kernel weights and FP32 sums over the
+    4^d window cells (each sum's rounding is at most 4^d * 2^-24 ~ 4e-6 of
+    the largest table value, typically far less): 5e-6 of the largest entry,
+    one block coupling all bodies;
   - the constrained solve with it matches the oracle (1e-9 at residual
     1e-10): M~ changes iteration counts only (Sec. V.A);
   - it needs fewer outer iterations than the analytic forms on multi-body
@@ -71,7 +74,7 @@ def test_pair_mtilde_matches_oracle(abi, mk):
     pr = oracle_problem(wl)
     Mo = mobility.pair_table_mtilde(pr.grid, pr.q, mobility.pair_sources(wl.n, pr.grid.h, d))
     assert np.array_equal(Mg, Mg.T)
-    assert np.abs(Mg - Mo).max() < 2e-6 * np.abs(Mo).max()
+    assert np.abs(Mg - Mo).max() < 5e-6 * np.abs(Mo).max()
 
 
 @pytest.mark.parametrize("prec", ["MIXED", "FP64"])
