@@ -374,7 +374,7 @@ __global__ void k_bd_gemv(int B, const long long* __restrict__ moff, const int* 
     int row = warp - r0;
     const T* Mr = M + moff[b] + (long long)row * nr;
     double acc = 0.0;
-    if (std::is_same<T, float>::value && std::is_same<Tv, float>::value) {
+    if constexpr (std::is_same<T, float>::value && std::is_same<Tv, float>::value) {
         // FP32 path: per-lane FP32 sums (FP64 arithmetic runs at a small
         // fraction of the FP32 rate on this part), combined in FP64 across
         // lanes; four independent partial sums per lane
