@@ -25,6 +25,7 @@ __all__ = [
     "parabolic_inflow",
     "ellipsoid_markers",
     "random_quaternion",
+    "quat_matrix",
     "batch_2d",
     "serve_3d",
     "Request",
