@@ -1442,10 +1442,11 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
     if (precision == IBR_FP64) {
         t += pg(e * blkmax);
     } else {
-        // padded block, X^T, the panel product, the diagonal inverses, and the
-        // packed TF32 hi / lo operands of the largest product
+        // padded block, X = L^-1, X^T, the recursion's product buffer (np^2 / 4),
+        // the diagonal inverses, and the packed TF32 hi / lo operands of the
+        // largest product
         const double np = std::ceil(std::sqrt(blkmax) / 128.0) * 128.0;
-        t += 2 * pg(4.0 * np * np) + pg(4.0 * np * 128.0) + pg(4.0 * np * 128.0) + pg(8.0 * np * np);
+        t += 3 * pg(4.0 * np * np) + pg(np * np + 4.0 * 128.0 * 128.0) + pg(4.0 * np * 128.0) + pg(8.0 * np * np);
     }
     return (long long)(t + 16.0 * 1048576.0);
 }

@@ -391,6 +391,26 @@ __global__ void k_put_diag_t(float* __restrict__ XT, int ld, int i, const float*
     for (int r = 0; r < GT; ++r) XT[(long long)(i * GT + r) * ld + i * GT + t] = Dinv[t * GT + r];
 }
 
+// X block (i, i) = Dinv_i (lower, zeros above)
+__global__ void k_put_diag(float* __restrict__ X, int ld, int i, const float* __restrict__ Dinv) {
+    const int t = threadIdx.x;
+    for (int r = 0; r < GT; ++r) X[(long long)(i * GT + r) * ld + i * GT + t] = Dinv[r * GT + t];
+}
+
+// dst[c][r] = src[r][c] for a rows x cols block (both multiples of 32),
+// through 32 x 33 shared-memory tiles; blocks of 32 x 8 threads
+__global__ void k_transpose_block(const float* __restrict__ src, int lds, float* __restrict__ dst, int ldd, int rows,
+                                  int cols) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    if (r0 >= rows || c0 >= cols) return;
+    for (int y = threadIdx.y; y < 32; y += 8)
+        tile[y][threadIdx.x] = src[(long long)(r0 + y) * lds + c0 + threadIdx.x];
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8)
+        dst[(long long)(c0 + y) * ldd + r0 + threadIdx.x] = tile[threadIdx.x][y];
+}
+
 // padded copy: P = [[M, 0], [0, pad I]] (n x n inside np x np)
 __global__ void k_pad_in(int n, int np, const float* __restrict__ M, float* __restrict__ P, float pad) {
     const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -455,20 +475,46 @@ void gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, i
     IBR_CUDA_TRY(cudaFreeAsync(pk, s));
 }
 
+// X[b0:b1, b0:b1] = L[b0:b1, b0:b1]^-1 (blocks of 128; X lower, XT = X^T
+// upper, both row-major np x np, their diagonal blocks already set) by
+// splitting at m: X11 and X22 recursively, then
+//   TT  = XT11 L21^T        ( = (L21 X11)^T, s1 x s2 )
+//   X21 = -X22 TT^T         ( = -X22 L21 X11, s2 x s1 ), XT12 = X21^T.
+// The zero upper part of X22 and lower part of XT11 enter the products as is.
+void trtri_rec(int b0, int b1, int np, const float* L, float* X, float* XT, float* TT, int* err_dev, cudaStream_t s) {
+    if (b1 - b0 <= 1) return;
+    const int m = b0 + (b1 - b0) / 2;
+    trtri_rec(b0, m, np, L, X, XT, TT, err_dev, s);
+    trtri_rec(m, b1, np, L, X, XT, TT, err_dev, s);
+    const int s1 = (m - b0) * GT, s2 = (b1 - m) * GT;
+    const long long o11 = (long long)b0 * GT * np + (long long)b0 * GT;
+    const long long o21 = (long long)m * GT * np + (long long)b0 * GT;
+    const long long o22 = (long long)m * GT * np + (long long)m * GT;
+    const long long o12 = (long long)b0 * GT * np + (long long)m * GT;
+    gemm_tf32x3(s1, s2, s1, XT + o11, np, L + o21, np, TT, s2, 1.f, 0.f, false, err_dev, s);
+    gemm_tf32x3(s2, s1, s2, X + o22, np, TT, s2, X + o21, np, -1.f, 0.f, false, err_dev, s);
+    ProfScope ps(KID_SPD_INV, s, 8.0 * s1 * s2);
+    dim3 grid(s1 / 32, s2 / 32), blk(32, 8);
+    k_transpose_block<<<grid, blk, 0, s>>>(X + o21, np, XT + o12, np, s2, s1);
+    IBR_CHECK_LAUNCH();
+}
+
 // M (n x n SPD, FP32, row-major) -> M^-1 on the tensor cores: padded to a
 // multiple of 128 with an identity block, blocked right-looking Cholesky
 // (diagonal blocks on CUDA cores, panel A_ik L_kk^-T and trailing update
-// A_ij -= L_ik L_jk^T as tensor-core products), X^T = (L^-1)^T block column by
-// block column (U = X^T[0:i,0:i] L_i,0:i^T, X^T[0:i, i] = -U L_ii^-T), then
-// M^-1 = X^T (X^T)^T (lower tiles) and the symmetric n x n corner.
+// A_ij -= L_ik L_jk^T as tensor-core products), X = L^-1 and X^T
+// recursively by 2 x 2 blocks (trtri_rec), then M^-1 = X^T (X^T)^T (lower
+// tiles) and the symmetric n x n corner.
 void spd_inverse_tc(int n, float* M, int* info_dev, double min_pivot, double pad, int* err_dev, cudaStream_t s) {
     set_attributes();
     const int np = (n + GT - 1) / GT * GT;
     const int nb = np / GT;
-    float *P = nullptr, *XT = nullptr, *U = nullptr, *Dinv = nullptr;
+    float *P = nullptr, *X = nullptr, *XT = nullptr, *TT = nullptr, *Dinv = nullptr;
     IBR_CUDA_TRY(cudaMallocAsync(&P, (size_t)np * np * sizeof(float), s));
+    IBR_CUDA_TRY(cudaMallocAsync(&X, (size_t)np * np * sizeof(float), s));
     IBR_CUDA_TRY(cudaMallocAsync(&XT, (size_t)np * np * sizeof(float), s));
-    IBR_CUDA_TRY(cudaMallocAsync(&U, (size_t)np * GT * sizeof(float), s));
+    // the largest s1 x s2 product of the recursion: s1 + s2 <= np, so s1 s2 <= np^2 / 4
+    IBR_CUDA_TRY(cudaMallocAsync(&TT, ((size_t)np * np / 4 + (size_t)GT * GT) * sizeof(float), s));
     IBR_CUDA_TRY(cudaMallocAsync(&Dinv, (size_t)nb * GT * GT * sizeof(float), s));
     const long long np2 = (long long)np * np;
     {
@@ -491,20 +537,18 @@ void spd_inverse_tc(int n, float* M, int* info_dev, double min_pivot, double pad
             gemm_tf32x3(rest, rest, GT, pan, np, pan, np, tr, np, -1.f, 1.f, true, err_dev, s);
         }
     }
+    // X = L^-1 (and X^T) by the recursive 2 x 2 block formula
+    // X21 = -X22 L21 X11: every level's products span the whole block
+    IBR_CUDA_TRY(cudaMemsetAsync(X, 0, (size_t)np2 * sizeof(float), s));
     IBR_CUDA_TRY(cudaMemsetAsync(XT, 0, (size_t)np2 * sizeof(float), s));
     for (int i = 0; i < nb; ++i) {
-        {
-            ProfScope ps(KID_SPD_INV, s, 4.0 * 2 * GT * GT);
-            k_put_diag_t<<<1, GT, 0, s>>>(XT, np, i, Dinv + (long long)i * GT * GT);
-            IBR_CHECK_LAUNCH();
-        }
-        if (i > 0) {
-            const int m = i * GT;
-            gemm_tf32x3(m, GT, m, XT, np, P + (long long)i * GT * np, np, U, GT, 1.f, 0.f, false, err_dev, s);
-            gemm_tf32x3(m, GT, GT, U, GT, Dinv + (long long)i * GT * GT, GT, XT + (long long)i * GT, np, -1.f, 0.f,
-                        false, err_dev, s);
-        }
+        ProfScope ps(KID_SPD_INV, s, 4.0 * 3 * GT * GT);
+        k_put_diag<<<1, GT, 0, s>>>(X, np, i, Dinv + (long long)i * GT * GT);
+        IBR_CHECK_LAUNCH();
+        k_put_diag_t<<<1, GT, 0, s>>>(XT, np, i, Dinv + (long long)i * GT * GT);
+        IBR_CHECK_LAUNCH();
     }
+    trtri_rec(0, nb, np, P, X, XT, TT, err_dev, s);
     gemm_tf32x3(np, np, np, XT, np, XT, np, P, np, 1.f, 0.f, true, err_dev, s);
     {
         ProfScope ps(KID_SPD_INV, s, 4.0 * 2.0 * n * n);
@@ -512,8 +556,9 @@ void spd_inverse_tc(int n, float* M, int* info_dev, double min_pivot, double pad
         IBR_CHECK_LAUNCH();
     }
     IBR_CUDA_TRY(cudaFreeAsync(P, s));
+    IBR_CUDA_TRY(cudaFreeAsync(X, s));
     IBR_CUDA_TRY(cudaFreeAsync(XT, s));
-    IBR_CUDA_TRY(cudaFreeAsync(U, s));
+    IBR_CUDA_TRY(cudaFreeAsync(TT, s));
     IBR_CUDA_TRY(cudaFreeAsync(Dinv, s));
 }
 
