@@ -326,7 +326,8 @@ int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, double sigma, 
  * `restart`, inner iterations n_s (0: 2) in `precision` with mobility model
  * mob_model: the outer Krylov workspace, the preconditioner (multigrid levels,
  * inner basis, P_S work), the marker data, the dense mobility blocks (and for
- * IBR_MOB_PAIR its table and the solves that build it), each allocation of >= 1 MiB
+ * IBR_MOB_PAIR its table and the solves that build it; in IBR_MIXED the
+ * tensor-core factorisation's padded copies and packed operands), each allocation of >= 1 MiB
  * rounded up to the allocator's 2 MiB pages.  Used by the serving engine's
  * admission control; an upper estimate of the growth of device memory in use. */
 int ibr_estimate_device_bytes(int dim, const int* n, int n_bodies, const int* n_markers, int restart, int n_s,
@@ -423,6 +424,10 @@ int ibr_server_submit(ibr_server* s, const ibr_request* req, long long* ticket);
  * IBR_EINVAL for an unknown or already collected ticket. */
 int ibr_server_poll(ibr_server* s, long long ticket, double timeout_ms, ibr_result* res, double* Lambda,
                     double* body_FT, double* v, double* p);
+/* Counters of the engine since ibr_server_create (requests submitted /
+ * completed / rejected, queued and running now, device bytes reserved now and
+ * at most, the budget, grids created / reused, geometry reuses, evictions,
+ * resident grids, tuned shapes). */
 int ibr_server_get_stats(ibr_server* s, ibr_server_stats* out);
 /* Stops the engine: requests not yet started are dropped, running ones
  * finish, resident grids and uncollected results are freed. NULL accepted. */
