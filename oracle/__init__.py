@@ -13,7 +13,8 @@ Bodies", arXiv:1505.07865), in float64 NumPy:
 * ``mac``        -- staggered (MAC) grid, gradient G, divergence D = -G^T,
                     vector Laplacian, viscous operator A (Sec. III.B, Eq. A_def).
 * ``ib``         -- interpolation J, spreading S, S~ = S - vol^-1 1^T,
-                    rigid-body map K and K^T (Sec. III.A, III.D, Sec. II).
+                    rigid-body map K and K^T, the body rotation Q(q) of a
+                    unit quaternion (Sec. III.A, III.D, Sec. II).
 * ``system``     -- the constrained saddle-point operator (Eq. constrained_Stokes
                     / constrained_periodic), its right-hand side, and a dense
                     bordered LU solve on tiny grids.
@@ -26,7 +27,10 @@ Bodies", arXiv:1505.07865), in float64 NumPy:
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants, brute force and an independent route
-(dense LU vs DFT).  ``mobility.mtilde_2d_steady`` evaluates the App. B
+(dense LU vs DFT): among them the rotation direction of K and Q(q) by
+hand-computed rotations, and the whole constrained solve by first-order
+convergence to the analytic flow of a spinning disk inside a fixed ring
+(``test_oracle_convergence.py``, the 2-D analogue of Sec. VII.C).  ``mobility.mtilde_2d_steady`` evaluates the App. B
 functional form with caller-supplied coefficients (the paper does not print
 them); the form is pinned by its stated limits, the coefficient values are an
 input, not an oracle claim.

@@ -14,6 +14,10 @@ velocity Omega about its reference point X):
   K^T Lambda       = [sum_i Lambda_i ; sum_i (q_i - X) x Lambda_i]
 and the constraint row of Eq. constrained_Stokes reads -J v = W with
 W = -K U (the markers move rigidly, J v = K U).
+
+Body orientation (Sec. II): a body's markers sit at q_i = X + Q(q) r_i with
+r_i given in the body frame and Q(q) the rotation of the unit quaternion q
+(``quat_rotate``).
 """
 import numpy as np
 
@@ -107,6 +111,34 @@ def interp_bruteforce(grid, q, v):
 
 def n_rot(d):
     return 1 if d == 2 else 3
+
+
+def _hamilton(p, q):
+    """Quaternion product p q of (w, x, y, z) quaternions (rows of [..., 4])."""
+    pw, px, py, pz = p
+    qw, qx, qy, qz = q
+    return np.array([pw * qw - px * qx - py * qy - pz * qz,
+                     pw * qx + px * qw + py * qz - pz * qy,
+                     pw * qy - px * qz + py * qw + pz * qx,
+                     pw * qz + px * qy - py * qx + pz * qw])
+
+
+def quat_rotate(quat, r):
+    """Lab-frame offsets Q(q) r_i of body-frame offsets r[N, 3] (Sec. II: the
+    body's orientation; the marker positions are q_i = X + Q(q) r_i).
+
+    Written from the definition of a rotation by a unit quaternion: the pure
+    quaternion (0, r) is conjugated, q (0, r) q^*, one marker at a time; the
+    quaternion is normalised first."""
+    qq = np.asarray(quat, dtype=np.float64)
+    qq = qq / np.sqrt(np.sum(qq * qq))
+    conj = qq * np.array([1.0, -1.0, -1.0, -1.0])
+    r = np.asarray(r, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros_like(r)
+    for i in range(r.shape[0]):
+        pure = np.array([0.0, r[i, 0], r[i, 1], r[i, 2]])
+        out[i] = _hamilton(_hamilton(qq, pure), conj)[1:]
+    return out
 
 
 def apply_K(rel, body, UO, d):

@@ -9,7 +9,9 @@ continuous function with support [-2, 2] that satisfies, for every real shift s,
   sum_{j even} phi(s - j)      = 1/2      (even-odd condition)
   sum_j phi(s - j)^2           = 3/8      (sum of squares)
 
-and it is built from those four conditions (no pasted table or listing).
+``phi`` evaluates Peskin's published closed form of that function (the
+roots of the quadratic the conditions give on each unit interval); the tests
+check the four conditions themselves by brute force over many shifts.
 """
 import numpy as np
 

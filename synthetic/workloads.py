@@ -25,7 +25,6 @@ __all__ = [
     "parabolic_inflow",
     "ellipsoid_markers",
     "random_quaternion",
-    "quat_matrix",
     "batch_2d",
     "serve_3d",
     "Request",
@@ -256,13 +255,6 @@ def random_quaternion(rng):
     return np.array([q[3], q[0], q[1], q[2]])
 
 
-def quat_matrix(q):
-    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
-    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
-                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
-                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
-
-
 @dataclass
 class Request:
     """One independent periodic problem of a batch or a served stream: the
@@ -288,11 +280,15 @@ class Request:
     def N(self):
         return int(sum(r.shape[0] for r in self.rels))
 
-    def workload(self):
-        """The same problem as a Workload (markers rotated into the lab frame)."""
+    def workload(self, rotate=None):
+        """The same problem as a Workload, the body-frame offsets turned into
+        lab-frame ones by rotate(quat, rel) (3-D; the caller supplies the
+        rotation, this module holds geometry only)."""
         bodies = []
         for c, q, r, uo in zip(self.centers, self.quats, self.rels, self.UO):
-            rel = r if self.d == 2 else r @ quat_matrix(q).T
+            if self.d == 3 and rotate is None:
+                raise ValueError("a 3-D request needs the rotation of its quaternions")
+            rel = r if self.d == 2 else rotate(q, r)
             bodies.append(Body(np.asarray(c, dtype=np.float64), rel, np.asarray(uo)))
         return Workload(f"req_{'x'.join(map(str, self.n))}_{len(bodies)}b", tuple(self.n), self.L, bodies=bodies,
                         tol=1e-8)

@@ -20,7 +20,7 @@ What is checked:
 import numpy as np
 import pytest
 
-from oracle import fft_stokes
+from oracle import fft_stokes, ib
 from oracle.system import drag
 from synthetic import Request, disk_markers, random_quaternion, sphere_markers, ellipsoid_markers
 
@@ -70,7 +70,7 @@ def _submit(abi, S, r, prec, opts=None, want_fields=True):
 
 def _alone(abi, r, prec, tol=1e-10):
     """the same request solved by ibr_solve_coupled on its own grid"""
-    wl = r.workload()
+    wl = r.workload(ib.quat_rotate)
     G = abi.create_grid(r.d, r.n, r.L, precision=prec)
     try:
         for c, q, rel in zip(r.centers, r.quats, r.rels):
@@ -216,7 +216,7 @@ def test_autotuned_schedule(abi):
     assert len({(m["n_s"], m["mg_pre"], m["mg_post"]) for m in out}) == 1
     for k, (r, m) in enumerate(zip(reqs, out)):
         assert m["status"] == abi.OK and m["rel_res_true"] <= 1e-8 * (1 + 1e-9)
-        vo, po, lo, fo = _oracle(("tune", k), r.workload())
+        vo, po, lo, fo = _oracle(("tune", k), r.workload(ib.quat_rotate))
         assert rel_err(m["v"], vo) < 1e-7 and rel_err(m["lam"], lo) < 1e-7 and rel_err(m["ft"], fo) < 1e-7
 
 

@@ -89,3 +89,38 @@ def test_J_matrix_matches_matrix_free():
     v = [rng.standard_normal(g.shape) for _ in range(2)]
     Jm = ib.J_matrix(g, q)
     assert np.allclose(Jm @ flat(v), ib.interp(g, q, v).ravel(), atol=1e-13)
+
+
+def test_K_rotation_direction_closed_form():
+    # Omega x r with the right-hand rule (Sec. II): a counter-clockwise spin
+    # omega = 1 moves the lever arm (r, 0) along +y, and a spin about +z moves
+    # +x towards +y; K^T gives the matching torque r x F
+    r = 0.3
+    V = ib.apply_K(np.array([[r, 0.0], [0.0, r]]), np.array([0, 0]), np.array([[0.0, 0.0, 1.0]]), 2)
+    assert np.allclose(V, [[0.0, r], [-r, 0.0]], atol=1e-15)
+    V3 = ib.apply_K(np.eye(3), np.zeros(3, dtype=np.int64), np.array([[0, 0, 0, 0.0, 0.0, 2.0]]), 3)
+    assert np.allclose(V3, [[0.0, 2.0, 0.0], [-2.0, 0.0, 0.0], [0.0, 0.0, 0.0]], atol=1e-15)
+    V3 = ib.apply_K(np.eye(3), np.zeros(3, dtype=np.int64), np.array([[0, 0, 0, 1.0, 0.0, 0.0]]), 3)
+    assert np.allclose(V3, [[0.0, 0.0, 0.0], [0.0, 0.0, 1.0], [0.0, -1.0, 0.0]], atol=1e-15)
+    # a force +y at the lever arm +x turns the body counter-clockwise
+    FT = ib.apply_KT(np.array([[r, 0.0]]), np.array([0]), np.array([[0.0, 5.0]]), 2, 1)
+    assert np.allclose(FT, [[0.0, 5.0, 5.0 * r]], atol=1e-15)
+    FT3 = ib.apply_KT(np.array([[1.0, 0.0, 0.0]]), np.array([0]), np.array([[0.0, 0.0, 2.0]]), 3, 1)
+    assert np.allclose(FT3, [[0.0, 0.0, 2.0, 0.0, -2.0, 0.0]], atol=1e-15)
+
+
+def test_quaternion_rotation_hand_computed():
+    s = np.sqrt(0.5)
+    # 90 degrees about z: x -> y, y -> -x, z fixed
+    out = ib.quat_rotate([s, 0.0, 0.0, s], np.eye(3))
+    assert np.allclose(out, [[0, 1, 0], [-1, 0, 0], [0, 0, 1]], atol=1e-15)
+    # 90 degrees about x: y -> z, z -> -y
+    out = ib.quat_rotate([s, s, 0.0, 0.0], np.eye(3))
+    assert np.allclose(out, [[1, 0, 0], [0, 0, 1], [0, -1, 0]], atol=1e-15)
+    # 120 degrees about (1,1,1)/sqrt(3) cycles the axes: x -> y -> z -> x
+    c, t = np.cos(np.pi / 3), np.sin(np.pi / 3) / np.sqrt(3.0)
+    out = ib.quat_rotate([c, t, t, t], np.eye(3))
+    assert np.allclose(out, [[0, 1, 0], [0, 0, 1], [1, 0, 0]], atol=1e-15)
+    # 180 degrees about y: x -> -x; an unnormalised quaternion is normalised
+    out = ib.quat_rotate([0.0, 0.0, 3.0, 0.0], np.array([[1.0, 2.0, 3.0]]))
+    assert np.allclose(out, [[-1.0, 2.0, -3.0]], atol=1e-15)

@@ -6,7 +6,8 @@ given rate, and the same seed giving the same mix."""
 import numpy as np
 import pytest
 
-from synthetic import batch_2d, ellipsoid_markers, quat_matrix, random_quaternion, serve_3d
+from oracle.ib import quat_rotate
+from synthetic import batch_2d, ellipsoid_markers, random_quaternion, serve_3d
 from synthetic.workloads import _periodic_gap
 
 pytest.importorskip("scipy")
@@ -70,5 +71,5 @@ def test_random_quaternions_are_rotations():
     for _ in range(20):
         q = random_quaternion(rng)
         assert abs(np.linalg.norm(q) - 1.0) < 1e-12
-        R = quat_matrix(q)
+        R = quat_rotate(q, np.eye(3)).T  # columns: the images of e_x, e_y, e_z
         assert np.allclose(R @ R.T, np.eye(3)) and abs(np.linalg.det(R) - 1.0) < 1e-12
