@@ -459,6 +459,24 @@ int ibr_profile_read(int idx, char* name, int name_len, long long* launches, dou
  * kz (any pointer may be NULL).  IBR_EINVAL past the last entry. */
 int ibr_tuned_smoother_tile(int idx, int* shape_c_esz, int* by, int* kz);
 
+/* The V-cycle schedules picked by the library's autotuner (measurement
+ * support; the paper leaves the multigrid to the implementer, Sec. V.B).  On
+ * a periodic 3-D grid the coarse levels of a V-cycle can run in one launch:
+ * one thread-block cluster of 8 CTAs per stacked field, the levels split into
+ * z-slabs held in the CTAs' shared memory (neighbouring slabs read through
+ * distributed shared memory), the smallest levels in the first CTA.  The
+ * first multigrid set-up of each hierarchy shape times one V-cycle with the
+ * per-level kernels and with the cluster kernel taking over at each feasible
+ * level, and keeps the fastest (the V-cycle's result is the same for every
+ * schedule; IBR_TUNE=0 in the environment: a fixed rule, the cluster kernel
+ * from the finest level of at most 32768 cells; IBR_MG_CLUSTER=0: never;
+ * IBR_MG_CLUSTER_LEVEL=<l>: from level l wherever that is feasible).
+ * Entry idx: shape_l_c_esz[6] = n0, n1, n2 of the finest level, levels,
+ * stacked fields, element bytes; cluster_level = the level the cluster kernel
+ * starts at, -2 for none (any pointer may be NULL).  IBR_EINVAL past the last
+ * entry. */
+int ibr_tuned_vcycle_schedule(int idx, int* shape_l_c_esz, int* cluster_level);
+
 /* Destroys the grid and frees its device memory. NULL is accepted. */
 int ibr_destroy_grid(ibr_grid* g);
 

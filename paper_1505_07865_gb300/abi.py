@@ -191,6 +191,7 @@ _SIGS = {
     "ibr_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "ibr_server_destroy": (ctypes.c_int, [_P]),
     "ibr_tuned_smoother_tile": (ctypes.c_int, [ctypes.c_int, _I, _I, _I]),
+    "ibr_tuned_vcycle_schedule": (ctypes.c_int, [ctypes.c_int, _I, _I]),
     "ibr_launch_count": (ctypes.c_longlong, []),
     "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ibr_profile_reset": (ctypes.c_int, []),
@@ -571,5 +572,18 @@ def tuned_smoother_tiles():
     by, kz = ctypes.c_int(), ctypes.c_int()
     while _lib.ibr_tuned_smoother_tile(i, v, ctypes.byref(by), ctypes.byref(kz)) == OK:
         out.append(tuple(v) + (by.value, kz.value))
+        i += 1
+    return out
+
+
+def tuned_vcycle_schedules():
+    """[(n0, n1, n2, levels, stacked fields, element bytes, first cluster level or -2)]
+    picked by the V-cycle schedule autotuner."""
+    out = []
+    i = 0
+    v = (ctypes.c_int * 6)()
+    cl = ctypes.c_int()
+    while _lib.ibr_tuned_vcycle_schedule(i, v, ctypes.byref(cl)) == OK:
+        out.append(tuple(v) + (cl.value,))
         i += 1
     return out

@@ -1,6 +1,8 @@
 // Vector kernels of the Krylov solvers (Sec. V: FGMRES outer, GMRES(N_s) inner).
 // Dot products use a fixed grid and a fixed-order final sum, so results are
 // bitwise reproducible run to run.
+#include <type_traits>
+
 #include "ibr_internal.cuh"
 
 namespace ibr {
@@ -33,6 +35,32 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* out) {
     __syncthreads();
 }
 
+// block-reduce the first nq of NV values per thread into out[0..nq) (thread 0
+// writes): the warp stage in the accumulator type TA (FP32 sums stay on the
+// FP32 pipe; FP64 runs at 1/64 of its rate on this part), the cross-warp
+// stage in double; fixed order, so bitwise reproducible
+template <typename TA, int NV>
+__device__ __forceinline__ void block_sum_t(TA (&v)[NV], int nq, double* out) {
+    __shared__ double sm[RED_THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        if (q < nq) {
+            TA x = v[q];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) sm[wid][q] = (double)x;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < RED_THREADS / 32; ++w) acc += sm[w][threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -42,8 +70,13 @@ __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, T* __res
 template <typename T>
 __global__ void k_scale_copy(long long n, const double* __restrict__ sc, int invert, const T* __restrict__ x,
                              T* __restrict__ y) {
-    double s = *sc;
-    T a = (T)(invert ? (s != 0.0 ? 1.0 / s : 0.0) : s);
+    __shared__ T as;
+    if (threadIdx.x == 0) {
+        const double s = *sc;
+        as = (T)(invert ? (s != 0.0 ? 1.0 / s : 0.0) : s);
+    }
+    __syncthreads();
+    const T a = as;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = a * x[i];
 }
@@ -59,7 +92,6 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(long long n, const T* __restrict__ V, long long ld, int k,
                                                       const T* __restrict__ w, double* __restrict__ partial) {
     for (int j0 = 0; j0 < k; j0 += MDOT_CHUNK) {
-        double acc[MDOT_CHUNK];
         T tacc[MDOT_CHUNK];
 #pragma unroll
         for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
@@ -71,10 +103,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(long long n, const T* __re
             for (int q = 0; q < MDOT_CHUNK; ++q)
                 if (q < nq) tacc[q] += V[(long long)(j0 + q) * ld + i] * wi;
         }
-#pragma unroll
-        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q];
         __shared__ double outv[MDOT_CHUNK];
-        block_sum<MDOT_CHUNK>(acc, outv);
+        block_sum_t<T, MDOT_CHUNK>(tacc, nq, outv);
         if (threadIdx.x < nq) partial[(long long)blockIdx.x * k + j0 + threadIdx.x] = outv[threadIdx.x];
         __syncthreads();
     }
@@ -96,18 +126,17 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_update_mdot(long long n, const T* __restrict__ V, long long ld,
                                                              int k, const double* __restrict__ h,
                                                              T* __restrict__ w, double* __restrict__ partial) {
-    __shared__ double hs[128];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __shared__ T hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = (T)h[j];
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         T s = T(0);
-        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        for (int j = 0; j < k; ++j) s += hs[j] * V[(long long)j * ld + i];
         w[i] = w[i] - s;
     }
     // the elements this thread wrote are re-read by the same thread below
     for (int j0 = 0; j0 < k; j0 += MDOT_CHUNK) {
-        double acc[MDOT_CHUNK];
         T tacc[MDOT_CHUNK];
 #pragma unroll
         for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
@@ -119,10 +148,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_mdot(long long n, const 
             for (int q = 0; q < MDOT_CHUNK; ++q)
                 if (q < nq) tacc[q] += V[(long long)(j0 + q) * ld + i] * wi;
         }
-#pragma unroll
-        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q];
         __shared__ double outv[MDOT_CHUNK];
-        block_sum<MDOT_CHUNK>(acc, outv);
+        block_sum_t<T, MDOT_CHUNK>(tacc, nq, outv);
         if (threadIdx.x < nq) partial[(long long)blockIdx.x * k + j0 + threadIdx.x] = outv[threadIdx.x];
         __syncthreads();
     }
@@ -133,21 +160,21 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_update_norm(long long n, const T* __restrict__ V, long long ld,
                                                              int k, const double* __restrict__ h,
                                                              T* __restrict__ w, double* __restrict__ partial) {
-    __shared__ double hs[128];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __shared__ T hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = (T)h[j];
     __syncthreads();
     T acc = T(0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         T s = T(0);
-        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        for (int j = 0; j < k; ++j) s += hs[j] * V[(long long)j * ld + i];
         T wi = w[i] - s;
         w[i] = wi;
         acc += wi * wi;
     }
-    double v[1] = {(double)acc};
+    T v[1] = {acc};
     __shared__ double o[1];
-    block_sum<1>(v, o);
+    block_sum_t<T, 1>(v, 1, o);
     if (threadIdx.x == 0) partial[blockIdx.x] = o[0];
 }
 
@@ -160,22 +187,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_norm2(long long n, const T* __r
         T wi = w[i];
         acc += wi * wi;
     }
-    double v[1] = {(double)acc};
+    T v[1] = {acc};
     __shared__ double o[1];
-    block_sum<1>(v, o);
+    block_sum_t<T, 1>(v, 1, o);
     if (threadIdx.x == 0) partial[blockIdx.x] = o[0];
 }
 
+// x (+)= sum_j y_j Z_j, accumulated in the wider of T and Tz (an FP32
+// combination stays on the FP32 pipe)
 template <typename T, typename Tz>
 __global__ void k_combine(long long n, const Tz* __restrict__ Z, long long ld, int k, const double* __restrict__ y,
                           T* __restrict__ x, int accumulate) {
-    __shared__ double ys[128];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+    using TA = typename std::conditional<(sizeof(T) > sizeof(Tz)), T, Tz>::type;
+    __shared__ TA ys[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = (TA)y[j];
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        double s = accumulate ? (double)x[i] : 0.0;
-        for (int j = 0; j < k; ++j) s += ys[j] * (double)Z[(long long)j * ld + i];
+        TA s = accumulate ? (TA)x[i] : TA(0);
+        for (int j = 0; j < k; ++j) s += ys[j] * (TA)Z[(long long)j * ld + i];
         x[i] = (T)s;
     }
 }
@@ -185,15 +215,13 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_block_sums(long long m, int C, const T* __restrict__ x,
                                                             double* __restrict__ partial) {
     for (int c = 0; c < C; ++c) {
-        double acc = 0.0;
         T tacc = T(0);
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
              i += (long long)gridDim.x * blockDim.x)
             tacc += x[(long long)c * m + i];
-        acc = (double)tacc;
-        double v[1] = {acc};
+        T v[1] = {tacc};
         __shared__ double o[1];
-        block_sum<1>(v, o);
+        block_sum_t<T, 1>(v, 1, o);
         if (threadIdx.x == 0) partial[(long long)blockIdx.x * C + c] = o[0];
     }
 }
@@ -203,11 +231,13 @@ __global__ void k_scale_vals(int C, double s, double* v) {
     if (c < C) v[c] *= s;
 }
 
+// component c = blockIdx.y
 template <typename T>
-__global__ void k_subtract_means(long long m, int C, T* __restrict__ x, const double* __restrict__ means) {
-    long long n = m * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] -= (T)means[i / m];
+__global__ void k_subtract_means(long long m, T* __restrict__ x, const double* __restrict__ means) {
+    const T mu = (T)means[blockIdx.y];
+    x += (long long)blockIdx.y * m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        x[i] -= mu;
 }
 
 // ---- small FP64 bookkeeping kernels (one thread) --------------------------
@@ -276,7 +306,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_norm(long long n, const T*
     if (st && st[1] == 0.0) return;
     const int K1 = k + 1;
     for (int j0 = 0; j0 < K1; j0 += MDOT_CHUNK) {
-        double acc[MDOT_CHUNK];
         T tacc[MDOT_CHUNK];
 #pragma unroll
         for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
@@ -309,9 +338,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_norm(long long n, const T*
             }
         }
 #pragma unroll
-        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = (double)tacc[q] + (double)tacc2[q];
+        for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] += tacc2[q];
         __shared__ double outv[MDOT_CHUNK];
-        block_sum<MDOT_CHUNK>(acc, outv);
+        block_sum_t<T, MDOT_CHUNK>(tacc, nq, outv);
         if (threadIdx.x < nq) partial[(long long)blockIdx.x * K1 + j0 + threadIdx.x] = outv[threadIdx.x];
         __syncthreads();
     }
@@ -330,6 +359,8 @@ __global__ void k_cgs_state(const double* hk, int k, double* st, double* h2) {
     st[0] = nw2;
     st[1] = (nu2 < 0.5 * nw2) ? 1.0 : 0.0;
     st[2] = nu2 > 0.0 ? nu2 : 0.0;
+    const double nu = sqrt(st[2]);
+    st[3] = nu > 0.0 ? 1.0 / nu : 0.0;
     for (int j = 0; j < k; ++j) h2[j] = 0.0;
 }
 
@@ -338,13 +369,13 @@ template <typename T>
 __global__ void k_cgs_sub(long long n, const T* __restrict__ V, long long ld, int k, const double* __restrict__ h,
                           T* __restrict__ w, const double* __restrict__ st) {
     if (st[1] == 0.0) return;
-    __shared__ double hs[128];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+    __shared__ T hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = (T)h[j];
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         T s = T(0);
-        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        for (int j = 0; j < k; ++j) s += hs[j] * V[(long long)j * ld + i];
         w[i] -= s;
     }
 }
@@ -359,6 +390,8 @@ __global__ void k_cgs_state2(const double* hk2, int k, double* st, double* h2) {
     }
     double nu2 = hk2[k] - s;
     st[2] = nu2 > 0.0 ? nu2 : 0.0;
+    const double nu = sqrt(st[2]);
+    st[3] = nu > 0.0 ? 1.0 / nu : 0.0;
 }
 
 // V_{k} = (w - sum_j hsel_j V_j) / sqrt(st[2]), hsel = st[1] ? h2 : h1; also an
@@ -372,14 +405,13 @@ __global__ void k_cgs_normalize(long long n, const T* __restrict__ V, long long 
     const double* h = st[1] != 0.0 ? h2 : h1;
     for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
     __syncthreads();
-    double nu = sqrt(st[2]);
-    T inv = (T)(nu > 0.0 ? 1.0 / nu : 0.0);
+    const T inv = (T)st[3];  // 1 / sqrt(st[2]), formed by the one-thread state kernel
     const long long stride = (long long)gridDim.x * blockDim.x;
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     for (; i + stride < n; i += 2 * stride) {
         T sa = T(0), sb = T(0);
         for (int j = 0; j < k; ++j) {
-            T hj = (T)hs[j];
+            T hj = hs[j];
             sa += hj * V[(long long)j * ld + i];
             sb += hj * V[(long long)j * ld + i + stride];
         }
@@ -394,19 +426,18 @@ __global__ void k_cgs_normalize(long long n, const T* __restrict__ V, long long 
     }
     if (i < n) {
         T s = T(0);
-        for (int j = 0; j < k; ++j) s += (T)hs[j] * V[(long long)j * ld + i];
+        for (int j = 0; j < k; ++j) s += hs[j] * V[(long long)j * ld + i];
         T v = (w[i] - s) * inv;
         vout[i] = v;
         if (out2 && i < n2) out2[i] = (T2)v;
     }
 }
 
-// y = x * inv_sqrt(*nrm2), plus an optional copy of the first n2 entries
+// y = x * (*inv_norm), plus an optional copy of the first n2 entries
 template <typename T, typename T2>
-__global__ void k_scale_rsqrt(long long n, const double* __restrict__ nrm2, const T* __restrict__ x, T* __restrict__ y,
-                              T2* __restrict__ out2, long long n2) {
-    double nr = sqrt(fmax(*nrm2, 0.0));
-    T a = (T)(nr > 0.0 ? 1.0 / nr : 0.0);
+__global__ void k_scale_rsqrt(long long n, const double* __restrict__ inv_norm, const T* __restrict__ x,
+                              T* __restrict__ y, T2* __restrict__ out2, long long n2) {
+    const T a = (T)*inv_norm;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         T v = a * x[i];
         y[i] = v;
@@ -719,9 +750,9 @@ void cgs_coeffs_only(long long n, const T* V, long long ld, int k, const T* w, d
 }
 
 template <typename T, typename T2>
-void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s) {
+void scale_rsqrt(long long n, const double* inv_norm, const T* x, T* y, T2* out2, long long n2, cudaStream_t s) {
     ProfScope ps(KID_SCALE, s, 2.0 * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
-    k_scale_rsqrt<T, T2><<<blocks_for(n), 256, 0, s>>>(n, nrm2, x, y, out2, n2);
+    k_scale_rsqrt<T, T2><<<blocks_for(n), 256, 0, s>>>(n, inv_norm, x, y, out2, n2);
     IBR_CHECK_LAUNCH();
 }
 
@@ -869,7 +900,7 @@ void block_means(long long m, int C, const T* x, double* partial, double* out, c
 template <typename T>
 void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t s) {
     ProfScope ps(KID_SUB_MEANS, s, 2.0 * m * C * sizeof(T));
-    k_subtract_means<T><<<blocks_for(m * C), 256, 0, s>>>(m, C, x, means);
+    k_subtract_means<T><<<dim3(blocks_for(m), C), 256, 0, s>>>(m, x, means);
     IBR_CHECK_LAUNCH();
 }
 

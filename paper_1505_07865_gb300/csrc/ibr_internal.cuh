@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
 #include <string>
 
 #include "../../include/ibrigid.h"
@@ -45,6 +46,28 @@ bool profiling_enabled();
         ::ibr::count_launch();              \
         IBR_CUDA_TRY(cudaGetLastError());   \
     } while (0)
+
+// Runs a set-up step (e.g. cudaFuncSetAttribute, which acts on the current
+// device only) once per CUDA device, from any host thread: the step runs with
+// the device current, under a lock, the first time run() is called on it.
+class PerDeviceOnce {
+  public:
+    template <typename F>
+    void run(F&& fn) {
+        int dev = 0;
+        IBR_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 128) throw Error{IBR_EINVAL, "device index out of range"};
+        std::lock_guard<std::mutex> lk(mu_);
+        const unsigned long long bit = 1ULL << (dev & 63);
+        if (done_[dev >> 6] & bit) return;
+        fn();
+        done_[dev >> 6] |= bit;
+    }
+
+  private:
+    std::mutex mu_;
+    unsigned long long done_[2] = {0ULL, 0ULL};
+};
 
 // kernel classes timed by the optional profiler (prof.cu)
 enum KernelId {
@@ -157,6 +180,15 @@ template <typename T>
 void mg_tune_smoother(const Geo& g, int C, cudaStream_t s);
 // tuned tile idx: n0, n1, n2, C, element size, by, kz (false past the end)
 bool tuned_tile(int idx, int* out7);
+// times the V-cycle schedules of a periodic 3-D hierarchy (per-level kernels,
+// or the thread-block-cluster kernel from each feasible level) once per
+// hierarchy shape and keeps the fastest (no-op elsewhere and during capture);
+// U[1..L), Fw[1..L): the hierarchy's level buffers, used as scratch
+template <typename T>
+void mg_tune_cluster(const Geo* lev, int L, T* const* U, T* const* Fw, int C, int coarse_sweeps, cudaStream_t s);
+// tuned schedule idx: n0, n1, n2, levels, C, element size, first cluster
+// level (-2: none) (false past the end)
+bool tuned_cluster(int idx, int* out7);
 // q = -D y - hd ; (P_S middle factor, Sec. V.B)
 template <typename T>
 void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_scale, T* q, cudaStream_t s);
@@ -238,9 +270,9 @@ void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* v
 template <typename T>
 void cgs_coeffs_only(long long n, const T* V, long long ld, int k, const T* w, double* partial, double* h1,
                      double* h2, double* st, cudaStream_t s);
-// y = x / sqrt(*nrm2) (0 if nrm2 == 0), plus optional out2[0..n2) copy
+// y = x * (*inv_norm) (the 1/|x| formed by givens_init), plus optional out2[0..n2) copy
 template <typename T, typename T2>
-void scale_rsqrt(long long n, const double* nrm2, const T* x, T* y, T2* out2, long long n2, cudaStream_t s);
+void scale_rsqrt(long long n, const double* inv_norm, const T* x, T* y, T2* out2, long long n2, cudaStream_t s);
 
 // The outer FGMRES basis in double-float: value = hi + lo (48-bit
 // significand), 8 bytes per entry like FP64; its Gram-Schmidt passes run on

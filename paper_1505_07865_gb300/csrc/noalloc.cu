@@ -15,6 +15,7 @@
 // execution overlaps on the GPU (different streams, or different host threads)
 // race on it.  No value in it needs to start at zero: every coarse-level entry
 // is written before it is read.
+#include <cmath>
 #include <mutex>
 
 #include "ibr_internal.cuh"
@@ -71,6 +72,12 @@ extern "C" int ibr_op_vcycle_noalloc(int dim, const int* n, const double* L, dou
         for (int a = 0; a < dim; ++a)
             if (n[a] < 4 || n[a] % 2 != 0 || !(L[a] > 0)) throw Error{IBR_EINVAL, "each n[a] even >= 4, L[a] > 0"};
         double h = L[0] / n[0];
+        long long cells = 1;
+        for (int a = 0; a < dim; ++a) {
+            if (std::fabs(L[a] / n[a] - h) > 1e-12 * h) throw Error{IBR_EINVAL, "cells must be cubes (L[a]/n[a] equal)"};
+            cells *= n[a];
+        }
+        if (cells >= (1LL << 31)) throw Error{IBR_EINVAL, "a field must have fewer than 2^31 cells"};
         Geo lev[32];
         int nl = 0;
         lev[nl++] = make_geo(dim, n, h);

@@ -184,8 +184,9 @@ struct ibr_grid {
     int m_alloc = 0;
     long long len_alloc = 0;
     long long w_len = 0;  // the len w's zero pad was last set for
-    // V: the basis in double-float (dflt, 8 bytes per entry); vk64: the FP64
-    // copy of the current basis vector that the preconditioner reads
+    // V: the basis, FP64 (or, with IBR_ARNOLDI=df, double-float: dflt, 8
+    // bytes per entry); vk64: in the double-float case the FP64 copy of the
+    // current basis vector that the preconditioner reads
     double *V = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *w = nullptr, *vk64 = nullptr;
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
     double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr, *shift = nullptr, *means = nullptr;
@@ -259,6 +260,10 @@ struct PC {
             mg_tune_smoother<T>(lg, G->d, G->stream);
             mg_tune_smoother<T>(lg, 1, G->stream);
         }
+        // V-cycle schedule (where the cluster kernel takes over), velocity and pressure
+        for (int C : {G->d, 1})
+            mg_tune_cluster<T>(mg.lev.data(), (int)mg.lev.size(), mg.u.data(), mg.f.data(), C, mg.coarse_sweeps,
+                               G->stream);
         Vi = dalloc<T>((size_t)(ns + 1) * nS);
         Zi = dalloc<T>((size_t)ns * nS);
         w = dalloc<T>(nS);
@@ -390,7 +395,7 @@ struct PC {
         long long nS = G->nS;
         norm2<T>(nS, rhs, partial, sc + 0, s);
         givens_init(sc + 0, gv, ns + 1, sc + 1, sc + 2, s);
-        scale_rsqrt<T, T>(nS, sc + 0, rhs, Vi, nullptr, 0, s);
+        scale_rsqrt<T, T>(nS, sc + 2, rhs, Vi, nullptr, 0, s);
         for (int j = 0; j < ns; ++j) {
             T* Vj = Vi + (long long)j * nS;
             T* Zj = Zi + (long long)j * nS;
@@ -1139,6 +1144,17 @@ void project_solution(ibr_grid* G, double* x) {
         subtract_means<double>(n, 1, x + (long long)d * n, G->means + d, s);
 }
 
+// The outer Arnoldi basis: FP64 (the default), or double-float with
+// IBR_ARNOLDI=df in the environment (its Gram-Schmidt passes on the FP32
+// pipe, a 48-bit significand; kept for comparison)
+bool arnoldi_double_float() {
+    static const bool df = [] {
+        const char* e = std::getenv("IBR_ARNOLDI");
+        return e && std::string(e) == "df";
+    }();
+    return df;
+}
+
 // warm: start from the x already in G->x (time stepping), else from x = 0
 int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm = false) {
     cudaStream_t s = G->stream;
@@ -1203,20 +1219,36 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
         // V_0 = r / |r|; in mixed precision the preconditioner's FP32 copy of
         // its fluid part is written by the same pass
         float* rs32 = G->precision == IBR_MIXED ? G->pc32->rs : nullptr;
-        // the preconditioner reads the fluid part from rs32 (mixed) or vk64
-        // (FP64), the constraint part from vk64
+        const long long lp = G->len_pad();
+        const bool df = arnoldi_double_float();
+        // double-float basis: the preconditioner reads the fluid part from
+        // rs32 (mixed) or vk64 (FP64), the constraint part from vk64
         const long long from64 = rs32 ? G->nS : 0;
         dflt* Vd = reinterpret_cast<dflt*>(G->V);
-        const long long lp = G->len_pad();
-        scale_df(lp, len, G->sc + 0, G->w, Vd, rs32, G->nS, G->vk64, from64, s);
+        if (df) {
+            scale_df(lp, len, G->sc + 0, G->w, Vd, rs32, G->nS, G->vk64, from64, s);
+        } else if (rs32) {
+            scale_rsqrt<double, float>(len, G->sc + 2, G->w, G->V, rs32, G->nS, s);
+        } else {
+            scale_rsqrt<double, double>(len, G->sc + 2, G->w, G->V, nullptr, 0, s);
+        }
         int k = 0;
         last_cycle_converged_est = false;
         for (int j = 0; j < m; ++j) {
             double* Zj = G->Z + (long long)j * len;
-            pc_apply(G, G->vk64, Zj, true);
+            double* Vj = G->V + (long long)j * lp;
+            pc_apply(G, df ? G->vk64 : Vj, Zj, true);
             full_matvec(G, Zj, G->w);
-            cgs_orthonormalize_df(lp, len, Vd, lp, j + 1, G->w, Vd + (long long)(j + 1) * lp, rs32, G->nS, G->vk64,
-                                  from64, G->partial, G->h1, G->h2, G->hk2, G->st, s);
+            if (df) {
+                cgs_orthonormalize_df(lp, len, Vd, lp, j + 1, G->w, Vd + (long long)(j + 1) * lp, rs32, G->nS,
+                                      G->vk64, from64, G->partial, G->h1, G->h2, G->hk2, G->st, s);
+            } else if (rs32) {
+                cgs_orthonormalize<double, float>(len, G->V, lp, j + 1, G->w, Vj + lp, rs32, G->nS, G->partial,
+                                                  G->h1, G->h2, G->hk2, G->st, s);
+            } else {
+                cgs_orthonormalize<double, double>(len, G->V, lp, j + 1, G->w, Vj + lp, nullptr, 0, G->partial,
+                                                   G->h1, G->h2, G->hk2, G->st, s);
+            }
             arnoldi_column(G->H, m + 1, G->h1, G->h2, G->st + 2, j, G->cs, G->sn, G->gv, G->sc + 3, G->sc + 4, s);
             k = j + 1;
             info.iters++;
@@ -1952,6 +1984,16 @@ int ibr_op_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float
         }
         IBR_CUDA_TRY(cudaFreeAsync(err, s));
         if (herr) throw Error{IBR_ECUDA, "a tensor-core product timed out waiting for its MMAs"};
+    });
+}
+
+int ibr_tuned_vcycle_schedule(int idx, int* shape_l_c_esz, int* cluster_level) {
+    return run_guarded("ibr_tuned_vcycle_schedule", [&] {
+        int v[7];
+        require(tuned_cluster(idx, v), "no tuned V-cycle schedule with this index");
+        if (shape_l_c_esz)
+            for (int q = 0; q < 6; ++q) shape_l_c_esz[q] = v[q];
+        if (cluster_level) *cluster_level = v[6];
     });
 }
 

@@ -18,11 +18,36 @@
 #include <iterator>
 #include <map>
 #include <mutex>
+#include <vector>
+
+#include <cooperative_groups.h>
 
 #include "ibr_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace ibr {
 namespace {
+
+// Division of non-negative 32-bit indices (n < 2^31) by a divisor fixed per
+// launch, by a multiply-high and a shift (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l.
+struct FastDiv {
+    unsigned m;
+    int l;
+};
+FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ULL << l) < d) ++l;
+    FastDiv f;
+    f.m = (unsigned)(((1ULL << 32) * ((1ULL << l) - d)) / d + 1);
+    f.l = l;
+    return f;
+}
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+    return (int)((__umulhi(f.m, (unsigned)n) + (unsigned)n) >> f.l);
+}
 
 // flat index and wrapped neighbour offsets of a cell; 32-bit (a field has
 // fewer than 2^31 cells, checked when the grid is created)
@@ -201,17 +226,17 @@ __device__ __forceinline__ void rbgs_cell(T* u, const T* f, const Geo& g, int fl
     }
 }
 
-// the same for the t-th cell of the given colour (x index ih = t mod n0/2)
+// the same for the t-th cell of the given colour (x index ih = t mod n0/2);
+// dh, d1: division by n0/2 and by n1
 template <int D, bool W, typename T>
-__device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, int fld, T sigma, T kh2, int color,
-                                           int zero_init, long long t) {
-    int hn0 = g.n0 >> 1;
-    int ih = (int)(t % hn0);
-    long long r = t / hn0;
-    int j = (int)(r % g.n1);
-    int k = (int)(r / g.n1);
-    rbgs_cell<D, W, T>(u, f, g, fld, sigma, kh2, rbgs_inv_diag<D, T>(sigma, kh2), zero_init,
-                       2 * ih + ((j + k + color) & 1), j, k);
+__device__ __forceinline__ void rbgs_point(T* u, const T* f, const Geo& g, int fld, T sigma, T kh2, T inv_diag,
+                                           int color, int zero_init, int t, FastDiv dh, FastDiv d1) {
+    const int hn0 = g.n0 >> 1;
+    const int r = fdiv(t, dh);
+    const int ih = t - r * hn0;
+    const int k = fdiv(r, d1);
+    const int j = r - k * g.n1;
+    rbgs_cell<D, W, T>(u, f, g, fld, sigma, kh2, inv_diag, zero_init, 2 * ih + ((j + k + color) & 1), j, k);
 }
 
 // residual f - (sigma u - kh2 Lap u) at fine cell (i, j, k)
@@ -281,11 +306,11 @@ __device__ __forceinline__ T restrict_cell(const T* u, const T* f, const Geo& gf
 
 template <int D, bool W, typename T>
 __device__ __forceinline__ T restrict_point(const T* u, const T* f, const Geo& gf, const Geo& gc, int fld, T sigma,
-                                            T kh2, long long t) {
-    int I = (int)(t % gc.n0);
-    long long r = t / gc.n0;
-    int J = (int)(r % gc.n1);
-    int K = (int)(r / gc.n1);
+                                            T kh2, int t, FastDiv dc0, FastDiv dc1) {
+    const int r = fdiv(t, dc0);
+    const int I = t - r * gc.n0;
+    const int K = fdiv(r, dc1);
+    const int J = r - K * gc.n1;
     return restrict_cell<D, W, T>(u, f, gf, fld, sigma, kh2, I, J, K);
 }
 
@@ -375,20 +400,21 @@ __device__ __forceinline__ T prolong_cell(const T* cc, const Geo& gc, int fld, i
 }
 
 template <int D, bool W, typename T>
-__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, int fld, long long t) {
-    int i = (int)(t % gf.n0);
-    long long r = t / gf.n0;
-    int j = (int)(r % gf.n1);
-    int k = (int)(r / gf.n1);
+__device__ __forceinline__ T prolong_point(const T* cc, const Geo& gf, const Geo& gc, int fld, int t, FastDiv df0,
+                                           FastDiv df1) {
+    const int r = fdiv(t, df0);
+    const int i = t - r * gf.n0;
+    const int k = fdiv(r, df1);
+    const int j = r - k * gf.n1;
     return prolong_cell<D, W, T>(cc, gc, fld, i, j, k);
 }
 
 // block-wide mean of a[0..n) (all threads get it); red: 32 doubles of shared memory
 template <typename T>
-__device__ double block_mean(const T* a, long long n, double* red) {
+__device__ double block_mean(const T* a, int n, double* red) {
     int tid = threadIdx.x, nt = blockDim.x;
     double part = 0.0;
-    for (long long c = tid; c < n; c += nt) part += (double)a[c];
+    for (int c = tid; c < n; c += nt) part += (double)a[c];
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = part;
@@ -406,33 +432,34 @@ __device__ double block_mean(const T* a, long long n, double* red) {
 
 // coarsest-level solve in shared memory: for a singular field f (in sf,
 // modified) is made mean-free, u (su) from zero by red-black sweeps, then made
-// mean-free
+// mean-free; d0, d1: division by n0 and n1
 template <int D, bool W, typename T>
-__device__ void coarse_block(T* su, T* sf, const Geo& g, int fld, T sigma, T kh2, int sweeps, double* red) {
-    int tid = threadIdx.x, nt = blockDim.x;
+__device__ void coarse_block(T* su, T* sf, const Geo& g, int fld, T sigma, T kh2, T inv, int sweeps, double* red,
+                             FastDiv d0, FastDiv d1) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nc = (int)g.ncell;
     const bool sing = singular_field(g, fld, (double)sigma);
-    T fmean = sing ? (T)block_mean(sf, g.ncell, red) : T(0);
-    for (long long c = tid; c < g.ncell; c += nt) {
+    T fmean = sing ? (T)block_mean(sf, nc, red) : T(0);
+    for (int c = tid; c < nc; c += nt) {
         sf[c] -= fmean;
         su[c] = T(0);
     }
     __syncthreads();
-    T inv = rbgs_inv_diag<D, T>(sigma, kh2);
     for (int s = 0; s < sweeps; ++s) {
         for (int color = 0; color < 2; ++color) {
-            for (long long c = tid; c < g.ncell; c += nt) {
-                int i = (int)(c % g.n0);
-                long long r = c / g.n0;
-                int j = (int)(r % g.n1);
-                int k = (int)(r / g.n1);
+            for (int c = tid; c < nc; c += nt) {
+                const int r = fdiv(c, d0);
+                const int i = c - r * g.n0;
+                const int k = fdiv(r, d1);
+                const int j = r - k * g.n1;
                 if (((i + j + k) & 1) != color) continue;
                 rbgs_cell<D, W, T>(su, sf, g, fld, sigma, kh2, inv, 0, i, j, k);
             }
             __syncthreads();
         }
     }
-    T umean = sing ? (T)block_mean(su, g.ncell, red) : T(0);
-    for (long long c = tid; c < g.ncell; c += nt) su[c] -= umean;
+    T umean = sing ? (T)block_mean(su, nc, red) : T(0);
+    for (int c = tid; c < nc; c += nt) su[c] -= umean;
     __syncthreads();
 }
 
@@ -510,7 +537,7 @@ __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __r
 // single-CTA coarse solve of the coarsest level (one CTA per field)
 template <int D, bool W, typename T>
 __global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __restrict__ f, Geo g, int fld0,
-                                                 T sigma, T kh2, int sweeps) {
+                                                 T sigma, T kh2, T inv, int sweeps, FastDiv d0, FastDiv d1) {
     extern __shared__ unsigned char smem_raw[];
     T* su = reinterpret_cast<T*>(smem_raw);
     T* sf = su + g.ncell;
@@ -518,26 +545,118 @@ __global__ void __launch_bounds__(1024) k_coarse(T* __restrict__ u, const T* __r
     int cmp = blockIdx.x;
     const T* ff = f + cmp * g.ncell;
     T* uu = u + cmp * g.ncell;
-    for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) sf[c] = ff[c];
+    for (int c = threadIdx.x; c < (int)g.ncell; c += blockDim.x) sf[c] = ff[c];
     __syncthreads();
-    coarse_block<D, W, T>(su, sf, g, field_of(fld0, cmp), sigma, kh2, sweeps, red);
-    for (long long c = threadIdx.x; c < g.ncell; c += blockDim.x) uu[c] = su[c];
+    coarse_block<D, W, T>(su, sf, g, field_of(fld0, cmp), sigma, kh2, inv, sweeps, red, d0, d1);
+    for (int c = threadIdx.x; c < (int)g.ncell; c += blockDim.x) uu[c] = su[c];
 }
 
 // The small levels of a V-cycle, all in one CTA's shared memory (one CTA per
 // field): levels tl.g[0] (finest of the tail) .. tl.g[nl-1] (coarsest), the
 // same sweeps, restriction, coarse solve and prolongation as the per-level
 // kernels, with __syncthreads between them instead of kernel launches.
+// Index arithmetic in 32 bits with the per-level divisors precomputed.
 struct TailLevels {
     int nl;
     Geo g[MG_TAIL_MAX_LEVELS];
     int uoff[MG_TAIL_MAX_LEVELS];
     int foff[MG_TAIL_MAX_LEVELS];
+    FastDiv dh[MG_TAIL_MAX_LEVELS];  // n0 / 2
+    FastDiv d0[MG_TAIL_MAX_LEVELS];  // n0
+    FastDiv d1[MG_TAIL_MAX_LEVELS];  // n1
+    // per level kappa h^-2 and the smoother's 1 / (sigma + 2D kappa h^-2),
+    // formed on the host in the kernels' precision (FP64 arithmetic runs at
+    // 1/64 of the FP32 rate on this part: no per-thread FP64 division)
+    float kh2f[MG_TAIL_MAX_LEVELS], invf[MG_TAIL_MAX_LEVELS];
+    double kh2d[MG_TAIL_MAX_LEVELS], invd[MG_TAIL_MAX_LEVELS];
 };
 
+template <typename T, typename L>
+__device__ __forceinline__ T lev_kh2(const L& tl, int l) {
+    if constexpr (sizeof(T) == 4) return tl.kh2f[l]; else return tl.kh2d[l];
+}
+template <typename T, typename L>
+__device__ __forceinline__ T lev_inv(const L& tl, int l) {
+    if constexpr (sizeof(T) == 4) return tl.invf[l]; else return tl.invd[l];
+}
+
+// the V-cycle over the levels of tl, whose finest level's f (and u unless
+// zero_start) are already in shared memory at sm; leaves u of the finest
+// level there.  Every thread of the CTA calls it.
 template <int D, bool W, typename T>
-__global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__ ug, const T* __restrict__ fg,
-                                                  int fld0, T sigma, double kappa, int zero_start, int pre, int post,
+__device__ void tail_solve(const TailLevels& tl, T* sm, int fld, T sigma, int zero_start, int pre, int post,
+                           int sweeps, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto half = [&](int l, int color, int zero) {
+        const Geo& g = tl.g[l];
+        const T kh2 = lev_kh2<T>(tl, l);
+        const T inv = lev_inv<T>(tl, l);
+        T* u = sm + tl.uoff[l];
+        const T* f = sm + tl.foff[l];
+        const int np = (int)(g.ncell >> 1);
+        for (int t = tid; t < np; t += nt)
+            rbgs_point<D, W, T>(u, f, g, fld, sigma, kh2, inv, color, zero, t, tl.dh[l], tl.d1[l]);
+        __syncthreads();
+    };
+    const int L = tl.nl;
+    if (L == 1) {
+        const Geo& g = tl.g[0];
+        if (zero_start) {
+            coarse_block<D, W, T>(sm + tl.uoff[0], sm + tl.foff[0], g, fld, sigma, lev_kh2<T>(tl, 0),
+                                  lev_inv<T>(tl, 0), sweeps, red, tl.d0[0], tl.d1[0]);
+        } else {
+            for (int s = 0; s < sweeps; ++s) {
+                half(0, 0, 0);
+                half(0, 1, 0);
+            }
+        }
+        return;
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        int zs = (l > 0) || zero_start;
+        if (pre == 0 && zs) {
+            T* u = sm + tl.uoff[l];
+            for (int c = tid; c < (int)tl.g[l].ncell; c += nt) u[c] = T(0);
+            __syncthreads();
+        }
+        for (int it = 0; it < pre; ++it) {
+            half(l, 0, zs && it == 0);
+            half(l, 1, 0);
+        }
+        const Geo& gf = tl.g[l];
+        const Geo& gc = tl.g[l + 1];
+        const T kh2 = lev_kh2<T>(tl, l);
+        const T* u = sm + tl.uoff[l];
+        const T* f = sm + tl.foff[l];
+        T* fc = sm + tl.foff[l + 1];
+        for (int t = tid; t < (int)gc.ncell; t += nt)
+            fc[t] = restrict_point<D, W, T>(u, f, gf, gc, fld, sigma, kh2, t, tl.d0[l + 1], tl.d1[l + 1]);
+        __syncthreads();
+    }
+    {
+        const Geo& g = tl.g[L - 1];
+        coarse_block<D, W, T>(sm + tl.uoff[L - 1], sm + tl.foff[L - 1], g, fld, sigma, lev_kh2<T>(tl, L - 1),
+                              lev_inv<T>(tl, L - 1), sweeps, red, tl.d0[L - 1], tl.d1[L - 1]);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const Geo& gf = tl.g[l];
+        const Geo& gc = tl.g[l + 1];
+        T* u = sm + tl.uoff[l];
+        const T* uc = sm + tl.uoff[l + 1];
+        for (int t = tid; t < (int)gf.ncell; t += nt)
+            u[t] += prolong_point<D, W, T>(uc, gf, gc, fld, t, tl.d0[l], tl.d1[l]);
+        __syncthreads();
+        for (int it = 0; it < post; ++it) {
+            half(l, 1, 0);
+            half(l, 0, 0);
+        }
+    }
+}
+
+template <int D, bool W, typename T>
+__global__ void __launch_bounds__(1024) k_mg_tail(const __grid_constant__ TailLevels tl, T* __restrict__ ug,
+                                                  const T* __restrict__ fg,
+                                                  int fld0, T sigma, int zero_start, int pre, int post,
                                                   int sweeps) {
     extern __shared__ unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -545,82 +664,231 @@ __global__ void __launch_bounds__(1024) k_mg_tail(TailLevels tl, T* __restrict__
     const int tid = threadIdx.x, nt = blockDim.x;
     const int cmp = blockIdx.x;
     const int fld = field_of(fld0, cmp);
-    const Geo g0 = tl.g[0];
-    ug += cmp * g0.ncell;
-    fg += cmp * g0.ncell;
+    const int n0 = (int)tl.g[0].ncell;
+    ug += (long long)cmp * n0;
+    fg += (long long)cmp * n0;
     {
         T* u0 = sm + tl.uoff[0];
         T* f0 = sm + tl.foff[0];
-        for (long long c = tid; c < g0.ncell; c += nt) {
+        for (int c = tid; c < n0; c += nt) {
             f0[c] = fg[c];
             u0[c] = zero_start ? T(0) : ug[c];
         }
     }
     __syncthreads();
-    auto half = [&](int l, int color, int zero) {
-        const Geo& g = tl.g[l];
-        T kh2 = (T)(kappa / (g.h * g.h));
-        T* u = sm + tl.uoff[l];
-        const T* f = sm + tl.foff[l];
-        for (long long t = tid; t < (g.ncell >> 1); t += nt)
-            rbgs_point<D, W, T>(u, f, g, fld, sigma, kh2, color, zero, t);
-        __syncthreads();
+    tail_solve<D, W, T>(tl, sm, fld, sigma, zero_start, pre, post, sweeps, red);
+    {
+        const T* u0 = sm + tl.uoff[0];
+        for (int c = tid; c < n0; c += nt) ug[c] = u0[c];
+    }
+}
+
+// ---- the coarse levels of a periodic 3-D V-cycle on one thread-block cluster ----
+// One cluster of MG_CL CTAs per stacked field runs levels cl.top .. of the
+// V-cycle in one launch.  The "distributed" levels (the first cl.nd) are split
+// into z-slabs of P = n2 / MG_CL planes, CTA r of the cluster keeping planes
+// [r P, (r+1) P) of u (and of f, except on the top level, whose f is read
+// from global memory) in its shared memory; a cell's neighbours in the planes
+// of the adjacent CTAs are read from their shared memory (distributed shared
+// memory).  The remaining small levels (the tail) live in CTA 0's shared
+// memory and run there (tail_solve) while the other CTAs wait.  Cluster
+// barriers separate the phases.  Same point arithmetic, summation order and
+// sweep order as the per-level kernels (k_rbgs_col, k_resid_restrict,
+// k_prolong) and the tail.
+constexpr int MG_CL = 8;
+constexpr int MG_CL_MAX_LEVELS = 6;
+
+struct ClusterLevels {
+    int nd;                        // distributed levels
+    int n0[MG_CL_MAX_LEVELS], n1[MG_CL_MAX_LEVELS], n2[MG_CL_MAX_LEVELS], P[MG_CL_MAX_LEVELS];
+    FastDiv dh[MG_CL_MAX_LEVELS];  // n0 / 2
+    FastDiv d0[MG_CL_MAX_LEVELS];  // n0
+    FastDiv d1[MG_CL_MAX_LEVELS];  // n1
+    float kh2f[MG_CL_MAX_LEVELS], invf[MG_CL_MAX_LEVELS];  // as in TailLevels
+    double kh2d[MG_CL_MAX_LEVELS], invd[MG_CL_MAX_LEVELS];
+    int uoff[MG_CL_MAX_LEVELS];    // u slab of level l in every CTA's shared memory (elements)
+    int foff[MG_CL_MAX_LEVELS];    // f slab (levels >= 1)
+    int toff;                      // tail region (CTA 0)
+    TailLevels tail;               // offsets relative to toff
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg_cluster(const __grid_constant__ ClusterLevels cl, T* __restrict__ ug,
+                                                     const T* __restrict__ fg,
+                                                     T sigma, int zero_start, int pre, int post, int sweeps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    __shared__ double red[32];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = (int)cluster.block_rank();
+    const int cmp = blockIdx.x / MG_CL;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int plane0 = cl.n0[0] * cl.n1[0];
+    const long long ncell0 = (long long)plane0 * cl.n2[0];
+    ug += cmp * ncell0;
+    fg += cmp * ncell0;
+    T* tailbase = sm + cl.toff;
+
+    // pointer to plane k (any, wrapped) of the u (or f) slabs of distributed level l
+    auto dplane = [&](int l, int off, int k) -> T* {
+        const int n2 = cl.n2[l], P = cl.P[l];
+        k = k < 0 ? k + n2 : (k >= n2 ? k - n2 : k);
+        const int owner = k / P;
+        return cluster.map_shared_rank(sm + off, owner) + (k - owner * P) * (cl.n0[l] * cl.n1[l]);
     };
-    const int L = tl.nl;
-    if (L == 1) {
-        const Geo& g = tl.g[0];
-        if (zero_start) {
-            coarse_block<D, W, T>(sm + tl.uoff[0], sm + tl.foff[0], g, fld, sigma, (T)(kappa / (g.h * g.h)), sweeps,
-                                  red);
-        } else {
-            for (int s = 0; s < sweeps; ++s) {
-                half(0, 0, 0);
-                half(0, 1, 0);
+    // red-black half sweep of distributed level l
+    auto dhalf = [&](int l, int color, int zero) {
+        const int n0 = cl.n0[l], n1 = cl.n1[l], P = cl.P[l], hn0 = n0 >> 1;
+        const int plane = n0 * n1;
+        T* u = sm + cl.uoff[l];
+        const T* ub = dplane(l, cl.uoff[l], r * P - 1);
+        const T* ua = dplane(l, cl.uoff[l], r * P + P);
+        const T* f = l == 0 ? fg + (long long)r * P * plane : sm + cl.foff[l];
+        const T kh2 = lev_kh2<T>(cl, l);
+        const T inv = lev_inv<T>(cl, l);
+        const int np = P * n1 * hn0;
+        for (int t = tid; t < np; t += nt) {
+            const int q = fdiv(t, cl.dh[l]);
+            const int ih = t - q * hn0;
+            const int kl = fdiv(q, cl.d1[l]);
+            const int j = q - kl * n1;
+            const int i = 2 * ih + ((j + r * P + kl + color) & 1);
+            const int c = i + n0 * j;
+            T* pc = u + kl * plane;
+            const T* pm = kl == 0 ? ub : pc - plane;
+            const T* pp = kl == P - 1 ? ua : pc + plane;
+            const int xp = (i == n0 - 1) ? 1 - n0 : 1;
+            const int xm = (i == 0) ? n0 - 1 : -1;
+            const int yp = (j == n1 - 1) ? (1 - n1) * n0 : n0;
+            const int ym = (j == 0) ? (n1 - 1) * n0 : -n0;
+            T nb = T(0);
+            if (!zero) {
+                nb = pc[c + xp] + pc[c + xm] + pc[c + yp] + pc[c + ym];
+                nb += pp[c] + pm[c];
             }
+            pc[c] = (f[kl * plane + c] + kh2 * nb) * inv;
         }
-    } else {
-        for (int l = 0; l + 1 < L; ++l) {
-            int zs = (l > 0) || zero_start;
-            if (pre == 0 && zs) {
-                T* u = sm + tl.uoff[l];
-                for (long long c = tid; c < tl.g[l].ncell; c += nt) u[c] = T(0);
-                __syncthreads();
-            }
-            for (int it = 0; it < pre; ++it) {
-                half(l, 0, zs && it == 0);
-                half(l, 1, 0);
-            }
-            const Geo& gf = tl.g[l];
-            const Geo& gc = tl.g[l + 1];
-            T kh2 = (T)(kappa / (gf.h * gf.h));
-            const T* u = sm + tl.uoff[l];
-            const T* f = sm + tl.foff[l];
-            T* fc = sm + tl.foff[l + 1];
-            for (long long t = tid; t < gc.ncell; t += nt)
-                fc[t] = restrict_point<D, W, T>(u, f, gf, gc, fld, sigma, kh2, t);
-            __syncthreads();
+        cluster.sync();
+    };
+    // residual of distributed level l at its cell (i, j, k) (k global)
+    auto dresid = [&](int l, int i, int j, int k, T kh2) -> T {
+        const int n0 = cl.n0[l], n1 = cl.n1[l];
+        const T* pc = dplane(l, cl.uoff[l], k);
+        const T* pm = dplane(l, cl.uoff[l], k - 1);
+        const T* pp = dplane(l, cl.uoff[l], k + 1);
+        const T* fp = l == 0 ? fg + (long long)k * n0 * n1 : dplane(l, cl.foff[l], k);
+        const int c = i + n0 * j;
+        const int xp = (i == n0 - 1) ? 1 - n0 : 1;
+        const int xm = (i == 0) ? n0 - 1 : -1;
+        const int yp = (j == n1 - 1) ? (1 - n1) * n0 : n0;
+        const int ym = (j == 0) ? (n1 - 1) * n0 : -n0;
+        const T uc = pc[c];
+        T nbs = pc[c + xp] + pc[c + xm] + pc[c + yp] + pc[c + ym];
+        nbs += pp[c] + pm[c];
+        return fp[c] - (sigma * uc - kh2 * (nbs - T(6) * uc));
+    };
+    // f of level l+1 = the averaged residual of distributed level l, for the
+    // coarse planes K whose first fine plane 2K this CTA owns
+    auto drestrict = [&](int l) {
+        const int n0c = cl.n0[l] >> 1, n1c = cl.n1[l] >> 1;
+        const int planec = n0c * n1c;
+        const int P = cl.P[l];
+        const int K0 = (r * P + 1) >> 1, K1 = (r * P + P + 1) >> 1;  // 2K in [rP, rP + P)
+        const bool coarse_dist = l + 1 < cl.nd;
+        const FastDiv dc0 = coarse_dist ? cl.d0[l + 1] : cl.tail.d0[0];
+        const int np = (K1 - K0) * planec;
+        const T kh2 = lev_kh2<T>(cl, l);
+        for (int t = tid; t < np; t += nt) {
+            const int q = fdiv(t, dc0);
+            const int I = t - q * n0c;
+            const int kk = q / n1c;
+            const int J = q - kk * n1c;
+            const int K = K0 + kk;
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                acc += dresid(l, 2 * I + (c & 1), 2 * J + ((c >> 1) & 1), 2 * K + ((c >> 2) & 1), kh2);
+            T* fcp = coarse_dist ? dplane(l + 1, cl.foff[l + 1], K)
+                                 : cluster.map_shared_rank(tailbase + cl.tail.foff[0], 0) + K * planec;
+            fcp[I + n0c * J] = acc * (T(1) / T(8));
         }
-        {
-            const Geo& g = tl.g[L - 1];
-            coarse_block<D, W, T>(sm + tl.uoff[L - 1], sm + tl.foff[L - 1], g, fld, sigma,
-                                  (T)(kappa / (g.h * g.h)), sweeps, red);
-        }
-        for (int l = L - 2; l >= 0; --l) {
-            const Geo& gf = tl.g[l];
-            const Geo& gc = tl.g[l + 1];
-            T* u = sm + tl.uoff[l];
-            const T* uc = sm + tl.uoff[l + 1];
-            for (long long t = tid; t < gf.ncell; t += nt) u[t] += prolong_point<D, W, T>(uc, gf, gc, fld, t);
-            __syncthreads();
-            for (int it = 0; it < post; ++it) {
-                half(l, 1, 0);
-                half(l, 0, 0);
+        cluster.sync();
+    };
+    // u of distributed level l += prolongation of level l+1's u (own planes)
+    auto dprolong = [&](int l) {
+        const int n0 = cl.n0[l], n1 = cl.n1[l], P = cl.P[l];
+        const int plane = n0 * n1;
+        const int n0c = n0 >> 1, n1c = n1 >> 1, n2c = cl.n2[l] >> 1;
+        const bool coarse_dist = l + 1 < cl.nd;
+        T* u = sm + cl.uoff[l];
+        const int np = P * plane;
+        const T w[2] = {T(0.75), T(0.25)};
+        for (int t = tid; t < np; t += nt) {
+            const int q = fdiv(t, cl.d0[l]);
+            const int i = t - q * n0;
+            const int kl = fdiv(q, cl.d1[l]);
+            const int j = q - kl * n1;
+            const int k = r * P + kl;
+            int I[2], Jc[2], Kc[2];
+            I[0] = i >> 1;
+            I[1] = (i & 1) ? (I[0] + 1 == n0c ? 0 : I[0] + 1) : (I[0] == 0 ? n0c - 1 : I[0] - 1);
+            Jc[0] = j >> 1;
+            Jc[1] = (j & 1) ? (Jc[0] + 1 == n1c ? 0 : Jc[0] + 1) : (Jc[0] == 0 ? n1c - 1 : Jc[0] - 1);
+            Kc[0] = k >> 1;
+            Kc[1] = (k & 1) ? (Kc[0] + 1 == n2c ? 0 : Kc[0] + 1) : (Kc[0] == 0 ? n2c - 1 : Kc[0] - 1);
+            const T* cp[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                cp[e] = coarse_dist ? dplane(l + 1, cl.uoff[l + 1], Kc[e])
+                                    : cluster.map_shared_rank(tailbase + cl.tail.uoff[0], 0) + Kc[e] * (n0c * n1c);
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+                const T ww = w[a] * w[b] * w[e];
+                acc += ww * cp[e][I[a] + n0c * Jc[b]];
             }
+            u[t] += acc;
+        }
+        cluster.sync();
+    };
+
+    // the top level's u slab from global memory (or zero)
+    {
+        T* u0 = sm + cl.uoff[0];
+        const int n = cl.P[0] * plane0;
+        const T* src = ug + (long long)r * n;
+        for (int c = tid; c < n; c += nt) u0[c] = zero_start ? T(0) : src[c];
+    }
+    cluster.sync();
+    const int nd = cl.nd;
+    for (int l = 0; l < nd; ++l) {
+        const int zs = (l > 0) || zero_start;
+        if (pre == 0 && zs) {
+            T* u = sm + cl.uoff[l];
+            for (int c = tid; c < cl.P[l] * cl.n0[l] * cl.n1[l]; c += nt) u[c] = T(0);
+            cluster.sync();
+        }
+        for (int it = 0; it < pre; ++it) {
+            dhalf(l, 0, zs && it == 0);
+            dhalf(l, 1, 0);
+        }
+        drestrict(l);
+    }
+    if (r == 0) tail_solve<3, false, T>(cl.tail, tailbase, 0, sigma, 1, pre, post, sweeps, red);
+    cluster.sync();
+    for (int l = nd - 1; l >= 0; --l) {
+        dprolong(l);
+        for (int it = 0; it < post; ++it) {
+            dhalf(l, 1, 0);
+            dhalf(l, 0, 0);
         }
     }
     {
-        const T* u0 = sm + tl.uoff[0];
-        for (long long c = tid; c < g0.ncell; c += nt) ug[c] = u0[c];
+        const T* u0 = sm + cl.uoff[0];
+        const int n = cl.P[0] * plane0;
+        T* dst = ug + (long long)r * n;
+        for (int c = tid; c < n; c += nt) dst[c] = u0[c];
     }
 }
 
@@ -936,30 +1204,34 @@ void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, int fld0, double sig
     size_t sm = 2 * (size_t)g.ncell * sizeof(T);
     int nt = g.ncell >= 1024 ? 1024 : (int)((g.ncell + 31) / 32 * 32);
     ProfScope ps(KID_COARSE, s, 2.0 * C * g.ncell * sizeof(T));
+    const FastDiv d0 = make_fastdiv(g.n0), d1 = make_fastdiv(g.n1);
+    const T inv = g.d == 3 ? rbgs_inv_diag<3, T>((T)sigma, kh2) : rbgs_inv_diag<2, T>((T)sigma, kh2);
     if (g.d == 3) {
         if (g.wall)
-            k_coarse<3, true, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+            k_coarse<3, true, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, inv, sweeps, d0, d1);
         else
-            k_coarse<3, false, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+            k_coarse<3, false, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, inv, sweeps, d0, d1);
     } else {
         if (g.wall)
-            k_coarse<2, true, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+            k_coarse<2, true, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, inv, sweeps, d0, d1);
         else
-            k_coarse<2, false, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, sweeps);
+            k_coarse<2, false, T><<<C, nt, sm, s>>>(u, f, g, fld0, (T)sigma, kh2, inv, sweeps, d0, d1);
     }
     IBR_CHECK_LAUNCH();
 }
 
+// the tail kernels' shared-memory limit, raised once per device (function
+// attributes belong to the device that is current when they are set)
 template <typename T>
 void mg_set_attributes() {
-    static bool done = false;
-    if (done) return;
-    const int sm = (int)MG_TAIL_MAX_SMEM;
-    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    done = true;
+    static PerDeviceOnce once;
+    once.run([] {
+        const int sm = (int)MG_TAIL_MAX_SMEM;
+        IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<3, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        IBR_CUDA_TRY(cudaFuncSetAttribute(k_mg_tail<2, true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    });
 }
 
 // shared memory of the tail kernel for levels [l0, L)
@@ -970,16 +1242,175 @@ static size_t tail_smem(const Geo* lev, int l0, int L) {
     return n * sizeof(T);
 }
 
+// tail levels [lt, L) in a TailLevels (offsets from 0, in elements)
+// kappa h^-2 and 1 / (sigma + 2D kappa h^-2) of a level, in float and double
+// (the same expressions as the per-level launches)
+template <typename L>
+void level_coefs(L& x, int q, const Geo& g, double sigma, double kappa) {
+    x.kh2f[q] = (float)(kappa / (g.h * g.h));
+    x.kh2d[q] = kappa / (g.h * g.h);
+    x.invf[q] = g.d == 3 ? rbgs_inv_diag<3, float>((float)sigma, x.kh2f[q]) : rbgs_inv_diag<2, float>((float)sigma, x.kh2f[q]);
+    x.invd[q] = g.d == 3 ? rbgs_inv_diag<3, double>(sigma, x.kh2d[q]) : rbgs_inv_diag<2, double>(sigma, x.kh2d[q]);
+}
+
 template <typename T>
-void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
-               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s) {
-    // the tail: the longest suffix of levels with <= MG_TAIL_MAX_CELLS cells each
-    // that fits in shared memory (the coarsest level always does)
+TailLevels make_tail(const Geo* lev, int lt, int L, double sigma, double kappa) {
+    TailLevels tl;
+    tl.nl = L - lt;
+    int off = 0;
+    for (int q = 0; q < tl.nl; ++q) {
+        tl.g[q] = lev[lt + q];
+        tl.uoff[q] = off;
+        off += (int)lev[lt + q].ncell;
+        tl.foff[q] = off;
+        off += (int)lev[lt + q].ncell;
+        tl.dh[q] = make_fastdiv(lev[lt + q].n0 / 2);
+        tl.d0[q] = make_fastdiv(lev[lt + q].n0);
+        tl.d1[q] = make_fastdiv(lev[lt + q].n1);
+        level_coefs(tl, q, lev[lt + q], sigma, kappa);
+    }
+    return tl;
+}
+
+// the first tail level: the longest suffix of levels with <= MG_TAIL_MAX_CELLS
+// cells each that fits in shared memory (the coarsest level always does)
+template <typename T>
+int tail_start(const Geo* lev, int L) {
     int lt = L - 1;
     while (lt - 1 >= 0 && L - (lt - 1) <= MG_TAIL_MAX_LEVELS && lev[lt - 1].ncell <= MG_TAIL_MAX_CELLS &&
            tail_smem<T>(lev, lt - 1, L) <= MG_TAIL_MAX_SMEM)
         --lt;
+    return lt;
+}
+
+// Cluster plan of a periodic 3-D hierarchy: levels [top, top + nd) distributed
+// over the MG_CL CTAs of a cluster (n2 a multiple of MG_CL), the tail [top +
+// nd, L) in CTA 0; top as fine as shared memory allows.  false: no such plan.
+constexpr size_t MG_CL_SMEM = 200 * 1024;
+// want: the top level to use (-1: the finest feasible level with at most
+// MG_CL_DEFAULT_TOP_CELLS cells: larger levels keep more of the GPU busy with
+// one launch per sweep than one 8-CTA cluster per field can)
+constexpr long long MG_CL_DEFAULT_TOP_CELLS = 32768;
+template <typename T>
+bool cluster_plan(const Geo* lev, int L, double sigma, double kappa, int want, int& top, ClusterLevels& cl) {
+    if (lev[0].d != 3 || lev[0].wall) return false;
+    const int lt = tail_start<T>(lev, L);
+    if (lt < 1) return false;
+    // distributed levels must be above the tail and split evenly in z
+    for (int t = 0; t < lt; ++t) {
+        if (want >= 0 ? t != want : lev[t].ncell > MG_CL_DEFAULT_TOP_CELLS) continue;
+        bool ok = lt - t <= MG_CL_MAX_LEVELS;
+        size_t bytes = tail_smem<T>(lev, lt, L);
+        for (int l = t; l < lt && ok; ++l) {
+            const Geo& g = lev[l];
+            if (g.n2 % MG_CL != 0 || g.n0 % 2 != 0) ok = false;
+            const size_t slab = (size_t)(g.n2 / MG_CL) * g.n0 * g.n1 * sizeof(T);
+            bytes += l == t ? slab : 2 * slab;
+        }
+        if (!ok || bytes + 64 > MG_CL_SMEM) continue;
+        top = t;
+        cl.nd = lt - t;
+        int off = 0;
+        for (int q = 0; q < cl.nd; ++q) {
+            const Geo& g = lev[t + q];
+            cl.n0[q] = g.n0;
+            cl.n1[q] = g.n1;
+            cl.n2[q] = g.n2;
+            cl.P[q] = g.n2 / MG_CL;
+            level_coefs(cl, q, g, sigma, kappa);
+            cl.dh[q] = make_fastdiv(g.n0 / 2);
+            cl.d0[q] = make_fastdiv(g.n0);
+            cl.d1[q] = make_fastdiv(g.n1);
+            const int slab = cl.P[q] * g.n0 * g.n1;
+            cl.uoff[q] = off;
+            off += slab;
+            cl.foff[q] = q == 0 ? -1 : off;
+            if (q > 0) off += slab;
+        }
+        cl.toff = (off + 3) & ~3;
+        cl.tail = make_tail<T>(lev, lt, L, sigma, kappa);
+        return true;
+    }
+    return false;
+}
+
+// whether this device runs MG_CL-CTA clusters of k_mg_cluster with MG_CL_SMEM
+// bytes of shared memory (checked once per device; IBR_MG_CLUSTER=0 in the
+// environment: never)
+template <typename T>
+bool cluster_ok() {
+    static const bool off = [] {
+        const char* e = std::getenv("IBR_MG_CLUSTER");
+        return e && e[0] == '0';
+    }();
+    if (off) return false;
+    static std::mutex mu;
+    static int state[128] = {0};  // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    IBR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (state[dev] == 0) {
+        state[dev] = 2;
+        if (cudaFuncSetAttribute(k_mg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_CL_SMEM) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = MG_CL;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(MG_CL, 1, 1);
+            cfg.blockDim = dim3(1024, 1, 1);
+            cfg.dynamicSmemBytes = MG_CL_SMEM;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, k_mg_cluster<T>, &cfg) == cudaSuccess && nc >= 1) state[dev] = 1;
+        }
+        cudaGetLastError();  // a refused query leaves no error behind
+    }
+    return state[dev] == 1;
+}
+
+// The V-cycle schedule autotuner's choice per hierarchy (finest level shape,
+// levels, stacked fields, element size): the level the cluster kernel starts
+// at, or -2 for none (per-level kernels and the one-CTA tail).
+std::mutex g_cl_mu;
+std::map<std::array<long long, 6>, int> g_cl_top;
+
+std::array<long long, 6> cl_key(const Geo* lev, int L, int C, size_t esz) {
+    return {lev[0].n0, lev[0].n1, lev[0].n2, L, C, (long long)esz};
+}
+
+// IBR_MG_CLUSTER_LEVEL=<level> in the environment: the cluster kernel from
+// that level whenever feasible (measurement and tests); -1 when unset
+int cluster_forced() {
+    static const int lv = [] {
+        const char* e = std::getenv("IBR_MG_CLUSTER_LEVEL");
+        return (e && e[0] >= '0' && e[0] <= '9') ? std::atoi(e) : -1;
+    }();
+    return lv;
+}
+
+int cluster_choice(const Geo* lev, int L, int C, size_t esz) {
+    if (cluster_forced() >= 0) return cluster_forced();
+    std::lock_guard<std::mutex> lk(g_cl_mu);
+    auto it = g_cl_top.find(cl_key(lev, L, C, esz));
+    return it == g_cl_top.end() ? -1 : it->second;
+}
+
+template <typename T>
+void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
+               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s) {
     auto Fl = [&](int l) -> const T* { return l == 0 ? F0 : Fw[l]; };
+    // periodic 3-D: the coarse levels on one thread-block cluster per field
+    ClusterLevels cl;
+    int top = 0;
+    const int want = cluster_choice(lev, L, C, sizeof(T));
+    const bool use_cluster =
+        want != -2 && cluster_plan<T>(lev, L, sigma, kappa, want, top, cl) && cluster_ok<T>();
+    const int lt = use_cluster ? top : tail_start<T>(lev, L);
     for (int l = 0; l < lt; ++l) {
         bool zs = (l > 0) || zero_start;
         if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(T) * C * lev[l].ncell, s));
@@ -989,39 +1420,49 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         }
         mg_residual_restrict<T>(lev[l], lev[l + 1], U[l], Fl(l), Fw[l + 1], C, fld0, sigma, kappa, s);
     }
-    {
-        TailLevels tl;
-        tl.nl = L - lt;
-        int off = 0;
-        for (int q = 0; q < tl.nl; ++q) {
-            tl.g[q] = lev[lt + q];
-            tl.uoff[q] = off;
-            off += (int)lev[lt + q].ncell;
-            tl.foff[q] = off;
-            off += (int)lev[lt + q].ncell;
-        }
+    const bool zs = (lt > 0) || zero_start;
+    const int z = zs ? 1 : 0;
+    const T sg = (T)sigma;
+    if (use_cluster) {
+        const long long n0 = lev[lt].ncell;
+        ProfScope ps(KID_COARSE, s, 2.0 * C * n0 * sizeof(T));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = MG_CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(MG_CL * C, 1, 1);
+        cfg.blockDim = dim3(1024, 1, 1);
+        cfg.dynamicSmemBytes = MG_CL_SMEM;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        T* ut = U[lt];
+        const T* ft = Fl(lt);
+        IBR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_mg_cluster<T>, cl, ut, ft, sg, z, pre, post, coarse_sweeps));
+        IBR_CHECK_LAUNCH();
+    } else {
+        TailLevels tl = make_tail<T>(lev, lt, L, sigma, kappa);
         size_t sm = tail_smem<T>(lev, lt, L);
         long long n0 = lev[lt].ncell;
         int nt = n0 >= 2048 ? 1024 : (int)(((n0 + 1) / 2 + 31) / 32 * 32);
         if (nt < 32) nt = 32;
-        bool zs = (lt > 0) || zero_start;
         ProfScope ps(KID_COARSE, s, 2.0 * C * n0 * sizeof(T));
         mg_set_attributes<T>();
-        const int z = zs ? 1 : 0;
-        const T sg = (T)sigma;
         if (lev[0].d == 3) {
             if (lev[0].wall)
-                k_mg_tail<3, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                k_mg_tail<3, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                        coarse_sweeps);
             else
-                k_mg_tail<3, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                k_mg_tail<3, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                         coarse_sweeps);
         } else {
             if (lev[0].wall)
-                k_mg_tail<2, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                k_mg_tail<2, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                        coarse_sweeps);
             else
-                k_mg_tail<2, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, kappa, z, pre, post,
+                k_mg_tail<2, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                         coarse_sweeps);
         }
         IBR_CHECK_LAUNCH();
@@ -1033,6 +1474,86 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
             mg_smooth<T>(lev[l], U[l], Fl(l), C, fld0, sigma, kappa, 0, false, s);
         }
     }
+}
+
+// Times one V-cycle of each schedule (no cluster; the cluster kernel from
+// each feasible level) on the hierarchy lev[0..L) with C stacked fields, on
+// the caller's level buffers U[1..L), Fw[1..L) (scratch during the set-up)
+// and scratch finest-level arrays, and keeps the fastest for this shape.
+// Once per shape and process, outside stream capture; the result of a
+// V-cycle does not depend on the schedule (the same arithmetic in the same
+// order), only its time.
+template <typename T>
+void mg_tune_cluster(const Geo* lev, int L, T* const* U, T* const* Fw, int C, int coarse_sweeps, cudaStream_t s) {
+    if (lev[0].d != 3 || lev[0].wall || !cluster_ok<T>() || cluster_forced() >= 0) return;
+    static const bool off = [] {
+        const char* e = std::getenv("IBR_TUNE");
+        return e && e[0] == '0';
+    }();
+    if (off) return;
+    const auto key = cl_key(lev, L, C, sizeof(T));
+    {
+        std::lock_guard<std::mutex> lk(g_cl_mu);
+        if (g_cl_top.count(key)) return;
+    }
+    cudaStreamCaptureStatus cs;
+    IBR_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return;
+    std::vector<int> cands = {-2};
+    for (int t = 0; t < L; ++t) {
+        ClusterLevels cl;
+        int top = 0;
+        if (cluster_plan<T>(lev, L, 0.0, 1.0, t, top, cl)) cands.push_back(t);
+    }
+    if (cands.size() < 2) return;
+    const size_t n = (size_t)C * lev[0].ncell;
+    T *u0 = nullptr, *f0 = nullptr;
+    IBR_CUDA_TRY(cudaMallocAsync(&u0, n * sizeof(T), s));
+    IBR_CUDA_TRY(cudaMallocAsync(&f0, n * sizeof(T), s));
+    IBR_CUDA_TRY(cudaMemsetAsync(f0, 0, n * sizeof(T), s));
+    std::vector<T*> Uv(U, U + L);
+    Uv[0] = u0;
+    cudaEvent_t e0, e1;
+    IBR_CUDA_TRY(cudaEventCreate(&e0));
+    IBR_CUDA_TRY(cudaEventCreate(&e1));
+    int best = -2;
+    float best_ms = 1e30f;
+    for (int c : cands) {
+        {
+            std::lock_guard<std::mutex> lk(g_cl_mu);
+            g_cl_top[key] = c;
+        }
+        mg_vcycle<T>(lev, L, Uv.data(), Fw, f0, C, 0, 0.0, 1.0, true, 2, 2, coarse_sweeps, s);
+        IBR_CUDA_TRY(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r)
+            mg_vcycle<T>(lev, L, Uv.data(), Fw, f0, C, 0, 0.0, 1.0, true, 2, 2, coarse_sweeps, s);
+        IBR_CUDA_TRY(cudaEventRecord(e1, s));
+        IBR_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        IBR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    IBR_CUDA_TRY(cudaFreeAsync(u0, s));
+    IBR_CUDA_TRY(cudaFreeAsync(f0, s));
+    std::lock_guard<std::mutex> lk(g_cl_mu);
+    g_cl_top[key] = best;
+}
+
+// tuned V-cycle schedule idx: n0, n1, n2, levels, stacked fields, element
+// size, first cluster level (-2: none); false past the end
+bool tuned_cluster(int idx, int* out7) {
+    std::lock_guard<std::mutex> lk(g_cl_mu);
+    if (idx < 0 || idx >= (int)g_cl_top.size()) return false;
+    auto it = g_cl_top.begin();
+    std::advance(it, idx);
+    for (int q = 0; q < 6; ++q) out7[q] = (int)it->first[q];
+    out7[6] = it->second;
+    return true;
 }
 
 template <typename T>
@@ -1091,6 +1612,7 @@ void wall_lift(const Geo& g, int a, int side, const double* data, double* b, dou
     template void mg_coarse_solve<T>(const Geo&, T*, const T*, int, int, double, double, int, cudaStream_t); \
     template void mg_set_attributes<T>();                                                                   \
     template void mg_tune_smoother<T>(const Geo&, int, cudaStream_t);                                       \
+    template void mg_tune_cluster<T>(const Geo*, int, T* const*, T* const*, int, int, cudaStream_t);          \
     template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, int, double, double, bool, \
                                int, int, int, cudaStream_t);                                                \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \

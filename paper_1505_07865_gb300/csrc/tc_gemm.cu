@@ -427,13 +427,14 @@ __global__ void k_sym_out(int n, int np, const float* __restrict__ P, float* __r
     M[id] = c <= r ? P[(long long)r * np + c] : P[(long long)c * np + r];
 }
 
+// shared-memory limits, raised once per device (function attributes belong to
+// the device that is current when they are set)
 void set_attributes() {
-    static const bool done = [] {
+    static PerDeviceOnce once;
+    once.run([] {
         IBR_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
         IBR_CUDA_TRY(cudaFuncSetAttribute(k_diag_block, cudaFuncAttributeMaxDynamicSharedMemorySize, DB_SMEM));
-        return true;
-    }();
-    (void)done;
+    });
 }
 
 }  // namespace

@@ -65,3 +65,12 @@ def test_noalloc_vcycle_rejects_grids_beyond_the_scratch(abi):
         abi.op_vcycle_noalloc(3, n, (1.0, 1.0, 1.0), 0.0, 1.0, f, f, 1)
     assert e.value.code == abi.EINVAL
     assert "static scratch" in abi.last_error()
+
+
+def test_noalloc_vcycle_rejects_non_cubic_cells(abi):
+    # the V-cycle's operator assumes one cell width h on every axis
+    f = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(abi.IbrError) as e:
+        abi.op_vcycle_noalloc(2, (32, 32), (1.0, 2.0), 0.0, 1.0, f, f, 1)
+    assert e.value.code == abi.EINVAL
+    assert "cubes" in abi.last_error()
