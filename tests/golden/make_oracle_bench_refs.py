@@ -10,8 +10,9 @@ oracle).  Calls only oracle/ and synthetic/.
   (synthetic.serve_3d, seed 1510; the geometry does not depend on the rate):
   Lambda by conjugate gradients on M (SPD) to a relative residual of 1e-12.
 * nozzle: the 256 x 128 nozzle at Re = 0 (steady Stokes, parabolic inflow =
-  outflow, no-slip channel walls; Sec. VII.F): Lambda, v and pi by the sparse
-  LU of the whole wall-bounded system with iterative refinement (App. D).
+  outflow, no-slip channel walls; Sec. VII.F): Lambda, and v and pi at 512
+  seeded cells, by the sparse LU of the whole wall-bounded system with
+  iterative refinement (App. D).
 
 Usage: python tests/golden/make_oracle_bench_refs.py
 """
@@ -70,8 +71,10 @@ def main():
     x = prob.solve(b)
     v, p, lam = prob.split(x)
     out["nozzle_re0_lambda"] = lam
-    out["nozzle_re0_v"] = np.concatenate([a.ravel() for a in v])
-    out["nozzle_re0_p"] = p.ravel()
+    cells = np.random.default_rng(256).choice(wg.ncell, size=512, replace=False)
+    out["nozzle_re0_cells"] = cells
+    out["nozzle_re0_v"] = np.concatenate([a.ravel()[cells] for a in v])
+    out["nozzle_re0_p"] = p.ravel()[cells]
     out["nozzle_re0_residual"] = np.array([prob.residual(x, b)])
     print("nozzle", lam.shape, prob.residual(x, b), flush=True)
     np.savez_compressed(os.path.join(HERE, "oracle_bench_refs.npz"), **out)
