@@ -10,6 +10,10 @@ Bodies", arXiv:1505.07865), in float64 NumPy:
 
 * ``peskin``     -- the 4-point Peskin kernel phi (Sec. III.A, kernel of the
                     paper's ref. IBM_PeskinReview).
+* ``bkp6``       -- the six-point kernel of Bao, Kaye and Peskin that the
+                    paper uses (Sec. III.A, ref. New6ptKernel), solved from
+                    its defining moment, even-odd and sum-of-squares
+                    conditions; ``Grid(kernel="bkp6")`` selects it for J, S.
 * ``mac``        -- staggered (MAC) grid, gradient G, divergence D = -G^T,
                     vector Laplacian, viscous operator A (Sec. III.B, Eq. A_def).
 * ``ib``         -- interpolation J, spreading S, S~ = S - vol^-1 1^T,
@@ -30,7 +34,10 @@ against closed forms, invariants, brute force and an independent route
 (dense LU vs DFT): among them the rotation direction of K and Q(q) by
 hand-computed rotations, and the whole constrained solve by first-order
 convergence to the analytic flow of a spinning disk inside a fixed ring
-(``test_oracle_convergence.py``, the 2-D analogue of Sec. VII.C).  ``mobility.mtilde_2d_steady`` evaluates the App. B
+(``test_oracle_convergence.py``, the 2-D analogue of Sec. VII.C), and the
+six-point kernel by its defining conditions, three continuous derivatives
+and the hydrodynamic radius a = 1.47 h the paper quotes (Sec. IV.A)
+(``test_oracle_bkp6.py``).  ``mobility.mtilde_2d_steady`` evaluates the App. B
 functional form with caller-supplied coefficients (the paper does not print
 them); the form is pinned by its stated limits, the coefficient values are an
 input, not an oracle claim.

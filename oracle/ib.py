@@ -21,31 +21,43 @@ r_i given in the body frame and Q(q) the rotation of the unit quaternion q
 """
 import numpy as np
 
-from .peskin import phi, support_weights
+from . import bkp6, peskin
+
+
+def kernel_module(grid):
+    """the 1-D kernel of the grid's regularised delta: the 4-point Peskin
+    kernel, or the six-point kernel of Bao, Kaye and Peskin"""
+    return bkp6 if getattr(grid, "kernel", "peskin4") == "bkp6" else peskin
+
+
+def kernel_width(grid):
+    return 6 if getattr(grid, "kernel", "peskin4") == "bkp6" else 4
 
 
 def _stencil(grid, q, alpha):
     """Per-axis node windows and weights for component alpha.
 
-    Returns a list over axes beta of (nodes[N,4] wrapped mod n_beta, w[N,4]).
-    Face i of component alpha sits at (i_beta + 1/2 - delta_{alpha beta}/2) h.
+    Returns a list over axes beta of (nodes[N,W] wrapped mod n_beta, w[N,W]),
+    W = 4 or 6 the kernel's support.  Face i of component alpha sits at
+    (i_beta + 1/2 - delta_{alpha beta}/2) h.
     """
     out = []
+    kw = kernel_width(grid)
     for b in range(grid.d):
         off = 0.0 if b == alpha else 0.5
         s = q[:, b] / grid.h - off
-        j0, w = support_weights(s)
-        nodes = (j0[:, None] + np.arange(4)) % grid.n[b]
+        j0, w = kernel_module(grid).support_weights(s)
+        nodes = (j0[:, None] + np.arange(kw)) % grid.n[b]
         out.append((nodes, w))
     return out
 
 
 def _tensor_iter(grid, st):
-    """Yield (flat_index[N], weight[N]) over the 4^d tensor-product support."""
+    """Yield (flat_index[N], weight[N]) over the W^d tensor-product support."""
     d = grid.d
     import itertools
 
-    for combo in itertools.product(range(4), repeat=d):
+    for combo in itertools.product(range(kernel_width(grid)), repeat=d):
         flat = np.zeros(st[0][0].shape[0], dtype=np.int64)
         w = np.ones(st[0][0].shape[0])
         stride = 1
@@ -104,7 +116,7 @@ def interp_bruteforce(grid, q, v):
             for b in range(grid.d):
                 dx = q[i, b] - coords[b]
                 dx = dx - grid.L[b] * np.round(dx / grid.L[b])
-                w = w * phi(dx / grid.h)
+                w = w * kernel_module(grid).phi(dx / grid.h)
             out[i, a] = np.sum(w * v[a])
     return out
 

@@ -21,7 +21,9 @@ import scipy.sparse as sp
 class Grid:
     """Uniform periodic MAC grid: d in {2, 3}, n = cells per axis (x first)."""
 
-    def __init__(self, n, L=None, eta=1.0, rho=0.0, dt=0.0):
+    def __init__(self, n, L=None, eta=1.0, rho=0.0, dt=0.0, kernel="peskin4"):
+        assert kernel in ("peskin4", "bkp6")
+        self.kernel = kernel  # regularised delta of J and S (Sec. III.A)
         self.n = tuple(int(v) for v in n)
         self.d = len(self.n)
         assert self.d in (2, 3)
