@@ -69,6 +69,10 @@ extern "C" {
 
 /* ---- kernels, precisions, kinematics, preconditioner variants ------------- */
 #define IBR_KERNEL_PESKIN4 4   /* 4-point Peskin kernel (Sec. III.A)            */
+#define IBR_KERNEL_BKP6    6   /* six-point kernel of Bao, Kaye and Peskin, the
+                                  kernel the paper uses (Sec. III.A): support 6
+                                  nodes per axis, three continuous derivatives;
+                                  periodic boxes only                           */
 #define IBR_FP64  0            /* every step in float64                           */
 #define IBR_MIXED 1            /* FP64 outer FGMRES / matvec / true residual;     */
                                /* FP32 preconditioner (MG, P_S, inner GMRES,      */
@@ -106,10 +110,11 @@ typedef struct ibr_solve_opts {
     int    mg_pre;         /* pre-smoothing sweeps per V-cycle level            */
     int    mg_post;        /* post-smoothing sweeps per V-cycle level           */
     int    mob_model;      /* IBR_MOB_*                                          */
-    double mob_a_over_h;   /* marker radius a/h in M~ (0: 1.25 in 3-D, Sec. IV.A;  */
-                           /* 1.04 in 2-D, where App. B's f(0) then equals the    */
-                           /* 4-point kernel's discrete periodic self-mobility)   */
-    double mob_coef[9];    /* App. B coefficients a0..a4, b0..b3 (2-D steady)   */
+    double mob_a_over_h;   /* marker radius a/h in M~; 0: the grid kernel's value */
+                           /* (ibr_mobility_defaults: 1.25 / 1.47 in 3-D, Sec.    */
+                           /* IV.A; in 2-D the fitted App. B self-mobility radius) */
+    double mob_coef[9];    /* App. B coefficients a0..a4, b0..b3 (2-D steady);   */
+                           /* all zero: the grid kernel's fitted set             */
     double time_cap_ms;    /* <= 0: none                                         */
 } ibr_solve_opts;
 
@@ -135,9 +140,20 @@ typedef struct ibr_step_info {
 } ibr_step_info;
 
 /* Fills opts with the defaults: tol 1e-8, restart 50, max_iters 1000, N_s 0 (automatic),
- * IBR_PC_LOWER, mg 2/2, IBR_MOB_AUTO, a/h 0 (=1.25 in 3-D, see ibr_solve_coupled),
- * the library's 2-D coefficient set, no time cap. */
+ * IBR_PC_LOWER, mg 2/2, IBR_MOB_AUTO, a/h 0 and coefficients 0 (the grid
+ * kernel's defaults, ibr_mobility_defaults), no time cap. */
 int ibr_solve_opts_default(ibr_solve_opts* opts);
+
+/* The library's default parameters of the analytic M~ for a kernel
+ * (IBR_KERNEL_PESKIN4 / IBR_KERNEL_BKP6) in dim 2 or 3: the marker radius a/h
+ * and, in 2-D, the coefficients a0..a4, b0..b3 of App. B's steady forms
+ * (Eq. fg_steady_2d; zeros in 3-D, where M~ is the RPY tensor, Eq. RPYTensor).
+ * 3-D radii are the paper's (Sec. IV.A: 1.25 h and 1.47 h).  The paper does
+ * not print its 2-D coefficients; these are fitted by its procedure (Sec.
+ * IV.B, App. B) to the library's own periodic pair mobility of each kernel
+ * (paper_1505_07865_gb300/fit_mobility_2d.py, output mobility_fit_2d.json).
+ * Either output may be NULL.  Needs no GPU. */
+int ibr_mobility_defaults(int dim, int kernel, double* a_over_h, double* coef9);
 
 /* Creates a uniform MAC grid (Sec. III).  dim in {2,3}; n[0..dim-1] cells per
  * axis (each even, >= 4); L[0..dim-1] box lengths (cubic cells: L[a]/n[a]
@@ -151,7 +167,9 @@ int ibr_solve_opts_default(ibr_solve_opts* opts);
  * (its equation is v = wall value, and it holds that value in the solution),
  * the high wall face is not stored.
  * eta > 0 viscosity; rho, dt >= 0 (rho == 0 or dt == 0: steady Stokes, A =
- * -eta h^-2 Lap).  kernel: IBR_KERNEL_PESKIN4.  precision: IBR_FP64 or
+ * -eta h^-2 Lap).  kernel: IBR_KERNEL_PESKIN4, or IBR_KERNEL_BKP6 on a
+ * periodic box (the analytic M~ then takes a = 1.47 h in 3-D, Sec. IV.A).
+ * precision: IBR_FP64 or
  * IBR_MIXED.  cuda_stream: a cudaStream_t, or NULL for a library-created
  * blocking stream (ordered with the legacy default stream).  On success *out owns the
  * grid's device memory.  Errors: IBR_EINVAL, IBR_ENOMEM, IBR_ECUDA. */

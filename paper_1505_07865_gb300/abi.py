@@ -21,6 +21,7 @@ LIBPATH = os.path.join(HERE, "libibrigid.so")
 OK, EINVAL, ENOMEM, ENOTCONV, ETIMEOUT, ENUMERIC, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 PERIODIC, NOSLIP, VELOCITY = 0, 1, 2
 KERNEL_PESKIN4 = 4
+KERNEL_BKP6 = 6
 FP64, MIXED = 0, 1
 PRESCRIBED, FREE = 0, 1
 PC_LOWER, PC_FULL = 0, 1
@@ -192,6 +193,7 @@ _SIGS = {
     "ibr_server_destroy": (ctypes.c_int, [_P]),
     "ibr_tuned_smoother_tile": (ctypes.c_int, [ctypes.c_int, _I, _I, _I]),
     "ibr_tuned_vcycle_schedule": (ctypes.c_int, [ctypes.c_int, _I, _I]),
+    "ibr_mobility_defaults": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _D, _D]),
     "ibr_launch_count": (ctypes.c_longlong, []),
     "ibr_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ibr_profile_reset": (ctypes.c_int, []),
@@ -587,3 +589,11 @@ def tuned_vcycle_schedules():
         out.append(tuple(v) + (cl.value,))
         i += 1
     return out
+
+
+def mobility_defaults(dim, kernel=KERNEL_PESKIN4):
+    """(a/h, [a0..a4, b0..b3]) of the library's analytic M~ for the kernel."""
+    aoh = ctypes.c_double()
+    c = np.zeros(9)
+    _check(_lib.ibr_mobility_defaults(int(dim), int(kernel), ctypes.byref(aoh), _dptr(c)))
+    return aoh.value, c

@@ -214,17 +214,14 @@ __global__ void __launch_bounds__(TB * TB) k_xtx(int n, const T* W, T* M, int nb
 }
 
 // periodic window of component al at point p (lab coordinates in [0, L)):
-// per axis b the first of the 4 nodes and their weights (face al sits at
+// per axis b the first of the KW nodes and their weights (face al sits at
 // integer positions along al and half-integer positions along the others)
-template <int D>
-__device__ __forceinline__ void pair_window(const Geo& g, const double* p, int al, int* j0, double (*w)[4]) {
+template <int D, int KW>
+__device__ __forceinline__ void pair_window(const Geo& g, const double* p, int al, int* j0, double (*w)[KW]) {
 #pragma unroll
     for (int b = 0; b < D; ++b) {
         const double sb = p[b] / g.h - (al == b ? 0.0 : 0.5);
-        const double fl = floor(sb);
-        j0[b] = (int)fl - 1;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) w[b][m] = peskin4(sb - (fl - 1.0 + m));
+        kernel_window(KW, sb, j0[b], w[b]);
     }
 }
 
@@ -232,7 +229,8 @@ __device__ __forceinline__ void pair_window(const Geo& g, const double* p, int a
 // the diagonal exit): it forms M~_ij and writes it and its transpose M~_ji
 // the same window with FP32 weights (the table is FP32): the position and
 // its offset from the window's first node stay FP64, the kernel value and the
-// 4^d-cell sums of the M~ build run on the FP32 pipe
+// KW^d-cell sums of the M~ build run on the FP32 pipe (the six-point weights
+// are formed in FP64 and rounded)
 __device__ __forceinline__ float peskin4f(float r) {
     r = fabsf(r);
     if (r < 1.0f) return 0.125f * (3.0f - 2.0f * r + sqrtf(1.0f + 4.0f * r - 4.0f * r * r));
@@ -240,20 +238,28 @@ __device__ __forceinline__ float peskin4f(float r) {
     return 0.0f;
 }
 
-template <int D>
-__device__ __forceinline__ void pair_window_f(const Geo& g, const double* p, int al, int* j0, float (*w)[4]) {
+template <int D, int KW>
+__device__ __forceinline__ void pair_window_f(const Geo& g, const double* p, int al, int* j0, float (*w)[KW]) {
 #pragma unroll
     for (int b = 0; b < D; ++b) {
         const double sb = p[b] / g.h - (al == b ? 0.0 : 0.5);
         const double fl = floor(sb);
-        j0[b] = (int)fl - 1;
-        const float fr = (float)(sb - fl);  // in [0, 1)
+        if (KW == 6) {
+            double w6[6];
+            j0[b] = (int)fl - 2;
+            bkp6_weights(sb - fl, w6);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) w[b][m] = peskin4f(fr + 1.0f - (float)m);
+            for (int m = 0; m < KW; ++m) w[b][m] = (float)w6[m];
+        } else {
+            j0[b] = (int)fl - 1;
+            const float fr = (float)(sb - fl);  // in [0, 1)
+#pragma unroll
+            for (int m = 0; m < KW; ++m) w[b][m] = peskin4f(fr + 1.0f - (float)m);
+        }
     }
 }
 
-template <int D>
+template <int D, int KW>
 __global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double* __restrict__ q, int S,
                                                      const double* __restrict__ x0, const float* __restrict__ tab,
                                                      double* __restrict__ M) {
@@ -283,17 +289,20 @@ __global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double
 #pragma unroll
             for (int al = 0; al < D; ++al) {
                 int j0[D];
-                float w[D][4];
-                pair_window_f<D>(g, p, al, j0, w);
+                float w[D][KW];
+                pair_window_f<D, KW>(g, p, al, j0, w);
                 float sum[D];
 #pragma unroll
                 for (int be = 0; be < D; ++be) sum[be] = 0.0f;
-                for (int c = 0; c < (1 << (2 * D)); ++c) {
+                const int S_win = D == 3 ? KW * KW * KW : KW * KW;
+                for (int c = 0; c < S_win; ++c) {
                     long long cell = 0, stride = 1;
                     float wt = 1.0f;
+                    int cc = c;
 #pragma unroll
                     for (int b = 0; b < D; ++b) {
-                        const int m = (c >> (2 * b)) & 3;
+                        const int m = cc % KW;
+                        cc /= KW;
                         int jj = (j0[b] + m) % ns[b];
                         if (jj < 0) jj += ns[b];
                         cell += jj * stride;
@@ -326,19 +335,21 @@ __global__ void __launch_bounds__(256) k_pair_mtilde(Geo g, int nr, const double
         }
 }
 
-template <int D>
+template <int D, int KW>
 __global__ void k_point_spread(Geo g, const double* __restrict__ x0, int beta, double scale, double* __restrict__ y) {
     const int c = threadIdx.x;
-    if (c >= (1 << (2 * D))) return;
+    if (c >= (D == 3 ? KW * KW * KW : KW * KW)) return;
     const int ns[3] = {g.n0, g.n1, g.n2};
     int j0[D];
-    double w[D][4];
-    pair_window<D>(g, x0, beta, j0, w);
+    double w[D][KW];
+    pair_window<D, KW>(g, x0, beta, j0, w);
     long long cell = 0, stride = 1;
     double wt = 1.0;
+    int cc = c;
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-        const int m = (c >> (2 * b)) & 3;
+        const int m = cc % KW;
+        cc /= KW;
         int jj = (j0[b] + m) % ns[b];
         if (jj < 0) jj += ns[b];
         cell += jj * stride;
@@ -415,18 +426,32 @@ void pair_mtilde(const Geo& g, int nr, const double* q, int S, const double* x0,
     ProfScope ps(KID_MTILDE, s, (double)n * g.d * g.d * 8);
     const int nt = (nr + 15) / 16;
     dim3 grid(nt, nt), blk(16, 16);
-    if (g.d == 3)
-        k_pair_mtilde<3><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
-    else
-        k_pair_mtilde<2><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
+    if (g.d == 3) {
+        if (g.kw == 6)
+            k_pair_mtilde<3, 6><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
+        else
+            k_pair_mtilde<3, 4><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
+    } else {
+        if (g.kw == 6)
+            k_pair_mtilde<2, 6><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
+        else
+            k_pair_mtilde<2, 4><<<grid, blk, 0, s>>>(g, nr, q, S, x0, tab, M);
+    }
     IBR_CHECK_LAUNCH();
 }
 
 void point_spread(const Geo& g, const double* x0, int beta, double scale, double* y, cudaStream_t s) {
-    if (g.d == 3)
-        k_point_spread<3><<<1, 64, 0, s>>>(g, x0, beta, scale, y);
-    else
-        k_point_spread<2><<<1, 16, 0, s>>>(g, x0, beta, scale, y);
+    if (g.d == 3) {
+        if (g.kw == 6)
+            k_point_spread<3, 6><<<1, 256, 0, s>>>(g, x0, beta, scale, y);
+        else
+            k_point_spread<3, 4><<<1, 64, 0, s>>>(g, x0, beta, scale, y);
+    } else {
+        if (g.kw == 6)
+            k_point_spread<2, 6><<<1, 64, 0, s>>>(g, x0, beta, scale, y);
+        else
+            k_point_spread<2, 4><<<1, 16, 0, s>>>(g, x0, beta, scale, y);
+    }
     IBR_CHECK_LAUNCH();
 }
 

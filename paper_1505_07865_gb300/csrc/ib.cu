@@ -3,7 +3,9 @@
 //  (J v)_i^a = sum_k v_k^a prod_b phi((q_i - r_k^a)_b / h)
 //  (S L)_k^a = h^-d sum_i L_i^a prod_b phi((q_i - r_k^a)_b / h)
 //
-// with the 4-point Peskin kernel phi.  Spreading is a face-major gather: the
+// with the 4-point Peskin kernel or the six-point kernel of Bao, Kaye and
+// Peskin as phi (window of g.kw = 4 or 6 nodes per axis).  Spreading is a
+// face-major gather: the
 // (face, marker, weight) triples of S are sorted by face once per geometry,
 // so each touched face is summed by one thread in a fixed order (no atomics,
 // bitwise reproducible).
@@ -33,7 +35,7 @@ __global__ void k_positions(int d, int N, const double* __restrict__ rb, const i
 }
 
 // For component a, axis b and window node m (t = (i*d + a)*d + b):
-// idx[t*4 + m] = the stored node the window node maps to and w[t*4 + m] its
+// idx[t*kw + m] = the stored node the window node maps to and w[t*kw + m] its
 // signed weight.  Periodic axes wrap.  On a wall axis the field is extended
 // beyond the walls by its mirror image with a sign (App. D): the component
 // tangential to the wall (cell-centred along b) by ghost = -mirror, the
@@ -50,12 +52,14 @@ __global__ void k_weights(Geo g, int N, const double* __restrict__ q, int* __res
     int b = t % d;
     double off = (a == b) ? 0.0 : 0.5;
     double s = q[i * d + b] / g.h - off;
-    double fl = floor(s);
-    int j0 = (int)fl - 1;
+    const int kw = g.kw;
+    int j0 = 0;
+    double wts[6];
+    kernel_window(kw, s, j0, wts);
     int nb = b == 0 ? g.n0 : (b == 1 ? g.n1 : g.n2);
     bool wall = (g.wall >> b) & 1;
-    for (int m = 0; m < 4; ++m) {
-        double ww = peskin4(s - (double)(j0 + m));
+    for (int m = 0; m < kw; ++m) {
+        double ww = wts[m];
         int j = j0 + m;
         int st;
         if (!wall) {
@@ -85,16 +89,19 @@ __global__ void k_weights(Geo g, int N, const double* __restrict__ q, int* __res
                 st = j;
             }
         }
-        idx[t * 4 + m] = st;
-        w64[t * 4 + m] = ww;
-        w32[t * 4 + m] = (float)ww;
+        idx[t * kw + m] = st;
+        w64[t * kw + m] = ww;
+        w32[t * kw + m] = (float)ww;
     }
 }
 
+// entry e of the (marker component, window cell) list: kw^D window cells per
+// marker component, window node m_b = (c / kw^b) mod kw on axis b
 template <int D>
 __device__ __forceinline__ void entry_face(const Geo& g, const int* __restrict__ idx, const double* __restrict__ w64,
                                            long long e, long long& key, double& wt, int& mcomp) {
-    const int S = D == 3 ? 64 : 16;
+    const int kw = g.kw;
+    const int S = D == 3 ? kw * kw * kw : kw * kw;
     int c = (int)(e % S);
     long long ia = e / S;  // i*D + a
     int a = (int)(ia % D);
@@ -104,12 +111,13 @@ __device__ __forceinline__ void entry_face(const Geo& g, const int* __restrict__
     wt = 1.0;
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-        int m = (c >> (2 * b)) & 3;
+        int m = c % kw;
+        c /= kw;
         long long t = ia * D + b;
-        int j = idx[t * 4 + m];
+        int j = idx[t * kw + m];
         cell += j * stride;
         stride *= ns[b];
-        wt *= w64[t * 4 + m];
+        wt *= w64[t * kw + m];
     }
     key = (long long)a * g.ncell + cell;
 }
@@ -260,14 +268,14 @@ __global__ void k_spread_gather(long long F, const long long* __restrict__ face,
     y[face[f]] += scale * s;
 }
 
-// one warp per marker; lanes stride the 4^D support of each component
-template <int D, typename T, typename Tadd>
+// one warp per marker; lanes stride the KW^D support of each component
+template <int D, int KW, typename T, typename Tadd>
 __global__ void k_interp(Geo g, int N, const int* __restrict__ idx, const T* __restrict__ w, const T* __restrict__ v,
                          T* __restrict__ out, T sign, const Tadd* __restrict__ add, T add_scale) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (warp >= N) return;
-    const int S = D == 3 ? 64 : 16;
+    const int S = D == 3 ? KW * KW * KW : KW * KW;
     const int ns[3] = {g.n0, g.n1, g.n2};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -277,14 +285,16 @@ __global__ void k_interp(Geo g, int N, const int* __restrict__ idx, const T* __r
         for (int c = lane; c < S; c += 32) {
             long long cell = 0, stride = 1;
             T wt = T(1);
+            int cc = c;
 #pragma unroll
             for (int b = 0; b < D; ++b) {
-                int m = (c >> (2 * b)) & 3;
+                const int m = cc % KW;
+                cc /= KW;
                 long long t = ia * D + b;
-                int j = idx[t * 4 + m];
+                int j = idx[t * KW + m];
                 cell += j * stride;
                 stride *= ns[b];
-                wt *= w[t * 4 + m];
+                wt *= w[t * KW + m];
             }
             acc += wt * va[cell];
         }
@@ -394,7 +404,7 @@ void markers_weights(const Geo& g, int N, const double* q, int* idx, double* w64
 }
 
 void markers_build_gather(const Geo& g, MarkerData& md, cudaStream_t s) {
-    const int S = g.d == 3 ? 64 : 16;
+    const int S = g.d == 3 ? g.kw * g.kw * g.kw : g.kw * g.kw;
     long long E = (long long)md.N * g.d * S;
     long long P = BS_ELEMS;
     while (P < E) P <<= 1;
@@ -468,11 +478,20 @@ void interp(const Geo& g, const MarkerData& md, const T* v, T* out, double sign,
     const T* w = sizeof(T) == 8 ? reinterpret_cast<const T*>(md.w64) : reinterpret_cast<const T*>(md.w32);
     int threads = 128;
     int blocks = grid_1d((long long)md.N * 32, threads);
-    ProfScope ps(KID_INTERP, s, (double)md.N * g.d * ((g.d == 3 ? 64 : 16) * sizeof(T) + g.d * 4 * sizeof(T) + sizeof(T)));
-    if (g.d == 3)
-        k_interp<3, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
-    else
-        k_interp<2, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
+    const int kw = g.kw;
+    ProfScope ps(KID_INTERP, s,
+                 (double)md.N * g.d * ((g.d == 3 ? kw * kw * kw : kw * kw) * sizeof(T) + g.d * kw * sizeof(T) + sizeof(T)));
+    if (g.d == 3) {
+        if (kw == 6)
+            k_interp<3, 6, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
+        else
+            k_interp<3, 4, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
+    } else {
+        if (kw == 6)
+            k_interp<2, 6, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
+        else
+            k_interp<2, 4, T, Tadd><<<blocks, threads, 0, s>>>(g, md.N, md.idx, w, v, out, (T)sign, add, (T)add_scale);
+    }
     IBR_CHECK_LAUNCH();
 }
 

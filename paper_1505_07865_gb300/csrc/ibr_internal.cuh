@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "../../include/ibrigid.h"
 
@@ -15,11 +16,51 @@ namespace ibr {
 // 4-point Peskin kernel: the continuous function on [-2,2] fixed by
 // sum_j phi(r-j) = 1, sum_j (r-j) phi(r-j) = 0, even/odd sums 1/2 and
 // sum_j phi(r-j)^2 = 3/8.
-__device__ __forceinline__ double peskin4(double r) {
+__host__ __device__ __forceinline__ double peskin4(double r) {
     r = fabs(r);
     if (r < 1.0) return 0.125 * (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r));
     if (r < 2.0) return 0.125 * (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r));
     return 0.0;
+}
+
+// Six-point kernel of Bao, Kaye and Peskin (the kernel Sec. III.A uses):
+// support [-3, 3], zeroth to third moments 1, 0, K, 0 with
+// K = 59/60 - sqrt(29)/20, even and odd nodes half each, sum of squares C
+// fixed at the integers.  For r in [0, 1) the weights w[m] = phi(r - (m - 2)),
+// m = 0..5, follow by elimination from the five linear conditions in terms of
+// t = phi(r - 3); the sum of squares leaves 28 t^2 + b t + c = C, whose root
+// with t = 0 at r = 0 is taken (its discriminant stays >= 1.39 on [0, 1), so
+// the branch is continuous); the root is formed without cancellation on both
+// signs of b.  FP64 (set-up only).
+__host__ __device__ __forceinline__ void bkp6_weights(double r, double* w) {
+    const double K = 59.0 / 60.0 - sqrt(29.0) / 20.0;
+    const double C = (0.625 - 0.25 * K) * (0.625 - 0.25 * K) + 0.125 + 2.0 * (0.125 * K - 0.0625) * (0.125 * K - 0.0625);
+    const double r2 = r * r, r3 = r2 * r, r4 = r2 * r2, r6 = r3 * r3;
+    const double b = -(84.0 * K * r + 18.0 * K + 28.0 * r3 + 18.0 * r2 - 88.0 * r - 27.0) / 12.0;
+    const double c = (720.0 * K * K * r2 + 108.0 * K * K + 480.0 * K * r4 - 1416.0 * K * r2 - 396.0 * K + 80.0 * r6 -
+                      436.0 * r4 + 644.0 * r2 + 603.0) /
+                     1152.0;
+    const double sd = sqrt(fmax(b * b - 112.0 * (c - C), 0.0));
+    const double t = b >= 0.0 ? 2.0 * (C - c) / (b + sd) : (sd - b) / 56.0;
+    w[0] = -0.0625 + 0.125 * K - 0.25 * K * r + r / 12.0 + 0.125 * r2 - r3 / 12.0 + t;
+    w[1] = 0.25 - 2.0 * r / 3.0 + 0.5 * K * r + r3 / 6.0 - 3.0 * t;
+    w[2] = 0.625 - 0.25 * K - 0.25 * r2 + 2.0 * t;
+    w[3] = 0.25 + 2.0 * r / 3.0 - 0.5 * K * r - r3 / 6.0 + 2.0 * t;
+    w[4] = -0.0625 + 0.125 * K + 0.25 * K * r - r / 12.0 + 0.125 * r2 + r3 / 12.0 - 3.0 * t;
+    w[5] = t;
+}
+
+// The kw (4 or 6) nodes j0 .. j0 + kw - 1 of the kernel window of position s
+// (grid units from node 0) and their weights phi(s - j).
+__host__ __device__ __forceinline__ void kernel_window(int kw, double s, int& j0, double* w) {
+    const double fl = floor(s);
+    if (kw == 6) {
+        j0 = (int)fl - 2;
+        bkp6_weights(s - fl, w);
+    } else {
+        j0 = (int)fl - 1;
+        for (int m = 0; m < 4; ++m) w[m] = peskin4(s - (fl - 1.0 + m));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -46,6 +87,34 @@ bool profiling_enabled();
         ::ibr::count_launch();              \
         IBR_CUDA_TRY(cudaGetLastError());   \
     } while (0)
+
+// Programmatic dependent launch for chains of dependent kernels on one
+// stream (the V-cycle, P_S): a kernel launched by launch_k may be scheduled
+// while its predecessor drains (its launch latency overlaps the predecessor's
+// last wave); it lets its own successor do the same (pdl_start) and waits for
+// the predecessor's results in hardware (griddepcontrol.wait) before reading
+// any input.  Kernels launched this way call pdl_start() first; outside a
+// programmatic launch both are no-ops.  IBR_PDL=0 in the environment: plain
+// launches.
+__device__ __forceinline__ void pdl_start() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    IBR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 // Runs a set-up step (e.g. cudaFuncSetAttribute, which acts on the current
 // device only) once per CUDA device, from any host thread: the step runs with
@@ -106,6 +175,7 @@ struct Geo {
     long long ncell;
     double h;
     int wall;
+    int kw;  // support of the kernel of J and S: 4 (Peskin) or 6 (Bao, Kaye, Peskin)
 };
 
 // field codes of the stencil and multigrid kernels: velocity components
@@ -121,6 +191,7 @@ inline Geo make_geo(int d, const int* n, double h) {
     g.ncell = (long long)g.n0 * g.n1 * g.n2;
     g.h = h;
     g.wall = 0;
+    g.kw = 4;
     return g;
 }
 
@@ -313,9 +384,9 @@ struct MarkerData {
     double* rel = nullptr;      // [N][d] q - X_body (unwrapped lever arm)
     int* body = nullptr;        // [N]
     int* body_start = nullptr;  // [B+1]
-    int* idx = nullptr;         // [N][d][d][4] stored node of window node m, comp alpha, axis beta
-    double* w64 = nullptr;      // [N][d][d][4] signed weights (mirror images carry -1)
-    float* w32 = nullptr;       // [N][d][d][4]
+    int* idx = nullptr;         // [N][d][d][kw] stored node of window node m, comp alpha, axis beta
+    double* w64 = nullptr;      // [N][d][d][kw] signed weights (mirror images carry -1)
+    float* w32 = nullptr;       // [N][d][d][kw]
     // face-major gather lists of S: faces F, entries E
     long long F = 0, E = 0;
     long long* face = nullptr;  // [F] alpha*ncell + cell

@@ -8,12 +8,22 @@
 #include <mutex>
 #include <vector>
 
+#include <cstdlib>
+
 #include "ibr_internal.cuh"
 
 namespace ibr {
 
 static std::atomic<long long> g_launches{0};
 static bool g_prof = false;
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("IBR_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 struct Pending {
     int kid;

@@ -583,11 +583,8 @@ void opts_default(ibr_solve_opts* o) {
     o->mg_pre = 2;
     o->mg_post = 2;
     o->mob_model = IBR_MOB_AUTO;
-    o->mob_a_over_h = 0.0;
-    // App. B functional form; builder-chosen coefficients (see the package's
-    // mobility notes): f~ -> ln x + 0.277 and g~ -> 1 at large x
-    const double c[9] = {0.6, 0.277, 1.0, 0.0, 0.6, 0.25, 1.0, 0.0, 0.5};
-    std::memcpy(o->mob_coef, c, sizeof(c));
+    o->mob_a_over_h = 0.0;            // the kernel's value (ibr_mobility_defaults)
+    for (double& c : o->mob_coef) c = 0.0;  // all zero: the kernel's fitted App. B set
     o->time_cap_ms = 0.0;
 }
 
@@ -598,6 +595,22 @@ double mob_self(const MobParams& p) {
     return std::log(p.l / (3.708 * p.a)) / (4.0 * M_PI * p.eta);
 }
 
+// The library's 2-D steady M~ (App. B, Eq. fg_steady_2d) per kernel: the
+// coefficients a0..a4, b0..b3 of the rational forms and the marker radius a/h
+// of the self-mobility f(0) = ln(l / (3.708 a)) / (4 pi eta), fitted by the
+// paper's procedure (Sec. IV.B, App. B) to the library's own periodic pair
+// mobility on a 256^2 grid (fit_mobility_2d.py; its output is
+// mobility_fit_2d.json beside this package: rms error 0.003 in f~, 0.006 in g~
+// over 0.1 <= r/h <= 20)
+constexpr double AOH_2D_PESKIN4 = 1.0427568763030746;
+constexpr double AOH_2D_BKP6 = 1.2268447983609203;
+constexpr double COEF_2D_PESKIN4[9] = {0.4285760175890488, 0.07516239469333616, 0.15497843271654263,
+                                       0.2490767399813471, 0.14442948562926494, 0.17060454818657458,
+                                       0.09800169052231841, 4.121975016785502e-14, 0.18362839492192692};
+constexpr double COEF_2D_BKP6[9] = {0.31867428077511517, 0.029809829931491737, 0.09128850757187502,
+                                    0.21765971572545198, 0.10879540295508049, 0.13289304886387499,
+                                    0.055576820005161384, 2.9295447563918447e-15, 0.14216790154120185};
+
 MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
     MobParams p;
     std::memset(&p, 0, sizeof(p));
@@ -606,10 +619,13 @@ MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
     require(model == IBR_MOB_RPY || model == IBR_MOB_FIT2D, "unknown mob_model");
     require(!(model == IBR_MOB_FIT2D && G->d != 2), "IBR_MOB_FIT2D is a 2-D model");
     require(!(model == IBR_MOB_RPY && G->d != 3), "IBR_MOB_RPY is a 3-D model");
-    // default marker radius: a = 1.25 h for the 4-point kernel in 3-D (Sec. IV.A);
-    // in 2-D the value at which ln(l/(3.708 a))/(4 pi eta) equals the discrete
-    // periodic self-mobility of the 4-point kernel, a = 1.04 h
-    double aoh = o.mob_a_over_h > 0 ? o.mob_a_over_h : (model == IBR_MOB_RPY ? 1.25 : 1.04);
+    // default marker radius: in 3-D a = 1.25 h for the 4-point kernel and
+    // 1.47 h for the six-point kernel (Sec. IV.A); in 2-D the value at which
+    // ln(l/(3.708 a))/(4 pi eta) equals the kernel's discrete periodic
+    // self-mobility (App. B)
+    const bool six = G->geo.kw == 6;
+    double aoh = o.mob_a_over_h > 0 ? o.mob_a_over_h
+                                    : (model == IBR_MOB_RPY ? (six ? 1.47 : 1.25) : (six ? AOH_2D_BKP6 : AOH_2D_PESKIN4));
     p.model = model;
     p.eta = G->eta;
     p.h = G->h;
@@ -624,7 +640,12 @@ MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
     p.a = aoh * G->h;
     // periodic-image correction of App. A (fully periodic boxes only)
     p.corr = (model == IBR_MOB_RPY && !G->walls()) ? 2.84 / (6.0 * M_PI * G->eta * G->L[0]) : 0.0;
-    std::memcpy(p.coef, o.mob_coef, sizeof(p.coef));
+    bool zero = true;
+    for (double c : o.mob_coef) zero = zero && c == 0.0;
+    if (zero)
+        std::memcpy(p.coef, six ? COEF_2D_BKP6 : COEF_2D_PESKIN4, sizeof(p.coef));
+    else
+        std::memcpy(p.coef, o.mob_coef, sizeof(p.coef));
     return p;
 }
 
@@ -725,7 +746,7 @@ double build_true_mobility(ibr_grid* G, double* M0) {
 // J(x0 + q_i - q_j) v is M_ij up to that (small) dependence on the sub-cell
 // position, which the average over the source points reduces.
 // Pair tables are shared by all grids of one shape (device, cells, box,
-// eta, rho, dt): the first grid that needs one builds it, grids created
+// eta, rho, dt, kernel): the first grid that needs one builds it, grids created
 // later (e.g. several resident grids of a serving engine) reuse it; it is
 // freed with the last grid that holds it.
 struct PairTable {
@@ -744,8 +765,8 @@ std::string pair_key(const ibr_grid* G) {
     int dev = 0;
     cudaGetDevice(&dev);
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "%d|%d|%d,%d,%d|%.17g,%.17g,%.17g|%.17g|%.17g|%.17g", dev, G->d, G->n[0], G->n[1],
-                  G->n[2], G->L[0], G->L[1], G->L[2], G->eta, G->rho, G->dt);
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d,%d,%d|%.17g,%.17g,%.17g|%.17g|%.17g|%.17g|k%d", dev, G->d, G->n[0],
+                  G->n[1], G->n[2], G->L[0], G->L[1], G->L[2], G->eta, G->rho, G->dt, G->geo.kw);
     return buf;
 }
 
@@ -912,9 +933,10 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     md.rel = dalloc<double>((size_t)N * d);
     md.body = dalloc<int>(N);
     md.body_start = dalloc<int>(B + 1);
-    md.idx = dalloc<int>((size_t)N * d * d * 4);
-    md.w64 = dalloc<double>((size_t)N * d * d * 4);
-    md.w32 = dalloc<float>((size_t)N * d * d * 4);
+    const int kw = G->geo.kw;
+    md.idx = dalloc<int>((size_t)N * d * d * kw);
+    md.w64 = dalloc<double>((size_t)N * d * d * kw);
+    md.w32 = dalloc<float>((size_t)N * d * d * kw);
     IBR_CUDA_TRY(cudaMemcpyAsync(rb_dev, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     IBR_CUDA_TRY(cudaMemcpyAsync(xcR_dev, xcR.data(), xcR.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     IBR_CUDA_TRY(cudaMemcpyAsync(md.body, body.data(), body.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1557,7 +1579,9 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
             require(std::fabs(L[a] / n[a] - h) <= 1e-12 * h, "cells must be cubes (L[a]/n[a] equal)");
         require(eta > 0, "eta must be positive");
         require(rho >= 0 && dt >= 0, "rho, dt must be >= 0");
-        require(kernel == IBR_KERNEL_PESKIN4, "kernel must be IBR_KERNEL_PESKIN4");
+        require(kernel == IBR_KERNEL_PESKIN4 || kernel == IBR_KERNEL_BKP6,
+                "kernel must be IBR_KERNEL_PESKIN4 or IBR_KERNEL_BKP6");
+        require(kernel == IBR_KERNEL_PESKIN4 || wall == 0, "IBR_KERNEL_BKP6 needs a periodic box");
         require(precision == IBR_FP64 || precision == IBR_MIXED, "precision must be IBR_FP64 or IBR_MIXED");
         std::unique_ptr<ibr_grid> G(new ibr_grid());
         G->d = dim;
@@ -1574,6 +1598,7 @@ int ibr_create_grid(ibr_grid** out, int dim, const int* n, const double* L, cons
         G->precision = precision;
         G->geo = make_geo(dim, n, h);
         G->geo.wall = wall;
+        G->geo.kw = kernel == IBR_KERNEL_BKP6 ? 6 : 4;
         require(G->geo.ncell < (1LL << 31), "a field must have fewer than 2^31 cells");
         G->nS = (long long)(dim + 1) * G->geo.ncell;
         G->len = G->nS;
@@ -1984,6 +2009,17 @@ int ibr_op_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float
         }
         IBR_CUDA_TRY(cudaFreeAsync(err, s));
         if (herr) throw Error{IBR_ECUDA, "a tensor-core product timed out waiting for its MMAs"};
+    });
+}
+
+int ibr_mobility_defaults(int dim, int kernel, double* a_over_h, double* coef9) {
+    return run_guarded("ibr_mobility_defaults", [&] {
+        require(dim == 2 || dim == 3, "dim must be 2 or 3");
+        require(kernel == IBR_KERNEL_PESKIN4 || kernel == IBR_KERNEL_BKP6, "unknown kernel");
+        const bool six = kernel == IBR_KERNEL_BKP6;
+        if (a_over_h) *a_over_h = dim == 3 ? (six ? 1.47 : 1.25) : (six ? AOH_2D_BKP6 : AOH_2D_PESKIN4);
+        if (coef9)
+            for (int q = 0; q < 9; ++q) coef9[q] = dim == 2 ? (six ? COEF_2D_BKP6 : COEF_2D_PESKIN4)[q] : 0.0;
     });
 }
 

@@ -158,6 +158,7 @@ constexpr int BX = 32, BY = 8;
 template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_stokes(const T* __restrict__ x, T* __restrict__ y, Geo g, T sigma, T kh2,
                                                 T ih, const double* __restrict__ shift) {
+    pdl_start();
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
@@ -467,6 +468,7 @@ __device__ void coarse_block(T* su, T* sf, const Geo& g, int fld, T sigma, T kh2
 template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __restrict__ f, Geo g, int fld0, T sigma,
                                               T kh2, T inv_diag, int color, int zero_init) {
+    pdl_start();
     int ih = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     int k = blockIdx.z % g.n2, cmp = blockIdx.z / g.n2;
     if (ih >= (g.n0 >> 1) || j >= g.n1) return;
@@ -484,6 +486,7 @@ __global__ void __launch_bounds__(256) k_rbgs(T* __restrict__ u, const T* __rest
 template <typename T>
 __global__ void __launch_bounds__(256) k_rbgs_col(T* __restrict__ u, const T* __restrict__ f, Geo g, int nkb, int kz,
                                                   T kh2, T inv_diag, int color, int zero_init) {
+    pdl_start();
     const int ih = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     const int cmp = blockIdx.z / nkb, kb = blockIdx.z - cmp * nkb;
     if (ih >= (g.n0 >> 1) || j >= g.n1) return;
@@ -516,6 +519,7 @@ template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f,
                                                         T* __restrict__ fc, Geo gf, Geo gc, int fld0, T sigma,
                                                         T kh2) {
+    pdl_start();
     int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
     int K = blockIdx.z % gc.n2, cmp = blockIdx.z / gc.n2;
     if (I >= gc.n0 || J >= gc.n1) return;
@@ -527,6 +531,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ u,
 template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ u, const T* __restrict__ uc, Geo gf, Geo gc,
                                                  int fld0) {
+    pdl_start();
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     int k = blockIdx.z % gf.n2, cmp = blockIdx.z / gf.n2;
     if (i >= gf.n0 || j >= gf.n1) return;
@@ -658,6 +663,7 @@ __global__ void __launch_bounds__(1024) k_mg_tail(const __grid_constant__ TailLe
                                                   const T* __restrict__ fg,
                                                   int fld0, T sigma, int zero_start, int pre, int post,
                                                   int sweeps) {
+    pdl_start();
     extern __shared__ unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[32];
@@ -716,6 +722,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_mg_cluster(const __grid_constant__ ClusterLevels cl, T* __restrict__ ug,
                                                      const T* __restrict__ fg,
                                                      T sigma, int zero_start, int pre, int post, int sweeps) {
+    pdl_start();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[32];
@@ -896,6 +903,7 @@ __global__ void __launch_bounds__(1024) k_mg_cluster(const __grid_constant__ Clu
 template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_ps_div(const T* __restrict__ y, const T* __restrict__ hd,
                                                 T* __restrict__ qr, T rhs_scale, T* __restrict__ q, Geo g, T ih) {
+    pdl_start();
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
@@ -926,6 +934,7 @@ template <int D, bool W, typename T>
 __global__ void __launch_bounds__(256) k_ps_finish(const T* __restrict__ y, const T* __restrict__ phi,
                                                    const T* __restrict__ q, T* __restrict__ z, Geo g, T h, T c_q,
                                                    T c_phi) {
+    pdl_start();
     int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     if (i >= g.n0 || j >= g.n1) return;
     Nbr n = neighbours<D>(g, i, j, k);
@@ -1022,14 +1031,14 @@ void stokes_apply(const Geo& g, const T* x, T* y, double sigma, double eta, cons
     const bool w = g.wall != 0;
     if (g.d == 3) {
         if (w)
-            k_stokes<3, true, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+            launch_k(k_stokes<3, true, T>, grid, blk, 0, s, x, y, g, (T)sigma, kh2, ih, shift_dev);
         else
-            k_stokes<3, false, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+            launch_k(k_stokes<3, false, T>, grid, blk, 0, s, x, y, g, (T)sigma, kh2, ih, shift_dev);
     } else {
         if (w)
-            k_stokes<2, true, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+            launch_k(k_stokes<2, true, T>, grid, blk, 0, s, x, y, g, (T)sigma, kh2, ih, shift_dev);
         else
-            k_stokes<2, false, T><<<grid, blk, 0, s>>>(x, y, g, (T)sigma, kh2, ih, shift_dev);
+            launch_k(k_stokes<2, false, T>, grid, blk, 0, s, x, y, g, (T)sigma, kh2, ih, shift_dev);
     }
     IBR_CHECK_LAUNCH();
 }
@@ -1062,7 +1071,7 @@ template <typename T>
 void launch_col(const Geo& g, T* u, const T* f, int C, ColTile t, T kh2, T inv, int color, int zi, cudaStream_t s) {
     const int nkb = (g.n2 + t.kz - 1) / t.kz;
     dim3 gc(((g.n0 >> 1) + 31) / 32, (g.n1 + t.by - 1) / t.by, nkb * C), blk(32, t.by);
-    k_rbgs_col<T><<<gc, blk, 0, s>>>(u, f, g, nkb, t.kz, kh2, inv, color, zi);
+    launch_k(k_rbgs_col<T>, gc, blk, 0, s, u, f, g, nkb, t.kz, kh2, inv, color, zi);
 }
 
 template <typename T>
@@ -1145,16 +1154,16 @@ void mg_smooth(const Geo& g, T* u, const T* f, int C, int fld0, double sigma, do
     if (g.d == 3) {
         T inv = rbgs_inv_diag<3, T>(sg, kh2);
         if (g.wall) {
-            k_rbgs<3, true, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+            launch_k(k_rbgs<3, true, T>, grid, blk, 0, s, u, f, g, fld0, sg, kh2, inv, color, zi);
         } else {
             launch_col<T>(g, u, f, C, col_tile(g, C, sizeof(T)), kh2, inv, color, zi, s);
         }
     } else {
         T inv = rbgs_inv_diag<2, T>(sg, kh2);
         if (g.wall)
-            k_rbgs<2, true, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+            launch_k(k_rbgs<2, true, T>, grid, blk, 0, s, u, f, g, fld0, sg, kh2, inv, color, zi);
         else
-            k_rbgs<2, false, T><<<grid, blk, 0, s>>>(u, f, g, fld0, sg, kh2, inv, color, zi);
+            launch_k(k_rbgs<2, false, T>, grid, blk, 0, s, u, f, g, fld0, sg, kh2, inv, color, zi);
     }
     IBR_CHECK_LAUNCH();
 }
@@ -1167,14 +1176,14 @@ void mg_residual_restrict(const Geo& gf, const Geo& gc, const T* u, const T* f, 
     ProfScope ps(KID_RESTRICT, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
     if (gf.d == 3) {
         if (gf.wall)
-            k_resid_restrict<3, true, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+            launch_k(k_resid_restrict<3, true, T>, grid, blk, 0, s, u, f, fc, gf, gc, fld0, (T)sigma, kh2);
         else
-            k_resid_restrict<3, false, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+            launch_k(k_resid_restrict<3, false, T>, grid, blk, 0, s, u, f, fc, gf, gc, fld0, (T)sigma, kh2);
     } else {
         if (gf.wall)
-            k_resid_restrict<2, true, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+            launch_k(k_resid_restrict<2, true, T>, grid, blk, 0, s, u, f, fc, gf, gc, fld0, (T)sigma, kh2);
         else
-            k_resid_restrict<2, false, T><<<grid, blk, 0, s>>>(u, f, fc, gf, gc, fld0, (T)sigma, kh2);
+            launch_k(k_resid_restrict<2, false, T>, grid, blk, 0, s, u, f, fc, gf, gc, fld0, (T)sigma, kh2);
     }
     IBR_CHECK_LAUNCH();
 }
@@ -1185,14 +1194,14 @@ void mg_prolong_correct(const Geo& gf, const Geo& gc, T* u, const T* uc, int C, 
     ProfScope ps(KID_PROLONG, s, (2.0 * gf.ncell + gc.ncell) * C * sizeof(T));
     if (gf.d == 3) {
         if (gf.wall)
-            k_prolong<3, true, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+            launch_k(k_prolong<3, true, T>, grid, blk, 0, s, u, uc, gf, gc, fld0);
         else
-            k_prolong<3, false, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+            launch_k(k_prolong<3, false, T>, grid, blk, 0, s, u, uc, gf, gc, fld0);
     } else {
         if (gf.wall)
-            k_prolong<2, true, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+            launch_k(k_prolong<2, true, T>, grid, blk, 0, s, u, uc, gf, gc, fld0);
         else
-            k_prolong<2, false, T><<<grid, blk, 0, s>>>(u, uc, gf, gc, fld0);
+            launch_k(k_prolong<2, false, T>, grid, blk, 0, s, u, uc, gf, gc, fld0);
     }
     IBR_CHECK_LAUNCH();
 }
@@ -1427,17 +1436,19 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         const long long n0 = lev[lt].ncell;
         ProfScope ps(KID_COARSE, s, 2.0 * C * n0 * sizeof(T));
         cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
+        cudaLaunchAttribute at[2];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = MG_CL;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.gridDim = dim3(MG_CL * C, 1, 1);
         cfg.blockDim = dim3(1024, 1, 1);
         cfg.dynamicSmemBytes = MG_CL_SMEM;
         cfg.stream = s;
         cfg.attrs = at;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = pdl_enabled() ? 2 : 1;
         T* ut = U[lt];
         const T* ft = Fl(lt);
         IBR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_mg_cluster<T>, cl, ut, ft, sg, z, pre, post, coarse_sweeps));
@@ -1452,17 +1463,17 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         mg_set_attributes<T>();
         if (lev[0].d == 3) {
             if (lev[0].wall)
-                k_mg_tail<3, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
+                launch_k(k_mg_tail<3, true, T>, C, nt, sm, s, tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                        coarse_sweeps);
             else
-                k_mg_tail<3, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
+                launch_k(k_mg_tail<3, false, T>, C, nt, sm, s, tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                         coarse_sweeps);
         } else {
             if (lev[0].wall)
-                k_mg_tail<2, true, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
+                launch_k(k_mg_tail<2, true, T>, C, nt, sm, s, tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                        coarse_sweeps);
             else
-                k_mg_tail<2, false, T><<<C, nt, sm, s>>>(tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
+                launch_k(k_mg_tail<2, false, T>, C, nt, sm, s, tl, U[lt], Fl(lt), fld0, sg, z, pre, post,
                                                         coarse_sweeps);
         }
         IBR_CHECK_LAUNCH();
@@ -1563,14 +1574,14 @@ void ps_divergence(const Geo& g, const T* y, const T* hd, T* q_rhs, double rhs_s
     const T ih = (T)(1.0 / g.h), rs = (T)rhs_scale;
     if (g.d == 3) {
         if (g.wall)
-            k_ps_div<3, true, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+            launch_k(k_ps_div<3, true, T>, grid, blk, 0, s, y, hd, q_rhs, rs, q, g, ih);
         else
-            k_ps_div<3, false, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+            launch_k(k_ps_div<3, false, T>, grid, blk, 0, s, y, hd, q_rhs, rs, q, g, ih);
     } else {
         if (g.wall)
-            k_ps_div<2, true, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+            launch_k(k_ps_div<2, true, T>, grid, blk, 0, s, y, hd, q_rhs, rs, q, g, ih);
         else
-            k_ps_div<2, false, T><<<grid, blk, 0, s>>>(y, hd, q_rhs, rs, q, g, ih);
+            launch_k(k_ps_div<2, false, T>, grid, blk, 0, s, y, hd, q_rhs, rs, q, g, ih);
     }
     IBR_CHECK_LAUNCH();
 }
@@ -1583,14 +1594,14 @@ void ps_finish(const Geo& g, const T* y, const T* phi, const T* q, T* z, double 
     const T h = (T)g.h, cq = (T)c_q, cp = (T)c_phi;
     if (g.d == 3) {
         if (g.wall)
-            k_ps_finish<3, true, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+            launch_k(k_ps_finish<3, true, T>, grid, blk, 0, s, y, phi, q, z, g, h, cq, cp);
         else
-            k_ps_finish<3, false, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+            launch_k(k_ps_finish<3, false, T>, grid, blk, 0, s, y, phi, q, z, g, h, cq, cp);
     } else {
         if (g.wall)
-            k_ps_finish<2, true, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+            launch_k(k_ps_finish<2, true, T>, grid, blk, 0, s, y, phi, q, z, g, h, cq, cp);
         else
-            k_ps_finish<2, false, T><<<grid, blk, 0, s>>>(y, phi, q, z, g, h, cq, cp);
+            launch_k(k_ps_finish<2, false, T>, grid, blk, 0, s, y, phi, q, z, g, h, cq, cp);
     }
     IBR_CHECK_LAUNCH();
 }

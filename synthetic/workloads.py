@@ -67,6 +67,7 @@ class Workload:
     bodies: list = field(default_factory=list)
     tol: float = 1e-8
     walls: tuple = ()           # per axis: True for walls at both ends (empty: all periodic)
+    kernel: str = "peskin4"     # regularised delta of J and S: "peskin4" or "bkp6" (six-point)
 
     @property
     def d(self):

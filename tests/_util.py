@@ -10,7 +10,7 @@ from oracle.system import Problem
 
 def oracle_problem(wl):
     q, rel, body = wl.markers()
-    g = Grid(wl.n, wl.L, wl.eta, wl.rho, wl.dt)
+    g = Grid(wl.n, wl.L, wl.eta, wl.rho, wl.dt, kernel=wl.kernel)
     q = np.mod(q, np.array(wl.L))
     return Problem(g, q, rel, body, len(wl.bodies))
 
@@ -26,7 +26,9 @@ def gpu_grid(abi, wl, precision, free=None, data=None):
                 bc.append(abi.PERIODIC)
             else:
                 bc.append(abi.VELOCITY if data is not None and (a, s) in data else abi.NOSLIP)
-    g = abi.create_grid(wl.d, wl.n, wl.L, bc=bc, eta=wl.eta, rho=wl.rho, dt=wl.dt, precision=precision)
+    kernel = abi.KERNEL_BKP6 if wl.kernel == "bkp6" else abi.KERNEL_PESKIN4
+    g = abi.create_grid(wl.d, wl.n, wl.L, bc=bc, eta=wl.eta, rho=wl.rho, dt=wl.dt, kernel=kernel,
+                        precision=precision)
     if data is not None:
         for (a, s), val in data.items():
             abi.set_boundary_velocity(g, 2 * a + s, np.ascontiguousarray(val, dtype=np.float64).ravel())

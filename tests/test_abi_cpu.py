@@ -55,6 +55,26 @@ def test_default_options(abi):
     o = abi.solve_opts_default()
     assert o.tol == 1e-8 and o.restart == 50 and o.n_s == 0 and o.variant == abi.PC_LOWER
     assert o.mg_pre == 2 and o.mg_post == 2 and o.mob_model == abi.MOB_AUTO
+    # zero radius and coefficients: the grid kernel's defaults
+    assert o.mob_a_over_h == 0.0 and not any(o.mob_coef)
+
+
+def test_mobility_defaults_are_the_committed_fit(abi):
+    # 3-D radii are the paper's (Sec. IV.A); the 2-D App. B sets are the
+    # output of the package's fit script (fit_mobility_2d.py, 256^2 fits)
+    import json
+    import os
+
+    fit = json.load(open(os.path.join(os.path.dirname(abi.__file__), "mobility_fit_2d.json")))
+    for kernel, a3 in ((abi.KERNEL_PESKIN4, 1.25), (abi.KERNEL_BKP6, 1.47)):
+        aoh, coef = abi.mobility_defaults(3, kernel)
+        assert aoh == a3 and not coef.any()
+        f = [x for x in fit["fits"] if x["kernel"] == kernel and x["n"] == 256][0]
+        aoh, coef = abi.mobility_defaults(2, kernel)
+        assert aoh == f["a_over_h"]
+        assert list(coef) == f["a"] + f["b"]
+    with pytest.raises(abi.IbrError):
+        abi.mobility_defaults(2, 5)
 
 
 @pytest.mark.parametrize("args,msg", [

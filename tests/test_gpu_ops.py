@@ -134,7 +134,8 @@ def test_mtilde_build_parity_2d_form(abi):
         n = rel.size
         out = torch.zeros(n * n, dtype=torch.float64, device="cuda")
         abi.op_mtilde(G, 0, out)
-        ref = mobility.mtilde_2d_steady(rel, 1.0 / 64, 1.0, 1.0, 1.04, list(o.mob_coef))
+        aoh, coef = abi.mobility_defaults(2)
+        ref = mobility.mtilde_2d_steady(rel, 1.0 / 64, 1.0, 1.0, aoh, list(coef))
         assert rel_err(out.cpu().numpy(), ref) < TOL
     finally:
         abi.destroy_grid(G)
