@@ -84,6 +84,10 @@ extern "C" {
 #define IBR_MOB_AUTO  0        /* RPY (3-D) / App. B steady form (2-D)            */
 #define IBR_MOB_RPY   1        /* Eq. RPYTensor (+ periodic correction, App. A)   */
 #define IBR_MOB_FIT2D 2        /* App. B Eq. fg_steady_2d                          */
+                               /* (analytic forms: with several bodies one dense
+                                  block of all markers, minimum-image distances
+                                  on periodic axes, while dim N <= 6144; else one
+                                  block per body, Sec. VIII)                     */
 #define IBR_MOB_TRUE  3        /* the true mobility M0 = J L^-1 S of all markers,
                                   one dense block, built in the set-up from
                                   N*dim Stokes solves (Sec. V.C, VII.F: for
@@ -281,10 +285,10 @@ int ibr_op_interp(ibr_grid* g, const double* v, double* U);
 int ibr_op_rigid(ibr_grid* g, const double* UO, double* V);
 int ibr_op_rigid_T(ibr_grid* g, const double* lam, double* FT);
 
-/* Copies dense mobility block b into out (row-major): the M~ block of body b
- * ((dim N_b)^2 doubles, Eq. M_tilde_ij), or the single block of all markers
- * ((dim N)^2 doubles, b = 0) with IBR_MOB_TRUE (M0) and with IBR_MOB_PAIR
- * while dim N <= 6144. */
+/* Copies dense mobility block b into out (row-major): the single block of all
+ * markers ((dim N)^2 doubles, b = 0) with IBR_MOB_TRUE (M0), and for one body or
+ * several bodies while dim N <= 6144 (Eq. M_tilde_ij for every marker pair);
+ * else the M~ block of body b ((dim N_b)^2 doubles). */
 int ibr_op_mtilde(ibr_grid* g, int body, double* out);
 
 /* out = M~^-1 rhs (block diagonal over bodies, [N*dim]) with the factorised

@@ -52,14 +52,20 @@ def fg_2d_steady(r, h, eta, l, a, coef):
     return f0 - ft / (4.0 * np.pi * eta), gt / (4.0 * np.pi * eta)
 
 
-def mtilde_block(rel, fg):
-    """Dense d N x d N block from pair functions fg(r) -> (f, g)."""
+def mtilde_block(rel, fg, box=None):
+    """Dense d N x d N block from pair functions fg(r) -> (f, g) (Eq.
+    M_tilde_ij: every marker pair).  box: periodic lengths per axis (0 for a
+    wall axis); displacements are then the minimum images."""
     rel = np.asarray(rel, dtype=np.float64)
     N, d = rel.shape
     M = np.zeros((N * d, N * d))
     for i in range(N):
         for j in range(N):
             rv = rel[i] - rel[j]
+            if box is not None:
+                for a in range(d):
+                    if box[a] > 0:
+                        rv[a] -= box[a] * np.round(rv[a] / box[a])
             r = np.sqrt(np.dot(rv, rv))
             f, g = fg(np.array(r))
             f = float(f)
@@ -72,7 +78,7 @@ def mtilde_block(rel, fg):
     return M
 
 
-def mtilde_3d_rpy(rel, h, eta, l, a_over_h=1.25, periodic=True):
+def mtilde_3d_rpy(rel, h, eta, l, a_over_h=1.25, periodic=True, box=None):
     a = a_over_h * h
     corr = 2.84 / (6.0 * np.pi * eta * l) if periodic else 0.0
 
@@ -80,12 +86,12 @@ def mtilde_3d_rpy(rel, h, eta, l, a_over_h=1.25, periodic=True):
         f, g = rpy_fg(r, a, eta)
         return f - corr, g
 
-    return mtilde_block(rel, fg)
+    return mtilde_block(rel, fg, box)
 
 
-def mtilde_2d_steady(rel, h, eta, l, a_over_h, coef):
+def mtilde_2d_steady(rel, h, eta, l, a_over_h, coef, box=None):
     a = a_over_h * h
-    return mtilde_block(rel, lambda r: fg_2d_steady(r, h, eta, l, a, coef))
+    return mtilde_block(rel, lambda r: fg_2d_steady(r, h, eta, l, a, coef), box)
 
 
 def pair_table_mtilde(grid, q, x0s):

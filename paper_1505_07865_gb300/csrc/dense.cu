@@ -52,6 +52,7 @@ __global__ void k_mtilde(int Nb, const double* __restrict__ rel, MobParams p, do
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         rv[a] = rel[i * D + a] - rel[j * D + a];
+        if (p.box[a] > 0.0) rv[a] -= p.box[a] * rint(rv[a] / p.box[a]);
         r2 += rv[a] * rv[a];
     }
     double r = sqrt(r2);

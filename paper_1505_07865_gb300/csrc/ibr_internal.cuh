@@ -232,9 +232,13 @@ void mg_coarse_solve(const Geo& g, T* u, const T* f, int C, int fld0, double sig
 constexpr int MG_TAIL_MAX_LEVELS = 8;
 constexpr long long MG_TAIL_MAX_CELLS = 4096;
 constexpr size_t MG_TAIL_MAX_SMEM = 200 * 1024;
+// rb_u, rb_f: scratch of C * lev[0].ncell each (or NULL): with them a periodic
+// 3-D finest level (n0 a multiple of 8) of a zero-start V-cycle with pre, post
+// >= 1 runs in red-black split layout (the same arithmetic, bitwise)
 template <typename T>
 void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
-               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s);
+               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s,
+               T* rb_u = nullptr, T* rb_f = nullptr);
 // red-black sweeps of the coarsest-level solve: enough for a preconditioner
 // (the coarsest grid has at most a few hundred cells)
 inline int mg_coarse_sweeps(const Geo& g) {
@@ -437,6 +441,7 @@ struct MobParams {
     double eta, h, l, a;
     double corr;      // periodic correction subtracted from f (3-D)
     double coef[9];
+    double box[3];    // periodic box lengths (0 on wall axes): displacements are minimum images
 };
 void mtilde_build(int d, int Nb, const double* rel_b, const MobParams& p, double* M, cudaStream_t s);
 // in place: M (n x n, row-major, SPD) -> M^-1 (full symmetric).  info_dev[0]

@@ -67,6 +67,7 @@ template <typename T>
 struct Multigrid {
     std::vector<Geo> lev;
     std::vector<T*> u, f;  // index 0 unused (caller's buffers)
+    T *rb_u = nullptr, *rb_f = nullptr;  // finest level in red-black split layout (periodic 3-D)
     int cmax = 0;
     int coarse_sweeps = 40;
 
@@ -97,8 +98,14 @@ struct Multigrid {
             g = c;
         }
         coarse_sweeps = mg_coarse_sweeps(lev.back());
+        if (g0.d == 3 && !g0.wall && g0.n0 % 8 == 0 && lev.size() > 1) {
+            rb_u = dalloc<T>((size_t)cmax * g0.ncell);
+            rb_f = dalloc<T>((size_t)cmax * g0.ncell);
+        }
     }
     void release() {
+        dfree(rb_u);
+        dfree(rb_f);
         for (auto& p : u) dfree(p);
         for (auto& p : f) dfree(p);
         u.clear();
@@ -113,7 +120,7 @@ struct Multigrid {
         std::vector<T*> U(u);
         U[0] = u0;
         mg_vcycle<T>(lev.data(), L, U.data(), f.data(), f0, C, fld0, sigma, kappa, zero_start, pre, post,
-                     coarse_sweeps, s);
+                     coarse_sweeps, s, rb_u, rb_f);
     }
 };
 
@@ -638,6 +645,7 @@ MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
             if ((G->geo.wall >> a) & 1) p.l = std::min(p.l, G->L[a]);
     }
     p.a = aoh * G->h;
+    for (int a = 0; a < 3; ++a) p.box[a] = (a < G->d && !((G->geo.wall >> a) & 1)) ? G->L[a] : 0.0;
     // periodic-image correction of App. A (fully periodic boxes only)
     p.corr = (model == IBR_MOB_RPY && !G->walls()) ? 2.84 / (6.0 * M_PI * G->eta * G->L[0]) : 0.0;
     bool zero = true;
@@ -953,7 +961,11 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     const bool true_mob = o.mob_model == IBR_MOB_TRUE;
     const bool pair_mob = o.mob_model == IBR_MOB_PAIR;
     require(!(pair_mob && G->walls()), "IBR_MOB_PAIR needs a periodic grid");
-    const bool one_block = true_mob || (pair_mob && (long long)N * d <= pair_full_max());
+    // the analytic forms and the pair table couple all bodies in one block
+    // (M~_ij for every marker pair, Sec. IV.B) while d N <= pair_full_max(),
+    // else one block per body (Sec. VIII's block-diagonal form)
+    const bool one_block = true_mob || (B > 1 && (long long)N * d <= pair_full_max()) ||
+                           (pair_mob && (long long)N * d <= pair_full_max());
     G->nblk = one_block ? 1 : B;
     const int nblk = G->nblk;
     G->moff.assign(nblk + 1, 0);
@@ -990,8 +1002,11 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
         for (int a = 0; a < d; ++a) fself += dg[a] / d;
     } else {
         MobParams mp = mob_params(G, o);
-        for (int bi = 0; bi < B; ++bi)
-            mtilde_build(d, G->bodies[bi].N, md.rel + (long long)bstart[bi] * d, mp, G->Mbuild + G->moff[bi], s);
+        if (one_block)
+            mtilde_build(d, N, md.q, mp, G->Mbuild, s);  // lab positions, minimum images
+        else
+            for (int bi = 0; bi < B; ++bi)
+                mtilde_build(d, G->bodies[bi].N, md.rel + (long long)bstart[bi] * d, mp, G->Mbuild + G->moff[bi], s);
         fself = mob_self(mp);
     }
     // info_dev[0]: failed pivot, info_dev[1]: tensor-core time-out flag
@@ -1464,6 +1479,8 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
     }
     t += pg(e * (ns + 1) * nS) + pg(e * ns * nS) + 4 * pg(e * nS) + pg(e * d * nc) + 3 * pg(e * nc);
     t += pg(8.0 * RED_BLOCKS * std::max(ns + 1, 4)) + 2 * pg(e * dN) + pg(8.0 * dN);
+    // the finest level's red-black split copies of u and f (periodic 3-D)
+    if (d == 3 && g.n0 % 8 == 0) t += 2 * pg(e * d * nc);
     // markers: positions, lever arms, windows (index, FP64 and FP32 weights),
     // face-major gather lists (at most 4^d faces per marker and component)
     const double win = (double)N * d * d * 4;
@@ -1490,6 +1507,8 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
              3 * pg(8.0 * nc);
         if (dN <= (double)pair_full_max()) blk2 = blkmax = dN * dN;
     }
+    // several bodies within the single-block limit: one block of all markers
+    if (B > 1 && dN <= (double)pair_full_max()) blk2 = blkmax = dN * dN;
     // mobility: built (FP64) + factorised inverse (precision) + work: the FP64
     // path's work block, or the tensor-core path's two padded blocks
     t += pg(8.0 * blk2) + pg(e * blk2);

@@ -689,6 +689,257 @@ __global__ void __launch_bounds__(1024) k_mg_tail(const __grid_constant__ TailLe
     }
 }
 
+// ---- the finest level of a periodic 3-D V-cycle in red-black split layout ----
+// During the V-cycle the finest level's u and f live in two arrays per
+// stacked field, one per colour: cell (i, j, k) of colour c = (i+j+k) & 1 at
+// index (i >> 1) + (n0/2) (j + n1 k) of colour array c (field q, colour c at
+// offset (2q + c) n/2).  A half sweep then reads the other colour's cells
+// contiguously (its x-neighbours are entries ih + p - 1 and ih + p of the
+// same row, p = (j+k+c) & 1; its y- and z-neighbours entry ih of rows j+-1
+// and planes k+-1), so every sector it loads is used, four cells per thread.
+// The conversion from and to the natural layout is folded into the first
+// (zero-start) and the last half sweep.  Same arithmetic and summation order
+// as rbgs_cell / resid_cell / prolong_cell: bitwise the same V-cycle.
+constexpr int RB_V = 4;  // cells of one colour per thread (n0 % 8 == 0)
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = double4;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+    const typename Vec4<T>::type x = *reinterpret_cast<const typename Vec4<T>::type*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+    typename Vec4<T>::type x;
+    x.x = v[0];
+    x.y = v[1];
+    x.z = v[2];
+    x.w = v[3];
+    *reinterpret_cast<typename Vec4<T>::type*>(p) = x;
+}
+
+// thread -> (field q, plane k, row j, first entry ih of its RB_V entries)
+struct RbIdx {
+    int q, k, j, ih;
+};
+__device__ __forceinline__ RbIdx rb_index(int t, int hq, FastDiv dq, int n1, FastDiv d1, int n2, FastDiv d2) {
+    RbIdx r;
+    const int row = fdiv(t, dq);
+    r.ih = (t - row * hq) * RB_V;
+    const int kk = fdiv(row, d1);
+    r.j = row - kk * n1;
+    r.q = fdiv(kk, d2);
+    r.k = kk - r.q * n2;
+    return r;
+}
+
+// the first (zero-start) half sweep of colour 0 from the natural f: writes
+// both colours of f into the split arrays and u_0 = f_0 / diag
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_first(const T* __restrict__ fnat, T* __restrict__ fs, T* __restrict__ us,
+                                                  int n0, int n1, int n2, int nthreads, FastDiv dq, FastDiv d1,
+                                                  FastDiv d2, T inv) {
+    pdl_start();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
+    const int hn = n0 >> 1, hq = hn / RB_V;
+    const RbIdx r = rb_index(t, hq, dq, n1, d1, n2, d2);
+    const long long half = (long long)hn * n1 * n2;
+    const long long rowoff = (long long)hn * (r.j + (long long)n1 * r.k) + r.ih;
+    const T* src = fnat + (long long)r.q * 2 * half + ((long long)n0 * (r.j + (long long)n1 * r.k) + 2 * r.ih);
+    T a[4], b[4];
+    ld4(src, a);
+    ld4(src + 4, b);
+    const T nat[8] = {a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3]};
+    const bool p0 = ((r.j + r.k) & 1) != 0;  // x offset of colour 0 in this row
+    T c0[4], c1[4], u0[4];
+#pragma unroll
+    for (int e = 0; e < RB_V; ++e) {
+        c0[e] = p0 ? nat[2 * e + 1] : nat[2 * e];
+        c1[e] = p0 ? nat[2 * e] : nat[2 * e + 1];
+        u0[e] = c0[e] * inv;  // the zero-start update (f + kappa h^-2 0) / diag
+    }
+    T* f0 = fs + (long long)(2 * r.q) * half;
+    T* f1 = f0 + half;
+    st4(f0 + rowoff, c0);
+    st4(f1 + rowoff, c1);
+    st4(us + (long long)(2 * r.q) * half + rowoff, u0);
+}
+
+// half sweep of colour c in split layout; last != 0: also writes both
+// colours of u to the natural array unat (the V-cycle's output)
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ us, const T* __restrict__ fs, int n0, int n1, int n2,
+                                                 int nthreads, FastDiv dq, FastDiv d1, FastDiv d2, T kh2, T inv,
+                                                 int color, T* __restrict__ unat) {
+    pdl_start();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
+    const int hn = n0 >> 1, hq = hn / RB_V;
+    const RbIdx r = rb_index(t, hq, dq, n1, d1, n2, d2);
+    const long long half = (long long)hn * n1 * n2;
+    T* dst = us + (long long)(2 * r.q + color) * half;
+    const T* src = us + (long long)(2 * r.q + 1 - color) * half;
+    const T* f = fs + (long long)(2 * r.q + color) * half;
+    const int p = (r.j + r.k + color) & 1;
+    const long long plane = (long long)hn * n1;
+    const long long row = (long long)hn * (r.j + (long long)n1 * r.k);
+    const long long rym = (long long)hn * ((r.j == 0 ? n1 - 1 : r.j - 1) + (long long)n1 * r.k);
+    const long long ryp = (long long)hn * ((r.j == n1 - 1 ? 0 : r.j + 1) + (long long)n1 * r.k);
+    const long long rzm = row + (r.k == 0 ? (long long)(n2 - 1) * plane : -plane);
+    const long long rzp = row + (r.k == n2 - 1 ? -(long long)(n2 - 1) * plane : plane);
+    T cen[4], ym[4], yp[4], zm[4], zp[4], ff[4];
+    ld4(src + row + r.ih, cen);
+    ld4(src + rym + r.ih, ym);
+    ld4(src + ryp + r.ih, yp);
+    ld4(src + rzm + r.ih, zm);
+    ld4(src + rzp + r.ih, zp);
+    ld4(f + row + r.ih, ff);
+    // the entry beyond the four: ih - 1 (p = 0) or ih + 4 (p = 1), wrapped in the row
+    const int ex = p == 0 ? (r.ih == 0 ? hn - 1 : r.ih - 1) : (r.ih + RB_V == hn ? 0 : r.ih + RB_V);
+    const T xe = src[row + ex];
+    T out[4];
+#pragma unroll
+    for (int e = 0; e < RB_V; ++e) {
+        // cell i = 2 (ih + e) + p: x+1 -> entry ih+e+p, x-1 -> entry ih+e+p-1
+        T xp, xm;
+        if (p == 0) {
+            xp = cen[e];
+            xm = e == 0 ? xe : cen[e - 1];
+        } else {
+            xp = e == RB_V - 1 ? xe : cen[e + 1];
+            xm = cen[e];
+        }
+        T nb = xp + xm + yp[e] + ym[e];
+        nb += zp[e] + zm[e];
+        out[e] = (ff[e] + kh2 * nb) * inv;
+    }
+    st4(dst + row + r.ih, out);
+    if (unat) {
+        // colour c at x = 2 (ih+e) + p, the other colour (unchanged) at 2 (ih+e) + 1 - p
+        T* o = unat + (long long)r.q * 2 * half + ((long long)n0 * (r.j + (long long)n1 * r.k) + 2 * r.ih);
+        if (p == 0) {
+            const T a[4] = {out[0], cen[0], out[1], cen[1]};
+            const T b[4] = {out[2], cen[2], out[3], cen[3]};
+            st4(o, a);
+            st4(o + 4, b);
+        } else {
+            const T a[4] = {cen[0], out[0], cen[1], out[1]};
+            const T b[4] = {cen[2], out[2], cen[3], out[3]};
+            st4(o, a);
+            st4(o + 4, b);
+        }
+    }
+}
+
+// coarse f = the averaged residual of the split finest level (resid_cell's
+// arithmetic and the restriction's child order: bitwise the natural
+// kernel's); one thread per coarse cell.  A child row (j, k) holds the
+// children 2I (colour p = (j+k) & 1, entry I of colour array p) and 2I+1
+// (entry I of array 1-p); their x-neighbours are entries I-1 of array 1-p
+// and I+1 of array p; the y- and z-neighbours entry I of the adjacent rows,
+// in the array of the other colour.  32-bit index arithmetic.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_restrict(const T* __restrict__ us, const T* __restrict__ fs,
+                                                     T* __restrict__ fc, int n0, int n1, int n2, int C, T sigma,
+                                                     T kh2, FastDiv dc0, FastDiv dc1, FastDiv dc2) {
+    pdl_start();
+    const int nc0 = n0 >> 1, nc1 = n1 >> 1, nc2 = n2 >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncc = nc0 * nc1 * nc2;
+    if (t >= ncc * C) return;
+    const int r = fdiv(t, dc0);
+    const int I = t - r * nc0;
+    const int kk = fdiv(r, dc1);
+    const int J = r - kk * nc1;
+    const int q = fdiv(kk, dc2);
+    const int K = kk - q * nc2;
+    const int hn = nc0;  // split row length n0 / 2
+    const long long half = (long long)hn * n1 * n2;
+    const T* ua[2] = {us + (long long)(2 * q) * half, us + (long long)(2 * q + 1) * half};
+    const T* fa[2] = {fs + (long long)(2 * q) * half, fs + (long long)(2 * q + 1) * half};
+    const int Im = I == 0 ? hn - 1 : I - 1, Ip = I + 1 == hn ? 0 : I + 1;
+    auto rowoff = [&](int j, int k) -> int {
+        j = j < 0 ? j + n1 : (j >= n1 ? j - n1 : j);
+        k = k < 0 ? k + n2 : (k >= n2 ? k - n2 : k);
+        return hn * (j + n1 * k);
+    };
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int a = c & 1, j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
+        const int col = (a + j + k) & 1;  // this child's colour; its neighbours are in array 1 - col
+        const T* un = ua[1 - col];
+        const int ro = rowoff(j, k);
+        const T uc = ua[col][ro + I];
+        // x+1, x-1: child 2I -> entries I (2I+1) and I-1 (2I-1); child 2I+1 -> I+1 (2I+2) and I (2I)
+        const T xp = un[ro + (a ? Ip : I)];
+        const T xm = un[ro + (a ? I : Im)];
+        T nbs = xp + xm + un[rowoff(j + 1, k) + I] + un[rowoff(j - 1, k) + I];
+        nbs += un[rowoff(j, k + 1) + I] + un[rowoff(j, k - 1) + I];
+        const T fv = fa[col][ro + I];
+        acc += fv - (sigma * uc - kh2 * (nbs - T(6) * uc));
+    }
+    fc[t] = acc * (T(1) / T(8));
+}
+
+// split finest u of colour 0 += the (tri)linear prolongation of the natural
+// coarse u (prolong_cell's weights and order).  Only colour 0: the next
+// operation, a colour-1 half sweep, overwrites every colour-1 value without
+// reading it, so correcting them would change nothing.  Four cells per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_prolong(T* __restrict__ us, const T* __restrict__ uc, int n0, int n1,
+                                                    int n2, int nthreads, FastDiv dq, FastDiv d1, FastDiv d2) {
+    pdl_start();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
+    const int hn = n0 >> 1, hq = hn / RB_V;
+    const RbIdx rr = rb_index(t, hq, dq, n1, d1, n2, d2);
+    const int nc0 = n0 >> 1, nc1 = n1 >> 1, nc2 = n2 >> 1;
+    const T* cc = uc + (long long)rr.q * nc0 * nc1 * nc2;
+    const int j = rr.j, k = rr.k;
+    const int p0 = (j + k) & 1;  // colour-0 cells of this row at x = 2 ih + p0
+    int Jc[2], Kc[2];
+    Jc[0] = j >> 1;
+    Jc[1] = (j & 1) ? (Jc[0] + 1 == nc1 ? 0 : Jc[0] + 1) : (Jc[0] == 0 ? nc1 - 1 : Jc[0] - 1);
+    Kc[0] = k >> 1;
+    Kc[1] = (k & 1) ? (Kc[0] + 1 == nc2 ? 0 : Kc[0] + 1) : (Kc[0] == 0 ? nc2 - 1 : Kc[0] - 1);
+    const T w[2] = {T(0.75), T(0.25)};
+    const long long half = (long long)hn * n1 * n2;
+    T* dst = us + (long long)(2 * rr.q) * half + (long long)hn * (j + (long long)n1 * k) + rr.ih;
+    T v[4];
+    ld4(dst, v);
+#pragma unroll
+    for (int e4 = 0; e4 < RB_V; ++e4) {
+        const int ih = rr.ih + e4;  // fine x = 2 ih + p0: parent I = ih, neighbour ih + 1 (p0 = 1) or ih - 1
+        int I[2];
+        I[0] = ih;
+        I[1] = p0 ? (ih + 1 == nc0 ? 0 : ih + 1) : (ih == 0 ? nc0 - 1 : ih - 1);
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+            const T ww = w[a] * w[b] * w[e];
+            acc += ww * cc[I[a] + nc0 * (Jc[b] + nc1 * Kc[e])];
+        }
+        v[e4] += acc;
+    }
+    st4(dst, v);
+}
+
 // ---- the coarse levels of a periodic 3-D V-cycle on one thread-block cluster ----
 // One cluster of MG_CL CTAs per stacked field runs levels cl.top .. of the
 // V-cycle in one launch.  The "distributed" levels (the first cl.nd) are split
@@ -1409,10 +1660,40 @@ int cluster_choice(const Geo* lev, int L, int C, size_t esz) {
     return it == g_cl_top.end() ? -1 : it->second;
 }
 
+// whether the finest level of this V-cycle runs in red-black split layout
+// (IBR_MG_SPLIT=0 in the environment: never)
+template <typename T>
+bool rb_split_ok(const Geo& g, const T* F0, const T* U0, const T* rb_u, const T* rb_f, bool zero_start, int pre,
+                 int post) {
+    static const bool off = [] {
+        const char* e = std::getenv("IBR_MG_SPLIT");
+        return e && e[0] == '0';
+    }();
+    const uintptr_t al = (uintptr_t)(RB_V * sizeof(T) * 2);
+    return !off && rb_u && rb_f && g.d == 3 && !g.wall && g.n0 % (2 * RB_V) == 0 && zero_start && pre >= 1 &&
+           post >= 1 &&
+           (((uintptr_t)F0 | (uintptr_t)U0 | (uintptr_t)rb_u | (uintptr_t)rb_f) % al) == 0;
+}
+
+template <typename T>
+void rb_launch_half(const Geo& g, int C, T* us, const T* fs, T kh2, T inv, int color, T* unat, cudaStream_t s) {
+    const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
+    const int hq = g.n0 / (2 * RB_V);
+    ProfScope ps(KID_RBGS, s, (unat ? 2.5 : 1.5) * C * g.ncell * sizeof(T));
+    launch_k(k_rb_half<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, us, fs, g.n0, g.n1, g.n2, nth,
+             make_fastdiv(hq), make_fastdiv(g.n1), make_fastdiv(g.n2), kh2, inv, color, unat);
+    IBR_CHECK_LAUNCH();
+}
+
 template <typename T>
 void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
-               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s) {
+               double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s, T* rb_u,
+               T* rb_f) {
     auto Fl = [&](int l) -> const T* { return l == 0 ? F0 : Fw[l]; };
+    // periodic 3-D finest level: red-black split layout (conversions folded
+    // into its first and last half sweeps)
+    const bool split = L > 1 && (long long)C * lev[0].ncell < (1LL << 31) &&
+                       rb_split_ok<T>(lev[0], F0, U[0], rb_u, rb_f, zero_start, pre, post);
     // periodic 3-D: the coarse levels on one thread-block cluster per field
     ClusterLevels cl;
     int top = 0;
@@ -1420,7 +1701,32 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
     const bool use_cluster =
         want != -2 && cluster_plan<T>(lev, L, sigma, kappa, want, top, cl) && cluster_ok<T>();
     const int lt = use_cluster ? top : tail_start<T>(lev, L);
+    const T rb_kh2 = (T)(kappa / (lev[0].h * lev[0].h));
+    const T rb_inv = rbgs_inv_diag<3, T>((T)sigma, rb_kh2);
     for (int l = 0; l < lt; ++l) {
+        if (l == 0 && split) {
+            const Geo& g = lev[0];
+            const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
+            {
+                ProfScope ps(KID_RBGS, s, 2.5 * C * g.ncell * sizeof(T));
+                launch_k(k_rb_first<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, F0, rb_f, rb_u, g.n0, g.n1, g.n2,
+                         nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2), rb_inv);
+                IBR_CHECK_LAUNCH();
+            }
+            rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+            for (int it = 1; it < pre; ++it) {
+                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, (T*)nullptr, s);
+                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+            }
+            const Geo& gc = lev[1];
+            const long long ncc = gc.ncell * C;
+            ProfScope ps(KID_RESTRICT, s, (2.0 * g.ncell + gc.ncell) * C * sizeof(T));
+            launch_k(k_rb_restrict<T>, dim3(grid_1d(ncc, 256)), dim3(256), 0, s, (const T*)rb_u, (const T*)rb_f,
+                     Fw[1], g.n0, g.n1, g.n2, C, (T)sigma, rb_kh2, make_fastdiv(gc.n0), make_fastdiv(gc.n1),
+                     make_fastdiv(gc.n2));
+            IBR_CHECK_LAUNCH();
+            continue;
+        }
         bool zs = (l > 0) || zero_start;
         if (pre == 0 && zs) IBR_CUDA_TRY(cudaMemsetAsync(U[l], 0, sizeof(T) * C * lev[l].ncell, s));
         for (int it = 0; it < pre; ++it) {
@@ -1479,6 +1785,21 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         IBR_CHECK_LAUNCH();
     }
     for (int l = lt - 1; l >= 0; --l) {
+        if (l == 0 && split) {
+            const Geo& g = lev[0];
+            {
+                const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
+                ProfScope ps(KID_PROLONG, s, (1.0 * g.ncell + lev[1].ncell) * C * sizeof(T));
+                launch_k(k_rb_prolong<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, rb_u, (const T*)U[1], g.n0, g.n1,
+                         g.n2, nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2));
+                IBR_CHECK_LAUNCH();
+            }
+            for (int it = 0; it < post; ++it) {
+                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, it + 1 == post ? U[0] : (T*)nullptr, s);
+            }
+            continue;
+        }
         mg_prolong_correct<T>(lev[l], lev[l + 1], U[l], U[l + 1], C, fld0, s);
         for (int it = 0; it < post; ++it) {
             mg_smooth<T>(lev[l], U[l], Fl(l), C, fld0, sigma, kappa, 1, false, s);
@@ -1625,7 +1946,7 @@ void wall_lift(const Geo& g, int a, int side, const double* data, double* b, dou
     template void mg_tune_smoother<T>(const Geo&, int, cudaStream_t);                                       \
     template void mg_tune_cluster<T>(const Geo*, int, T* const*, T* const*, int, int, cudaStream_t);          \
     template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, int, double, double, bool, \
-                               int, int, int, cudaStream_t);                                                \
+                               int, int, int, cudaStream_t, T*, T*);                                        \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \
     template void ps_finish<T>(const Geo&, const T*, const T*, const T*, T*, double, double, cudaStream_t);
 IBR_INST(double)

@@ -149,7 +149,10 @@ def test_device_memory_estimate_is_consistent(abi):
     # dense mobility blocks: (3 N)^2 entries in FP64 (built) + FP32 (inverse, work)
     dm = e(2, (64, 64), [2000]) - e(2, (64, 64), [1000])
     assert dm > 0
-    assert e(2, (64, 64), [2000]) - e(2, (64, 64), [1000, 1000]) > 0  # one block of 2N costs more than two of N
+    # beyond the single-block limit (d N > 6144) bodies get a block each: one
+    # block of 2N costs more than two of N; within it they share one block
+    assert e(2, (64, 64), [4000]) - e(2, (64, 64), [2000, 2000]) > 0
+    assert e(2, (64, 64), [2000]) == e(2, (64, 64), [1000, 1000])
     with pytest.raises(abi.IbrError):
         e(4, (8, 8), [1])
 

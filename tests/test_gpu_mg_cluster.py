@@ -88,3 +88,38 @@ def test_schedule_autotuner_picks_a_candidate():
     assert {t[4] for t in mine} == {1, 3}, mine
     for t in mine:
         assert t[6] in (-2, 0, 1), t
+
+
+PS_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1505_07865_gb300 import abi
+n, prec, out = {n!r}, {prec!r}, {out!r}
+G = abi.create_grid(3, n, [v / n[0] for v in n], precision=getattr(abi, prec))
+ncell = int(np.prod(n))
+r = torch.tensor(np.random.default_rng(3).standard_normal(4 * ncell), device="cuda")
+z = torch.zeros(4 * ncell, dtype=torch.float64, device="cuda")
+abi.op_stokes_pc(G, r, z)
+torch.cuda.synchronize()
+np.save(out, z.cpu().numpy())
+abi.destroy_grid(G)
+"""
+
+
+@pytest.mark.parametrize("n,prec", [((64, 48, 32), "MIXED"), ((128, 128, 128), "MIXED"), ((64, 64, 64), "FP64"),
+                                    ((96, 96, 96), "MIXED")])
+def test_split_layout_finest_level_equals_natural(tmp_path, n, prec):
+    # one application of P_S (its zero-start V-cycles run the finest level in
+    # red-black split layout) against the same with IBR_MG_SPLIT=0
+    outs = []
+    for split in ("1", "0"):
+        out = str(tmp_path / f"z_{split}.npy")
+        env = dict(os.environ)
+        env["IBR_MG_SPLIT"] = split
+        code = PS_CHILD.format(root=ROOT, n=n, prec=prec, out=out)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-3000:]
+        outs.append(np.load(out))
+    err = np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1])
+    print(n, prec, err)
+    assert err < (1e-13 if prec == "FP64" else 1e-6), err

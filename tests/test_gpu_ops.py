@@ -209,3 +209,35 @@ def test_smoother_tiles_are_tuned_candidates(abi):
     assert {t[3] for t in mine} == {1, 3}
     for t in mine:
         assert t[5] in (4, 8) and t[6] in (2, 4, 6, 8, 11, 16, 22, 32)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mtilde_couples_bodies_with_minimum_images(abi, dim):
+    # several bodies within the single-block limit: one block of all markers,
+    # Eq. M_tilde_ij for every pair with minimum-image displacements (one body
+    # straddles the periodic seam)
+    rng = np.random.default_rng(17)
+    if dim == 2:
+        n, h = (48, 48), 1.0 / 48
+        bodies = [Body(np.array([0.03, 0.5]), disk_markers(0.1, h), rng.standard_normal(3)),
+                  Body(np.array([0.55, 0.42]), disk_markers(0.12, h), rng.standard_normal(3))]
+    else:
+        n, h = (24, 24, 24), 1.0 / 24
+        bodies = [Body(np.array([0.97, 0.5, 0.45]), sphere_markers(0.15, 40), rng.standard_normal(6)),
+                  Body(np.array([0.45, 0.55, 0.6]), sphere_markers(0.12, 30), rng.standard_normal(6))]
+    wl = Workload("coupled", n, (1.0,) * dim, bodies=bodies)
+    pr = oracle_problem(wl)
+    G = gpu_grid(abi, wl, abi.FP64)
+    try:
+        abi.prepare(G)
+        m = pr.N * dim
+        out = torch.zeros(m * m, dtype=torch.float64, device="cuda")
+        abi.op_mtilde(G, 0, out)
+        aoh, coef = abi.mobility_defaults(dim)
+        if dim == 2:
+            ref = mobility.mtilde_2d_steady(pr.q, h, 1.0, 1.0, aoh, list(coef), box=(1.0, 1.0))
+        else:
+            ref = mobility.mtilde_3d_rpy(pr.q, h, 1.0, 1.0, aoh, periodic=True, box=(1.0, 1.0, 1.0))
+        assert rel_err(out.cpu().numpy(), ref) < TOL
+    finally:
+        abi.destroy_grid(G)
