@@ -60,9 +60,10 @@ def parse():
                     help="default run: skip the batch, serving and nozzle legs that follow the headline")
     ap.add_argument("--no-autotune", action="store_true", help="batch: fixed schedule")
     ap.add_argument("--autotune", action="store_true", help="serve: autotune the schedule per shape")
-    ap.add_argument("--mob", default="pair", choices=["auto", "pair"],
+    ap.add_argument("--mob", default="pair", choices=["auto", "auto-coupled", "pair"],
                     help="batch / serve: approximate mobility (pair: the grid's tabulated pair mobility; auto: the "
-                         "analytic forms)")
+                         "analytic forms, one block per body; auto-coupled: the analytic forms, one block of all "
+                         "markers)")
     ap.add_argument("--re", type=float, default=10.0, help="Reynolds number of the nozzle workload")
     ap.add_argument("--n-s", type=int, default=0, help="inner iterations N_s (0: the library's automatic choice)")
     ap.add_argument("--mg", default="2,2", help="pre,post multigrid sweeps per level")
@@ -529,9 +530,9 @@ def run_ours(args, world, rank, local):
                          "share_of_profiled_step": kms / prof_total},
     }
     if kname == "mg_smooth_rbgs":
-        roof["note"] = ("in the solve the finest level's u and f (50 MB) stay in L2 between half sweeps: ncu in situ "
-                        "measures ~1 MB of DRAM traffic per launch and 72 % issue activity, so the kernel is "
-                        "issue/latency-bound and this HBM fraction is a lower bound")
+        roof["note"] = ("finest-level half sweeps in red-black split layout (k_rb_first/k_rb_half, 3 stacked fields): "
+                        "in the solve the level's u and f (50 MB) stay in L2 between half sweeps, so ncu in situ "
+                        "measures almost no DRAM traffic per launch; the HBM copy rate is the denominator all the same")
     breakdown = {k: {"launches_per_step": v[0] / args.profile_steps, "ms_per_step": v[1] / args.profile_steps,
                      "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -570,6 +571,8 @@ def run_ours(args, world, rank, local):
         "tensor_roofline": tensor_roof,
         "smoother_tiles": [{"level": list(t[:3]), "fields": t[3], "bytes": t[4], "block": [32, t[5]], "kz": t[6]}
                            for t in abi.tuned_smoother_tiles()],
+        "vcycle_schedules": [{"finest": list(t[:3]), "levels": t[3], "fields": t[4], "bytes": t[5],
+                              "cluster_from_level": t[6]} for t in abi.tuned_vcycle_schedules()],
         "kernel_breakdown": breakdown,
         "clocks": clk,
         "err_vs_oracle": {"mixed": err_mixed, "fp64": err_fp64, "tol": TOL,
@@ -701,7 +704,7 @@ def _server_submit(S, r, precision, want_fields=False, opts=None):
 def _mob_opts(abi, mob, restart):
     o = abi.solve_opts_default()
     o.tol = TOL
-    o.mob_model = abi.MOB_PAIR if mob == "pair" else abi.MOB_AUTO
+    o.mob_model = {"pair": abi.MOB_PAIR, "auto": abi.MOB_AUTO, "auto-coupled": abi.MOB_AUTO | abi.MOB_COUPLED}[mob]
     if restart:
         o.restart = restart
     return o

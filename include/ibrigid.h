@@ -84,10 +84,17 @@ extern "C" {
 #define IBR_MOB_AUTO  0        /* RPY (3-D) / App. B steady form (2-D)            */
 #define IBR_MOB_RPY   1        /* Eq. RPYTensor (+ periodic correction, App. A)   */
 #define IBR_MOB_FIT2D 2        /* App. B Eq. fg_steady_2d                          */
-                               /* (analytic forms: with several bodies one dense
-                                  block of all markers, minimum-image distances
-                                  on periodic axes, while dim N <= 6144; else one
-                                  block per body, Sec. VIII)                     */
+                               /* (analytic forms: one dense block per body,
+                                  the block-diagonal form of Sec. IX, bodies
+                                  not coupled; see IBR_MOB_COUPLED)              */
+#define IBR_MOB_COUPLED 16     /* OR-ed with IBR_MOB_AUTO / RPY / FIT2D: one dense
+                                  block of all markers (M~_ij for every pair,
+                                  Sec. IV.B; minimum-image displacements on
+                                  periodic axes) while dim N <= 6144, else one
+                                  block per body.  The analytic far field is
+                                  not the periodic one: on crowded periodic 2-D
+                                  problems coupling raised FGMRES iterations
+                                  several-fold, hence off by default          */
 #define IBR_MOB_TRUE  3        /* the true mobility M0 = J L^-1 S of all markers,
                                   one dense block, built in the set-up from
                                   N*dim Stokes solves (Sec. V.C, VII.F: for

@@ -26,6 +26,7 @@ FP64, MIXED = 0, 1
 PRESCRIBED, FREE = 0, 1
 PC_LOWER, PC_FULL = 0, 1
 MOB_AUTO, MOB_RPY, MOB_FIT2D, MOB_TRUE, MOB_PAIR = 0, 1, 2, 3, 4
+MOB_COUPLED = 16  # OR-ed with MOB_AUTO / MOB_RPY / MOB_FIT2D: one block of all markers
 
 
 class SolveOpts(ctypes.Structure):

@@ -176,7 +176,7 @@ struct ibr_grid {
     std::vector<int> roff;
     long long* moff_dev = nullptr;
     int* roff_dev = nullptr;
-    int nblk = 0;              // dense mobility blocks (one per body, or one for all with IBR_MOB_TRUE)
+    int nblk = 0;              // dense mobility blocks (one per body, or one for all markers when coupled)
     double* Mbuild = nullptr;  // M~ (or M0) as built (FP64)
     double* Minv64 = nullptr;
     float* Minv32 = nullptr;
@@ -621,7 +621,7 @@ constexpr double COEF_2D_BKP6[9] = {0.31867428077511517, 0.029809829931491737, 0
 MobParams mob_params(const ibr_grid* G, const ibr_solve_opts& o) {
     MobParams p;
     std::memset(&p, 0, sizeof(p));
-    int model = o.mob_model;
+    int model = o.mob_model & ~IBR_MOB_COUPLED;
     if (model == IBR_MOB_AUTO) model = G->d == 3 ? IBR_MOB_RPY : IBR_MOB_FIT2D;
     require(model == IBR_MOB_RPY || model == IBR_MOB_FIT2D, "unknown mob_model");
     require(!(model == IBR_MOB_FIT2D && G->d != 2), "IBR_MOB_FIT2D is a 2-D model");
@@ -961,11 +961,12 @@ void prepare(ibr_grid* G, const ibr_solve_opts& o) {
     const bool true_mob = o.mob_model == IBR_MOB_TRUE;
     const bool pair_mob = o.mob_model == IBR_MOB_PAIR;
     require(!(pair_mob && G->walls()), "IBR_MOB_PAIR needs a periodic grid");
-    // the analytic forms and the pair table couple all bodies in one block
-    // (M~_ij for every marker pair, Sec. IV.B) while d N <= pair_full_max(),
-    // else one block per body (Sec. VIII's block-diagonal form)
-    const bool one_block = true_mob || (B > 1 && (long long)N * d <= pair_full_max()) ||
-                           (pair_mob && (long long)N * d <= pair_full_max());
+    // the pair table, and the analytic forms with IBR_MOB_COUPLED, couple all
+    // bodies in one block (M~_ij for every marker pair, Sec. IV.B) while
+    // d N <= pair_full_max(); otherwise one block per body (the block-diagonal
+    // form of Sec. IX, interactions between bodies left out)
+    const bool coupled = pair_mob || (o.mob_model & IBR_MOB_COUPLED);
+    const bool one_block = true_mob || (coupled && (long long)N * d <= pair_full_max());
     G->nblk = one_block ? 1 : B;
     const int nblk = G->nblk;
     G->moff.assign(nblk + 1, 0);
@@ -1507,8 +1508,8 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
              3 * pg(8.0 * nc);
         if (dN <= (double)pair_full_max()) blk2 = blkmax = dN * dN;
     }
-    // several bodies within the single-block limit: one block of all markers
-    if (B > 1 && dN <= (double)pair_full_max()) blk2 = blkmax = dN * dN;
+    // coupled analytic forms within the single-block limit: one block of all markers
+    if ((mob_model & IBR_MOB_COUPLED) && dN <= (double)pair_full_max()) blk2 = blkmax = dN * dN;
     // mobility: built (FP64) + factorised inverse (precision) + work: the FP64
     // path's work block, or the tensor-core path's two padded blocks
     t += pg(8.0 * blk2) + pg(e * blk2);

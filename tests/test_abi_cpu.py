@@ -149,10 +149,13 @@ def test_device_memory_estimate_is_consistent(abi):
     # dense mobility blocks: (3 N)^2 entries in FP64 (built) + FP32 (inverse, work)
     dm = e(2, (64, 64), [2000]) - e(2, (64, 64), [1000])
     assert dm > 0
-    # beyond the single-block limit (d N > 6144) bodies get a block each: one
-    # block of 2N costs more than two of N; within it they share one block
-    assert e(2, (64, 64), [4000]) - e(2, (64, 64), [2000, 2000]) > 0
-    assert e(2, (64, 64), [2000]) == e(2, (64, 64), [1000, 1000])
+    # the analytic forms give one block per body: one block of 2N costs more
+    # than two of N; coupled (one block of all markers while d N <= 6144)
+    # two bodies of N cost what one body of 2N does, beyond the limit a block each
+    assert e(2, (64, 64), [2000]) - e(2, (64, 64), [1000, 1000]) > 0
+    cpl = abi.MOB_AUTO | abi.MOB_COUPLED
+    assert e(2, (64, 64), [2000], mob_model=cpl) == e(2, (64, 64), [1000, 1000], mob_model=cpl)
+    assert e(2, (64, 64), [4000], mob_model=cpl) - e(2, (64, 64), [2000, 2000], mob_model=cpl) > 0
     with pytest.raises(abi.IbrError):
         e(4, (8, 8), [1])
 

@@ -213,7 +213,7 @@ def test_smoother_tiles_are_tuned_candidates(abi):
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_mtilde_couples_bodies_with_minimum_images(abi, dim):
-    # several bodies within the single-block limit: one block of all markers,
+    # several bodies within the single-block limit, coupling requested: one block of all markers,
     # Eq. M_tilde_ij for every pair with minimum-image displacements (one body
     # straddles the periodic seam)
     rng = np.random.default_rng(17)
@@ -229,7 +229,9 @@ def test_mtilde_couples_bodies_with_minimum_images(abi, dim):
     pr = oracle_problem(wl)
     G = gpu_grid(abi, wl, abi.FP64)
     try:
-        abi.prepare(G)
+        o = abi.solve_opts_default()
+        o.mob_model = abi.MOB_AUTO | abi.MOB_COUPLED
+        abi.prepare(G, o)
         m = pr.N * dim
         out = torch.zeros(m * m, dtype=torch.float64, device="cuda")
         abi.op_mtilde(G, 0, out)
