@@ -550,6 +550,9 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "tol": TOL, "precision": "mixed", "restart": SCHEDULE["restart"],
                    "n_s": SCHEDULE["n_s"] or 2, "mg_sweeps": [SCHEDULE["mg_pre"], SCHEDULE["mg_post"]],
                    "preconditioner": "lower-triangular Schur", "setup_in_step": True,
+                   "arnoldi": {"cgs2": "CGS2 over the FP64 basis (pipelined)",
+                               "df": "CGS2 over a double-float basis (pipelined)"}.get(
+                                   os.environ.get("IBR_ARNOLDI", ""), "modified Gram-Schmidt over the FP64 basis"),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (FP64 system vector 67 MB, Krylov basis > 1 GB)"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),

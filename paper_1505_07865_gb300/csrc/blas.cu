@@ -499,202 +499,520 @@ __device__ __forceinline__ dflt df_zero() {
     return r;
 }
 
-// The basis kernels below work on pairs of entries (one 16-byte load each):
-// n2 = number of pairs, ld2 = leading dimension in pairs (the basis is
-// allocated with an even length, its pad entry zero).  Loads of the next
-// pair are issued before the arithmetic on the current one, and sums over
-// basis vectors use independent partial accumulators, so that enough bytes
-// are in flight per SM to stream at HBM speed.
-__device__ __forceinline__ void ld_pair(const dflt* __restrict__ p, long long q, dflt& a, dflt& b) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p) + q);
-    a.hi = v.x;
-    a.lo = v.y;
-    b.hi = v.z;
-    b.lo = v.w;
+
+// ---- the Gram-Schmidt passes of the double-float basis, pipelined --------
+// One block walks tiles of PG_TP = 256 entry pairs of the system vector.  Its
+// producer warp moves the tile's rows (the w row and, per stage, up to PG_CV
+// basis rows of 4 KB each) into shared memory with bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on the stage's "full"
+// mbarrier), PG_NST stages ahead of the eight consumer warps, which release a
+// stage on its "empty" mbarrier.  Three passes share the pipeline:
+//   PG_CONVERT: w (FP64 on entry) is rewritten in place as double-float; the
+//               dots V_j . w (j < k) and |w|^2;
+//   PG_SUB:     w <- w - V h1 (first sweep over the tile's basis rows), then the
+//               dots of the new w (second sweep; the rows come again from the
+//               L2); skipped when st[1] == 0 (no second Gram-Schmidt pass);
+//   PG_NORM:    V_k = (w - V hsel) / sqrt(st[2]), hsel = st[1] ? h2 : h1, with
+//               its FP32 (out32, i < n32) and FP64 (out64, from64 <= i < n64)
+//               copies.
+// Subtraction: consumer thread t owns pair t of the tile and sums h_j V_j in
+// double-float over the basis rows.  Dots: warp g takes row g of each stage
+// (basis vectors j = g mod 8), lane l the pairs l + 32 u; each dot is a
+// compensated pair (s, c): the product of two double-float entries exact up to
+// the lo * lo term (FMA two-product), its high part added to s by Knuth's
+// two-sum, every error term to c.  The w tile the dots read is double-
+// buffered by tile parity, so one named barrier per tile suffices.  A wait
+// that times out sets *err and the block stops.
+constexpr int PG_TP = 256;                           // pairs per tile
+constexpr int PG_ROW = PG_TP * 16;                   // bytes per row of a tile (4 KB)
+constexpr int PG_CV = 8;                             // basis rows per stage
+constexpr int PG_NST = 2;                            // stages
+constexpr int PG_STAGE = (PG_CV + 1) * PG_ROW;       // w row + PG_CV basis rows
+constexpr int PG_CONS = 256;                         // consumer threads (one per pair)
+constexpr int PG_THREADS = PG_CONS + 32;             // + the producer warp
+constexpr int PG_MAXCH = 16;                         // stages per tile sweep: k <= 128
+constexpr int PG_BLOCKS = 2 * 152;                   // two resident blocks per SM
+constexpr int PG_SMEM = PG_NST * PG_STAGE            // stages
+                        + 3 * PG_ROW                 // w as loaded, w as used (two tiles)
+                        + 8 * 16 * 8 + 8 * 8         // per-warp dots, norm
+                        + 128 * 8                    // coefficients (double-float)
+                        + 2 * PG_NST * 8 + 24;       // mbarriers, issued count, flags
+enum { PG_CONVERT = 0, PG_SUB = 1, PG_NORM = 2 };
+
+// (s, c) += v . w over the two entries of a pair (v, w: hi, lo, hi, lo)
+__device__ __forceinline__ void dv_acc(const float4 v, const float4 w, float& s, float& c) {
+    float p = __fmul_rn(v.x, w.x);
+    float e = __fmaf_rn(v.x, w.x, -p);
+    e = __fmaf_rn(v.x, w.y, e);
+    e = __fmaf_rn(v.y, w.x, e);
+    float t, r;
+    two_sum(s, p, t, r);
+    c = __fadd_rn(c, __fadd_rn(r, e));
+    p = __fmul_rn(v.z, w.z);
+    e = __fmaf_rn(v.z, w.z, -p);
+    e = __fmaf_rn(v.z, w.w, e);
+    e = __fmaf_rn(v.w, w.z, e);
+    two_sum(t, p, s, r);
+    c = __fadd_rn(c, __fadd_rn(r, e));
 }
-__device__ __forceinline__ void ld_pair_rw(const dflt* p, long long q, dflt& a, dflt& b) {
-    const float4 v = reinterpret_cast<const float4*>(p)[q];
-    a.hi = v.x;
-    a.lo = v.y;
-    b.hi = v.z;
-    b.lo = v.w;
+// (s, c) += h x for double-float h and x (the same product and compensation)
+__device__ __forceinline__ void dv_axpy(const dflt h, float xh, float xl, float& s, float& c) {
+    const float p = __fmul_rn(h.hi, xh);
+    float e = __fmaf_rn(h.hi, xh, -p);
+    e = __fmaf_rn(h.hi, xl, e);
+    e = __fmaf_rn(h.lo, xh, e);
+    float t, r;
+    two_sum(s, p, t, r);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(r, e));
 }
-__device__ __forceinline__ void st_pair(dflt* p, long long q, dflt a, dflt b) {
-    reinterpret_cast<float4*>(p)[q] = make_float4(a.hi, a.lo, b.hi, b.lo);
+// the double-float value of s + c
+__device__ __forceinline__ dflt dv_value(float s, float c) {
+    float t, r;
+    two_sum(s, c, t, r);
+    dflt v;
+    v.hi = t;
+    v.lo = r;
+    return v;
 }
-__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
-    float s, e;
-    two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    return quick_two_sum(s, e);
+// (s, c) += (s2, c2)
+__device__ __forceinline__ void dv_merge(float& s, float& c, float s2, float c2) {
+    float t, r;
+    two_sum(s, s2, t, r);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(r, c2));
 }
 
-// w (FP64, n entries) -> double-float in place (same 8 bytes per entry): the
-// one pass per Arnoldi step that uses the FP64 pipe
-__global__ void k_to_df(long long n, double* w) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const dflt v = df_from(w[i]);
-        reinterpret_cast<dflt*>(w)[i] = v;
-    }
-}
+__device__ __forceinline__ float4 f4(dflt a, dflt b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
+__device__ __forceinline__ dflt f4a(float4 v) { dflt r; r.hi = v.x; r.lo = v.y; return r; }
+__device__ __forceinline__ dflt f4b(float4 v) { dflt r; r.hi = v.z; r.lo = v.w; return r; }
 
-// partial[blk*(k+1) + j] = V_j . w (j < k) and w . w (j == k)
-__global__ void __launch_bounds__(RED_THREADS) k_df_mdot_norm(long long n2, const dflt* __restrict__ V, long long ld2,
-                                                              int k, const dflt* __restrict__ w,
-                                                              double* __restrict__ partial,
-                                                              const double* __restrict__ st) {
-    if (st && st[1] == 0.0) return;
-    const int K1 = k + 1;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (int j0 = 0; j0 < K1; j0 += MDOT_CHUNK) {
-        const int nv = min(MDOT_CHUNK, k - j0);  // basis vectors in this chunk (may be <= 0)
-        const bool with_norm = j0 + MDOT_CHUNK >= K1;
-        dflt acc[MDOT_CHUNK];
-#pragma unroll
-        for (int q = 0; q < MDOT_CHUNK; ++q) acc[q] = df_zero();
-        dflt cv[MDOT_CHUNK][2], cw[2];
-        long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-        if (p < n2) {
-            ld_pair(w, p, cw[0], cw[1]);
-#pragma unroll
-            for (int q = 0; q < MDOT_CHUNK; ++q)
-                if (q < nv) ld_pair(V, (long long)(j0 + q) * ld2 + p, cv[q][0], cv[q][1]);
+// DF: the basis is double-float (float pairs, arithmetic on the FP32 pipe);
+// otherwise FP64 (the same 16-byte pairs, FP64 arithmetic; PG_CONVERT then
+// only reads w).
+template <int MODE, bool DF>
+__global__ void __launch_bounds__(PG_THREADS, 2)
+    k_gs_pipe(long long n2, const void* __restrict__ V, long long ld2, int k, void* wv, const double* __restrict__ h1,
+              const double* __restrict__ h2, const double* __restrict__ st, double* __restrict__ partial,
+              void* __restrict__ vout, float* __restrict__ out32, long long n32, double* __restrict__ out64,
+              long long from64, long long n64, int* __restrict__ err) {
+    if (MODE == PG_SUB && st[1] == 0.0) return;
+    extern __shared__ __align__(128) uint8_t smem[];
+    float4* win = reinterpret_cast<float4*>(smem + PG_NST * PG_STAGE);  // w row as loaded
+    float4* wuse = win + PG_TP;                                          // [2][PG_TP] w rows the dots use
+    double* wred = reinterpret_cast<double*>(wuse + 2 * PG_TP);          // [8][16] per-warp dots
+    double* nred = wred + 8 * 16;                                        // [8] norm
+    dflt* hs = reinterpret_cast<dflt*>(nred + 8);                        // [128] coefficients (DF)
+    double* hd = reinterpret_cast<double*>(hs);                          // [128] coefficients (FP64)
+    uint64_t* full = reinterpret_cast<uint64_t*>(hs + 128);
+    uint64_t* empty = full + PG_NST;
+    long long* issued = reinterpret_cast<long long*>(empty + PG_NST);
+    int* fail = reinterpret_cast<int*>(issued + 1);
+    int* pdone = fail + 1;
+    int* pfail = pdone + 1;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nch = (k + PG_CV - 1) / PG_CV;
+    const long long ntile = (n2 + PG_TP - 1) / PG_TP;
+    if (t == 0) {
+        *fail = 0;
+        *pdone = 0;
+        *pfail = 0;
+        *issued = 0;
+        for (int q = 0; q < PG_NST; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&empty[q])));
         }
-        while (p < n2) {
-            const long long pn = p + stride;
-            dflt nv2[MDOT_CHUNK][2], nw[2];
-            if (pn < n2) {
-                ld_pair(w, pn, nw[0], nw[1]);
-#pragma unroll
-                for (int q = 0; q < MDOT_CHUNK; ++q)
-                    if (q < nv) ld_pair(V, (long long)(j0 + q) * ld2 + pn, nv2[q][0], nv2[q][1]);
-            }
-#pragma unroll
-            for (int q = 0; q < MDOT_CHUNK; ++q) {
-                if (q < nv) {
-                    acc[q] = df_fma(cv[q][0], cw[0], acc[q]);
-                    acc[q] = df_fma(cv[q][1], cw[1], acc[q]);
-                } else if (q == nv && with_norm) {
-                    acc[q] = df_fma(cw[0], cw[0], acc[q]);
-                    acc[q] = df_fma(cw[1], cw[1], acc[q]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (MODE != PG_CONVERT) {
+        const double* h = (MODE == PG_NORM && st[1] != 0.0) ? h2 : h1;
+        for (int j = t; j < k; j += blockDim.x) {
+            if (DF)
+                hs[j] = df_from(h[j]);
+            else
+                hd[j] = h[j];
+        }
+    }
+    __syncthreads();
+    const uint32_t sbase = smem_u32(smem);
+    if (warp == 8) {
+        // producer: one lane issues every copy, in the consumers' order, and
+        // leaves the number of items it issued in *issued when it stops
+        if (lane == 0) {
+            long long it = 0;
+            const int sweeps = MODE == PG_SUB ? 2 : 1;
+            bool stop = false;
+            for (long long tile = blockIdx.x; tile < ntile && !stop; tile += gridDim.x) {
+                const long long p0 = tile * PG_TP;
+                const uint32_t rb = (uint32_t)(min((long long)PG_TP, n2 - p0) * 16);
+                for (int sw = 0; sw < sweeps && !stop; ++sw) {
+                    for (int c = 0; c < nch; ++c, ++it) {
+                        const int q = (int)(it % PG_NST);
+                        if (it >= PG_NST && !mbar_wait(smem_u32(&empty[q]), (uint32_t)((it / PG_NST - 1) & 1))) {
+                            // only the consumers write *fail; they learn of this
+                            // by their own bounded waits
+                            *(volatile int*)pfail = 1;
+                            stop = true;
+                            break;
+                        }
+                        if (*(volatile int*)fail) {
+                            stop = true;
+                            break;
+                        }
+                        const bool with_w = sw == 0 && c == 0;
+                        const int nv = min(PG_CV, k - c * PG_CV);
+                        const uint32_t fb = smem_u32(&full[q]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                     "r"((with_w ? rb : 0u) + (uint32_t)nv * rb)
+                                     : "memory");
+                        const uint32_t sq = sbase + q * PG_STAGE;
+                        if (with_w) bulk_g2s(sq, reinterpret_cast<const float4*>(wv) + p0, rb, fb);
+                        for (int v = 0; v < nv; ++v)
+                            bulk_g2s(sq + (v + 1) * PG_ROW,
+                                     reinterpret_cast<const float4*>(V) + (long long)(c * PG_CV + v) * ld2 + p0, rb,
+                                     fb);
+                    }
                 }
             }
-            if (pn < n2) {
-                cw[0] = nw[0];
-                cw[1] = nw[1];
+            *(volatile long long*)issued = it;
+            __threadfence_block();
+            *(volatile int*)pdone = 1;
+        }
+        return;
+    }
+    // consumers (256 threads; named barrier 1 keeps the producer out).  Every
+    // consumer thread walks every tile of the block and passes the same named
+    // barriers whatever its own waits gave; after a failed wait it waits no
+    // more and does no more work.
+    // dot accumulators: DF (s, c) float pairs, FP64 in as64
+    float as[DF ? PG_MAXCH : 1], ac[DF ? PG_MAXCH : 1];
+    double as64[DF ? 1 : PG_MAXCH];
 #pragma unroll
-                for (int q = 0; q < MDOT_CHUNK; ++q) {
-                    cv[q][0] = nv2[q][0];
-                    cv[q][1] = nv2[q][1];
+    for (int q = 0; q < (DF ? PG_MAXCH : 1); ++q) as[q] = ac[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < (DF ? 1 : PG_MAXCH); ++q) as64[q] = 0.0;
+    float ns = 0.f, nc = 0.f;
+    double nn64 = 0.0;
+    dflt inv = df_zero();
+    double inv64 = 0.0;
+    if (MODE == PG_NORM) {
+        // 1 / sqrt(st[2]) from the one-thread state kernel
+        if (DF)
+            inv = df_from(st[3]);
+        else
+            inv64 = st[3];
+    }
+    long long it = 0;
+    bool ok = true;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int par = 0;
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x, par ^= 1) {
+        const long long p0 = tile * PG_TP;
+        const int np = (int)min((long long)PG_TP, n2 - p0);
+        float4* wu = wuse + par * PG_TP;
+        if (MODE != PG_CONVERT) {
+            // sweep 1: s = V h at pair t (DF: compensated sums), then w - s
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+            double d0 = 0.0, d1 = 0.0;
+            for (int c = 0; c < nch; ++c, ++it) {
+                const int q = (int)(it % PG_NST);
+                if (ok && !mbar_wait(smem_u32(&full[q]), (uint32_t)((it / PG_NST) & 1))) {
+                    ok = false;
+                    atomicExch(fail, 1);
+                }
+                if (!ok) continue;
+                const float4* sg = reinterpret_cast<const float4*>(smem + q * PG_STAGE);
+                if (c == 0) win[t] = t < np ? sg[t] : z4;
+                if (t < np) {
+#pragma unroll
+                    for (int v = 0; v < PG_CV; ++v) {
+                        const int j = c * PG_CV + v;
+                        if (j < k) {
+                            if constexpr (DF) {
+                                const float4 x = sg[(v + 1) * PG_TP + t];
+                                const dflt hj = hs[j];
+                                dv_axpy(hj, x.x, x.y, s0, c0);
+                                dv_axpy(hj, x.z, x.w, s1, c1);
+                            } else {
+                                const double2 x = reinterpret_cast<const double2*>(sg)[(v + 1) * PG_TP + t];
+                                const double hj = hd[j];
+                                d0 = fma(hj, x.x, d0);
+                                d1 = fma(hj, x.y, d1);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[q])) : "memory");
+            }
+            if (ok) {
+                const long long p = p0 + t;
+                float4 y = z4;  // w - s (SUB), the new basis entries (NORM)
+                float2 y32 = make_float2(0.f, 0.f);
+                double y64[2] = {0.0, 0.0};
+                if constexpr (DF) {
+                    const float4 x = win[t];
+                    dflt r0 = df_sub(f4a(x), dv_value(s0, c0)), r1 = df_sub(f4b(x), dv_value(s1, c1));
+                    if (MODE == PG_NORM) {
+                        r0 = df_fma(r0, inv, df_zero());
+                        r1 = df_fma(r1, inv, df_zero());
+                        y32 = make_float2(r0.hi, r1.hi);
+                        y64[0] = df_to(r0);
+                        y64[1] = df_to(r1);
+                    }
+                    y = f4(r0, r1);
+                } else {
+                    const double2 x = reinterpret_cast<const double2*>(win)[t];
+                    double r0 = x.x - d0, r1 = x.y - d1;
+                    if (MODE == PG_NORM) {
+                        r0 *= inv64;
+                        r1 *= inv64;
+                        y32 = make_float2((float)r0, (float)r1);
+                        y64[0] = r0;
+                        y64[1] = r1;
+                    }
+                    const double2 yd = make_double2(r0, r1);
+                    y = *reinterpret_cast<const float4*>(&yd);
+                }
+                if (t >= np) y = z4;
+                if (MODE == PG_SUB) {
+                    wu[t] = y;
+                    if (t < np) reinterpret_cast<float4*>(wv)[p] = y;
+                } else if (t < np) {
+                    reinterpret_cast<float4*>(vout)[p] = y;
+                    const long long i = 2 * p;
+                    if (out32) {
+                        if (i + 1 < n32)
+                            *reinterpret_cast<float2*>(out32 + i) = y32;
+                        else if (i < n32)
+                            out32[i] = y32.x;
+                    }
+                    if (out64) {
+                        if (i >= from64 && i < n64) out64[i] = y64[0];
+                        if (i + 1 >= from64 && i + 1 < n64) out64[i + 1] = y64[1];
+                    }
                 }
             }
-            p = pn;
+            if (MODE == PG_SUB) asm volatile("bar.sync 1, %0;" ::"n"(PG_CONS) : "memory");
         }
-        double out[MDOT_CHUNK];
+        if constexpr (MODE != PG_NORM) {
+            // the dot sweep
 #pragma unroll
-        for (int q = 0; q < MDOT_CHUNK; ++q) out[q] = df_to(acc[q]);
-        __shared__ double outv[MDOT_CHUNK];
-        block_sum<MDOT_CHUNK>(out, outv);
-        const int nq = min(MDOT_CHUNK, K1 - j0);
-        if (threadIdx.x < nq) partial[(long long)blockIdx.x * K1 + j0 + threadIdx.x] = outv[threadIdx.x];
-        __syncthreads();
+            for (int c = 0; c < PG_MAXCH; ++c) {
+                if (c >= nch) break;
+                const int q = (int)(it % PG_NST);
+                const bool got = ok && mbar_wait(smem_u32(&full[q]), (uint32_t)((it / PG_NST) & 1));
+                if (ok && !got) {
+                    ok = false;
+                    atomicExch(fail, 1);
+                }
+                ++it;
+                const float4* sg = reinterpret_cast<const float4*>(smem + q * PG_STAGE);
+                if (MODE == PG_CONVERT && c == 0) {
+                    if (got) {
+                        float4 y = z4;
+                        if (t < np) {
+                            if constexpr (DF) {
+                                const double2 x = reinterpret_cast<const double2*>(sg)[t];
+                                y = f4(df_from(x.x), df_from(x.y));
+                                reinterpret_cast<float4*>(wv)[p0 + t] = y;
+                            } else {
+                                y = sg[t];
+                            }
+                        }
+                        wu[t] = y;
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(PG_CONS) : "memory");
+                }
+                if (!got) continue;
+                if (c == 0) {
+                    if constexpr (DF) {
+                        const float4 y = wu[t];
+                        dv_acc(y, y, ns, nc);
+                    } else {
+                        const double2 y = reinterpret_cast<const double2*>(wu)[t];
+                        nn64 = fma(y.x, y.x, fma(y.y, y.y, nn64));
+                    }
+                }
+                const int j = c * PG_CV + warp;
+                if (j < k) {
+                    const float4* row = sg + (warp + 1) * PG_TP;
+                    if constexpr (DF) {
+                        float s2[2] = {0.f, 0.f}, c2[2] = {0.f, 0.f};
+#pragma unroll
+                        for (int u = 0; u < PG_TP / 32; ++u) {
+                            const int pp = lane + 32 * u;
+                            if (pp < np) dv_acc(row[pp], wu[pp], s2[u & 1], c2[u & 1]);
+                        }
+                        dv_merge(s2[0], c2[0], s2[1], c2[1]);
+                        dv_merge(as[c], ac[c], s2[0], c2[0]);
+                    } else {
+                        const double2* r2 = reinterpret_cast<const double2*>(row);
+                        const double2* w2 = reinterpret_cast<const double2*>(wu);
+                        double e[2] = {0.0, 0.0};
+#pragma unroll
+                        for (int u = 0; u < PG_TP / 32; ++u) {
+                            const int pp = lane + 32 * u;
+                            if (pp < np) {
+                                const double2 x = r2[pp], y = w2[pp];
+                                e[u & 1] = fma(x.x, y.x, fma(x.y, y.y, e[u & 1]));
+                            }
+                        }
+                        as64[c] += e[0] + e[1];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[q])) : "memory");
+            }
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(PG_CONS) : "memory");
+    if (t == 0 && *(volatile int*)pfail) atomicExch(err, 1);
+    if (t == 0 && *(volatile int*)fail) {
+        // after a time-out: let the producer stop, then wait (bounded) for the
+        // copies still in flight into this block's stages before it exits
+        atomicExch(err, 1);
+        const unsigned long long t0 = global_ns();
+        while (!*(volatile int*)pdone && global_ns() - t0 < MBAR_WAIT_LIMIT_NS) {
+        }
+        const long long ni = *(volatile long long*)issued;
+        for (long long x = ni > PG_NST ? ni - PG_NST : 0; x < ni; ++x)
+            mbar_wait(smem_u32(&full[x % PG_NST]), (uint32_t)((x / PG_NST) & 1));
+    }
+    if constexpr (MODE != PG_NORM) {
+        // per-warp dots and the norm in FP64, fixed order
+#pragma unroll
+        for (int c = 0; c < PG_MAXCH; ++c) {
+            if (c >= nch) break;
+            double x;
+            if constexpr (DF)
+                x = (double)as[c] + (double)ac[c];
+            else
+                x = as64[c];
+            x = warp_sum(x);
+            if (lane == 0) wred[warp * 16 + c] = x;
+        }
+        const double x = warp_sum(DF ? (double)ns + (double)nc : nn64);
+        if (lane == 0) nred[warp] = x;
+        asm volatile("bar.sync 1, %0;" ::"n"(PG_CONS) : "memory");
+        const int S = k + 1;
+        if (t < S) {
+            double y = 0.0;
+            if (t < k) {
+                y = wred[(t % 8) * 16 + t / 8];
+            } else {
+                for (int g = 0; g < 8; ++g) y += nred[g];
+            }
+            partial[(long long)blockIdx.x * S + t] = y;
+        }
     }
 }
 
-// s = sum_{j<k} hs_j V_j at pair q: 8 vectors per trip, loads issued together,
-// four independent partial sums
-__device__ __forceinline__ void df_combo_pair(const dflt* __restrict__ V, long long ld2, int k, const dflt* hs,
-                                              long long q, dflt& s0, dflt& s1) {
-    dflt a[4][2];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) a[t][0] = a[t][1] = df_zero();
-    int j = 0;
-    for (; j + 8 <= k; j += 8) {
-        dflt v[8][2];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) ld_pair(V, (long long)(j + u) * ld2 + q, v[u][0], v[u][1]);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            a[u & 3][0] = df_fma(hs[j + u], v[u][0], a[u & 3][0]);
-            a[u & 3][1] = df_fma(hs[j + u], v[u][1], a[u & 3][1]);
-        }
-    }
-    for (; j < k; ++j) {
-        dflt v0, v1;
-        ld_pair(V, (long long)j * ld2 + q, v0, v1);
-        a[0][0] = df_fma(hs[j], v0, a[0][0]);
-        a[0][1] = df_fma(hs[j], v1, a[0][1]);
-    }
-    s0 = df_add(df_add(a[0][0], a[1][0]), df_add(a[2][0], a[3][0]));
-    s1 = df_add(df_add(a[0][1], a[1][1]), df_add(a[2][1], a[3][1]));
-}
-
-// second Gram-Schmidt pass (only when st[1] != 0): w <- w - V h
-__global__ void __launch_bounds__(RED_THREADS) k_df_sub(long long n2, const dflt* __restrict__ V, long long ld2, int k,
-                                                        const double* __restrict__ h, dflt* __restrict__ w,
-                                                        const double* __restrict__ st) {
-    if (st[1] == 0.0) return;
-    __shared__ dflt hs[128];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = df_from(h[j]);
-    __syncthreads();
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
-         p += (long long)gridDim.x * blockDim.x) {
-        dflt s0, s1, w0, w1;
-        ld_pair_rw(w, p, w0, w1);
-        df_combo_pair(V, ld2, k, hs, p, s0, s1);
-        st_pair(w, p, df_sub(w0, s0), df_sub(w1, s1));
-    }
-}
-
-// V_k = (w - V hsel) / sqrt(st[2]) (hsel = st[1] ? h2 : h1); out32[i] (i <
-// n32) its float value, out64[i] (from64 <= i < n64) its FP64 value
-__global__ void __launch_bounds__(RED_THREADS) k_df_normalize(long long n2, const dflt* __restrict__ V, long long ld2,
-                                                              int k, const double* __restrict__ h1,
-                                                              const double* __restrict__ h2,
-                                                              const double* __restrict__ st,
-                                                              const dflt* __restrict__ w, dflt* __restrict__ vout,
-                                                              float* __restrict__ out32, long long n32,
-                                                              double* __restrict__ out64, long long from64,
-                                                              long long n64) {
-    __shared__ dflt hs[128];
-    const double* h = st[1] != 0.0 ? h2 : h1;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = df_from(h[j]);
-    __syncthreads();
-    const double nu = sqrt(st[2]);
-    const dflt inv = df_from(nu > 0.0 ? 1.0 / nu : 0.0);
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
-         p += (long long)gridDim.x * blockDim.x) {
-        dflt s0, s1, w0, w1;
-        ld_pair(w, p, w0, w1);
-        df_combo_pair(V, ld2, k, hs, p, s0, s1);
-        const dflt v0 = df_fma(df_sub(w0, s0), inv, df_zero());
-        const dflt v1 = df_fma(df_sub(w1, s1), inv, df_zero());
-        st_pair(vout, p, v0, v1);
-        const long long i = 2 * p;
-        if (out32) {
-            if (i < n32) out32[i] = v0.hi;
-            if (i + 1 < n32) out32[i + 1] = v1.hi;
-        }
-        if (out64) {
-            if (i >= from64 && i < n64) out64[i] = df_to(v0);
-            if (i + 1 >= from64 && i + 1 < n64) out64[i + 1] = df_to(v1);
-        }
-    }
-}
-
-// V_0 = x / sqrt(*nrm2) in double-float (n entries, even), with the same copies
-__global__ void k_df_scale(long long n, const double* __restrict__ nrm2, const double* __restrict__ x,
+// V_0 = x * (*inv_norm) in double-float (n entries, even), with the same copies
+__global__ void k_df_scale(long long n, const double* __restrict__ inv_norm, const double* __restrict__ x,
                            dflt* __restrict__ vout, float* __restrict__ out32, long long n32,
                            double* __restrict__ out64, long long from64, long long n64) {
-    const double nr = sqrt(fmax(*nrm2, 0.0));
-    const dflt a = df_from(nr > 0.0 ? 1.0 / nr : 0.0);
+    const dflt a = df_from(*inv_norm);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const dflt v = df_fma(df_from(x[i]), a, df_zero());
         vout[i] = v;
         if (out32 && i < n32) out32[i] = v.hi;
         if (out64 && i >= from64 && i < n64) out64[i] = df_to(v);
+    }
+}
+
+// ---- modified Gram-Schmidt over the FP64 basis: one pass per basis vector ---
+// Step i of MGS subtracts the projection on V_i from w and, in the same pass
+// over the entries, forms the dot of the updated w with V_{i+1} (or, after
+// the last vector, |w|^2): two FP64 FMAs per entry.  The pass for V_0 only
+// forms V_0 . w, the last pass scales w into V_K.  A pass leaves one partial
+// sum per block; the next pass reduces them itself, in every block and in a
+// fixed order (bitwise the same value everywhere, no separate reduction
+// kernel), and block 0 records the coefficient.
+constexpr int MG_BLOCKS = RED_BLOCKS;  // 4 x 152
+
+// the sum of the previous pass' partials (fixed order), broadcast to the block
+__device__ __forceinline__ double mgs_prev(const double* __restrict__ pin, int nblk, double* sh) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) x += pin[b];
+    double v[1] = {x};
+    block_sum<1>(v, sh);
+    return sh[0];
+}
+
+// mode 0: pout = V_0 . w.  mode 1: h = sum(pin), hcol[i] = h (block 0),
+// w -= h V_i, pout = V_{i+1} . w (i + 1 < K) or w . w (i + 1 == K).
+// n2: entry pairs (n even, a zero pad entry), V_i: rows of ld doubles.
+__global__ void __launch_bounds__(RED_THREADS) k_mgs_step(long long n2, const double* __restrict__ Vi,
+                                                          const double* __restrict__ Vn, double* __restrict__ w,
+                                                          const double* __restrict__ pin, double* __restrict__ pout,
+                                                          double* __restrict__ hcol, int mode) {
+    pdl_start();
+    __shared__ double sh[1];
+    double h = 0.0;
+    if (mode == 1) {
+        h = mgs_prev(pin, gridDim.x, sh);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *hcol = h;
+    }
+    const double2* v2 = reinterpret_cast<const double2*>(Vi);
+    const double2* n2p = reinterpret_cast<const double2*>(Vn);  // NULL: the norm of w
+    double2* w2 = reinterpret_cast<double2*>(w);
+    double a0 = 0.0, a1 = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
+         p += (long long)gridDim.x * blockDim.x) {
+        double2 x = w2[p];
+        if (mode == 1) {
+            const double2 v = __ldcs(v2 + p);  // last use of V_i in this step
+            x.x = fma(-h, v.x, x.x);
+            x.y = fma(-h, v.y, x.y);
+            w2[p] = x;
+        }
+        const double2 u = mode == 0 ? __ldg(v2 + p) : (n2p ? __ldg(n2p + p) : x);
+        a0 = fma(u.x, x.x, a0);
+        a1 = fma(u.y, x.y, a1);
+    }
+    double v[1] = {a0 + a1};
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = sh[0];
+}
+
+// nu^2 = sum(pin) = |w|^2; st[2] = nu^2, st[3] = 1 / nu (block 0);
+// V_K = w / nu, out32 (first n32 entries, float) its FP32 copy
+__global__ void __launch_bounds__(RED_THREADS) k_mgs_norm(long long n2, const double* __restrict__ w,
+                                                          const double* __restrict__ pin, double* __restrict__ st,
+                                                          double* __restrict__ vout, float* __restrict__ out32,
+                                                          long long n32) {
+    pdl_start();
+    __shared__ double sh[1];
+    __shared__ double inv_s;
+    const double nu2 = mgs_prev(pin, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        const double nu = sqrt(fmax(nu2, 0.0));
+        inv_s = nu > 0.0 ? 1.0 / nu : 0.0;
+        if (blockIdx.x == 0) {
+            st[0] = nu2;
+            st[1] = 0.0;
+            st[2] = fmax(nu2, 0.0);
+            st[3] = inv_s;
+        }
+    }
+    __syncthreads();
+    const double inv = inv_s;
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    double2* v2 = reinterpret_cast<double2*>(vout);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
+         p += (long long)gridDim.x * blockDim.x) {
+        const double2 x = w2[p];
+        const double2 y = make_double2(x.x * inv, x.y * inv);
+        v2[p] = y;
+        if (out32) {
+            const long long i = 2 * p;
+            if (i + 1 < n32)
+                *reinterpret_cast<float2*>(out32 + i) = make_float2((float)y.x, (float)y.y);
+            else if (i < n32)
+                out32[i] = (float)y.x;
+        }
     }
 }
 
@@ -757,23 +1075,35 @@ void scale_rsqrt(long long n, const double* inv_norm, const T* x, T* y, T2* out2
 }
 
 
-void cgs_orthonormalize_df(long long n, long long n_real, const dflt* V, long long ld, int k, double* w, dflt* vout,
-                           float* out32, long long n32, double* out64, long long from64, double* partial, double* h1,
-                           double* h2, double* hk2, double* st, cudaStream_t s) {
+void cgs_orthonormalize_pipe(bool df, long long n, long long n_real, const void* V, long long ld, int k, double* w,
+                             void* vout, float* out32, long long n32, double* out64, long long from64,
+                             double* partial, double* h1, double* h2, double* hk2, double* st, int* err,
+                             cudaStream_t s) {
     if ((n & 1) || (ld & 1) || n_real > n)
-        throw Error{IBR_EINVAL, "double-float basis: length and leading dimension must be even"};
-    dflt* wd = reinterpret_cast<dflt*>(w);
+        throw Error{IBR_EINVAL, "pipelined Gram-Schmidt: length and leading dimension must be even"};
+    if (k < 1 || k > PG_CV * PG_MAXCH) throw Error{IBR_EINVAL, "pipelined Gram-Schmidt: 1 <= k <= 128 required"};
+    if ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(vout)) & 15)
+        throw Error{IBR_EINVAL, "pipelined Gram-Schmidt: V, w and vout must be 16-byte aligned"};
+    static PerDeviceOnce once;
+    once.run([] {
+        const void* f[6] = {(const void*)k_gs_pipe<PG_CONVERT, true>, (const void*)k_gs_pipe<PG_SUB, true>,
+                            (const void*)k_gs_pipe<PG_NORM, true>,    (const void*)k_gs_pipe<PG_CONVERT, false>,
+                            (const void*)k_gs_pipe<PG_SUB, false>,    (const void*)k_gs_pipe<PG_NORM, false>};
+        for (const void* fn : f)
+            IBR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
+    });
     const long long n2 = n / 2, ld2 = ld / 2;
+    const int grid = (int)std::min<long long>((n2 + PG_TP - 1) / PG_TP, PG_BLOCKS);
+    auto conv = df ? k_gs_pipe<PG_CONVERT, true> : k_gs_pipe<PG_CONVERT, false>;
+    auto sub = df ? k_gs_pipe<PG_SUB, true> : k_gs_pipe<PG_SUB, false>;
+    auto norm = df ? k_gs_pipe<PG_NORM, true> : k_gs_pipe<PG_NORM, false>;
     {
-        ProfScope ps(KID_CONVERT, s, 2.0 * n * 8.0);
-        k_to_df<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w);
+        // first dots and |w|^2 (double-float: w converted in place first)
+        ProfScope ps(KID_MDOT, s, (k + (df ? 2.0 : 1.0)) * n * 8.0);
+        conv<<<grid, PG_THREADS, PG_SMEM, s>>>(n2, V, ld2, k, w, nullptr, nullptr, nullptr, partial, nullptr, nullptr,
+                                               0, nullptr, 0, 0, err);
         IBR_CHECK_LAUNCH();
-    }
-    {
-        ProfScope ps(KID_MDOT, s, (k + 1.0) * n * 8.0);
-        k_df_mdot_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, wd, partial, nullptr);
-        IBR_CHECK_LAUNCH();
-        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, h1);
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, grid, k + 1, h1);
         IBR_CHECK_LAUNCH();
     }
     {
@@ -782,13 +1112,13 @@ void cgs_orthonormalize_df(long long n, long long n_real, const dflt* V, long lo
         IBR_CHECK_LAUNCH();
     }
     {
-        // second pass, skipped inside the kernels unless st[1] != 0
-        ProfScope ps(KID_UPD_MDOT, s, (2.0 * k + 3.0) * n * 8.0);
-        k_df_sub<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, h1, wd, st);
+        // second pass in one kernel, skipped unless st[1] != 0: w -= V h1, then
+        // the dots of the new w (the basis rows re-read from the L2)
+        ProfScope ps(KID_UPD_MDOT, s, (k + 2.0) * n * 8.0);
+        sub<<<grid, PG_THREADS, PG_SMEM, s>>>(n2, V, ld2, k, w, h1, nullptr, st, partial, nullptr, nullptr, 0,
+                                              nullptr, 0, 0, err);
         IBR_CHECK_LAUNCH();
-        k_df_mdot_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, wd, partial, st);
-        IBR_CHECK_LAUNCH();
-        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, hk2);
+        k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, grid, k + 1, hk2);
         IBR_CHECK_LAUNCH();
         k_cgs_state2<<<1, 1, 0, s>>>(hk2, k, st, h2);
         IBR_CHECK_LAUNCH();
@@ -796,16 +1126,46 @@ void cgs_orthonormalize_df(long long n, long long n_real, const dflt* V, long lo
     {
         ProfScope ps(KID_UPD_NORM, s,
                      (k + 2.0) * n * 8.0 + (out32 ? 4.0 * n32 : 0.0) + (out64 ? 8.0 * (n_real - from64) : 0.0));
-        k_df_normalize<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n2, V, ld2, k, h1, h2, st, wd, vout, out32, n32, out64,
-                                                          from64, n_real);
+        norm<<<grid, PG_THREADS, PG_SMEM, s>>>(n2, V, ld2, k, w, h1, h2, st, nullptr, vout, out32, n32, out64, from64,
+                                               n_real, err);
         IBR_CHECK_LAUNCH();
     }
 }
 
-void scale_df(long long n, long long n_real, const double* nrm2, const double* x, dflt* vout, float* out32,
+void scale_df(long long n, long long n_real, const double* inv_norm, const double* x, dflt* vout, float* out32,
               long long n32, double* out64, long long from64, cudaStream_t s) {
     ProfScope ps(KID_SCALE, s, 16.0 * n);
-    k_df_scale<<<blocks_for(n), 256, 0, s>>>(n, nrm2, x, vout, out32, n32, out64, from64, n_real);
+    k_df_scale<<<blocks_for(n), 256, 0, s>>>(n, inv_norm, x, vout, out32, n32, out64, from64, n_real);
+    IBR_CHECK_LAUNCH();
+}
+
+void mgs_orthonormalize(long long n, const double* V, long long ld, int k, double* w, double* vout, float* out32,
+                        long long n32, double* partial, double* h, double* st, cudaStream_t s) {
+    if ((n & 1) || (ld & 1) || k < 1)
+        throw Error{IBR_EINVAL, "modified Gram-Schmidt: even length and leading dimension, k >= 1 required"};
+    if ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(vout)) & 15)
+        throw Error{IBR_EINVAL, "modified Gram-Schmidt: V, w and vout must be 16-byte aligned"};
+    const long long n2 = n / 2;
+    double* pa = partial;
+    double* pb = partial + MG_BLOCKS;
+    {
+        ProfScope ps(KID_MDOT, s, 2.0 * n * 8.0);
+        launch_k(k_mgs_step, dim3(MG_BLOCKS), dim3(RED_THREADS), 0, s, n2, V, (const double*)nullptr, w,
+                 (const double*)nullptr, pa, (double*)nullptr, 0);
+        IBR_CHECK_LAUNCH();
+    }
+    for (int i = 0; i < k; ++i) {
+        // V_i, V_{i+1} (or the norm) and w read, w written
+        ProfScope ps(KID_UPD_MDOT, s, (i + 1 < k ? 4.0 : 3.0) * n * 8.0);
+        const double* Vn = i + 1 < k ? V + (long long)(i + 1) * ld : nullptr;
+        launch_k(k_mgs_step, dim3(MG_BLOCKS), dim3(RED_THREADS), 0, s, n2, V + (long long)i * ld, Vn, w,
+                 (const double*)pa, pb, h + i, 1);
+        IBR_CHECK_LAUNCH();
+        std::swap(pa, pb);
+    }
+    ProfScope ps(KID_UPD_NORM, s, 2.0 * n * 8.0 + (out32 ? 4.0 * n32 : 0.0));
+    launch_k(k_mgs_norm, dim3(MG_BLOCKS), dim3(RED_THREADS), 0, s, n2, (const double*)w, (const double*)pa, st, vout,
+             out32, n32);
     IBR_CHECK_LAUNCH();
 }
 

@@ -101,6 +101,40 @@ __device__ __forceinline__ void pdl_start() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 bool pdl_enabled();
+
+// Bulk asynchronous copies into shared memory with completion counted on an
+// mbarrier (the producer / consumer pipelines of the tensor-core products and
+// of the double-float Gram-Schmidt passes).  Every wait is bounded: after
+// MBAR_WAIT_LIMIT_NS the caller gets false, records an error and stops.
+constexpr unsigned long long MBAR_WAIT_LIMIT_NS = 4000000000ULL;  // 4 s per wait
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > MBAR_WAIT_LIMIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
 template <typename... KArgs, typename... Args>
 void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
@@ -355,17 +389,30 @@ void scale_rsqrt(long long n, const double* inv_norm, const T* x, T* y, T2* out2
 struct __align__(8) dflt {
     float hi, lo;
 };
-// cgs_orthonormalize for a double-float basis V and an FP64 w (converted to
-// double-float in place, w's contents are consumed): the same passes and
-// outputs (h1, h2, hk2, st), vout = the new basis vector; out32
-// (first n32 entries, float) and out64 (entries from64..n_real-1, FP64)
+// Modified Gram-Schmidt of w against the FP64 basis V_0..V_{k-1} (rows of
+// ld doubles) and V_k = the normalised remainder into vout, with an FP32 copy
+// of its first n32 entries (out32, may be NULL): h[0..k) the coefficients,
+// st[2] = |w_perp|^2, st[3] its inverse square root, st[1] = 0.  k + 2
+// launches, two FP64 FMAs per entry and basis vector; w is overwritten.  n and
+// ld even (entries past the system length are a zero pad of w and of every
+// basis vector), V, w, vout 16-byte aligned; partial holds 2 * 608 doubles.
+void mgs_orthonormalize(long long n, const double* V, long long ld, int k, double* w, double* vout, float* out32,
+                        long long n32, double* partial, double* h, double* st, cudaStream_t s);
+// cgs_orthonormalize of the outer FGMRES basis, pipelined on bulk copies: V
+// is FP64 or (df) double-float, 8 bytes per entry either way; w is FP64 on
+// entry (double-float: converted in place, w's contents are consumed); the
+// same passes and outputs (h1, h2, hk2, st); vout = the new basis vector;
+// out32 (first n32 entries, float) and out64 (entries from64..n_real-1, FP64)
 // copies of it for the preconditioner (either may be NULL).  n and ld even
-// (entries n_real..n-1 are a zero pad of w and of every basis vector).
-void cgs_orthonormalize_df(long long n, long long n_real, const dflt* V, long long ld, int k, double* w, dflt* vout,
-                           float* out32, long long n32, double* out64, long long from64, double* partial, double* h1,
-                           double* h2, double* hk2, double* st, cudaStream_t s);
-// vout = x / sqrt(*nrm2) in double-float (n entries), with the same copies
-void scale_df(long long n, long long n_real, const double* nrm2, const double* x, dflt* vout, float* out32,
+// (entries n_real..n-1 are a zero pad of w and of every basis vector), V, w
+// and vout 16-byte aligned, 1 <= k <= 128; partial holds 304 * (k + 1)
+// doubles.  A wait that times out sets *err (device int).
+void cgs_orthonormalize_pipe(bool df, long long n, long long n_real, const void* V, long long ld, int k, double* w,
+                             void* vout, float* out32, long long n32, double* out64, long long from64,
+                             double* partial, double* h1, double* h2, double* hk2, double* st, int* err,
+                             cudaStream_t s);
+// vout = x * (*inv_norm) in double-float (n entries), with the same copies
+void scale_df(long long n, long long n_real, const double* inv_norm, const double* x, dflt* vout, float* out32,
               long long n32, double* out64, long long from64, cudaStream_t s);
 
 // small single-thread kernels for the Arnoldi/Givens bookkeeping (FP64)

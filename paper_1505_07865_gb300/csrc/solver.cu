@@ -198,6 +198,7 @@ struct ibr_grid {
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
     double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr, *shift = nullptr, *means = nullptr;
     double *hk2 = nullptr, *st = nullptr;
+    int* wait_err = nullptr;    // set by a pipelined Gram-Schmidt pass whose wait timed out
     double* host_sc = nullptr;  // pinned
     double* FT = nullptr;
     double* UO = nullptr;
@@ -575,6 +576,7 @@ void free_outer(ibr_grid* G) {
     double** ps[] = {&G->V, &G->Z, &G->b, &G->x, &G->w, &G->H, &G->cs, &G->sn, &G->gv, &G->yv,
                      &G->h1, &G->h2, &G->sc, &G->partial, &G->shift, &G->means, &G->hk2, &G->st, &G->vk64};
     for (double** p : ps) dfree(*p);
+    dfree(G->wait_err);
     G->m_alloc = 0;
     G->have_solution = false;  // x is gone
 }
@@ -1107,6 +1109,10 @@ void ensure_outer(ibr_grid* G, int m) {
     // and w carries the same zero pad entry
     const long long lp = G->len_pad();
     G->V = dalloc<double>((size_t)(m + 1) * lp);
+    // the Gram-Schmidt passes read whole entry pairs: a pad entry (odd len) is zero
+    if (lp > len)
+        IBR_CUDA_TRY(cudaMemset2DAsync(G->V + len, lp * sizeof(double), 0, (lp - len) * sizeof(double), m + 1,
+                                       G->stream));
     G->vk64 = dalloc<double>(len);
     G->Z = dalloc<double>((size_t)m * len);
     G->b = dalloc<double>(len);
@@ -1123,6 +1129,8 @@ void ensure_outer(ibr_grid* G, int m) {
     G->hk2 = dalloc<double>(m + 2);
     G->st = dalloc<double>(4);
     G->sc = dalloc<double>(8);
+    G->wait_err = dalloc<int>(1);
+    IBR_CUDA_TRY(cudaMemsetAsync(G->wait_err, 0, sizeof(int), G->stream));
     G->partial = dalloc<double>((size_t)RED_BLOCKS * std::max(m + 1, 4));
     G->shift = dalloc<double>(4);
     G->means = dalloc<double>(4);
@@ -1182,15 +1190,23 @@ void project_solution(ibr_grid* G, double* x) {
         subtract_means<double>(n, 1, x + (long long)d * n, G->means + d, s);
 }
 
-// The outer Arnoldi basis: FP64 (the default), or double-float with
-// IBR_ARNOLDI=df in the environment (its Gram-Schmidt passes on the FP32
-// pipe, a 48-bit significand; kept for comparison)
-bool arnoldi_double_float() {
-    static const bool df = [] {
+// The outer Arnoldi orthogonalisation.  Default: modified Gram-Schmidt over
+// the FP64 basis, in both precisions (two FP64 FMAs per entry and basis
+// vector; on this part the FP64 pipe, not HBM, bounds these passes).  For
+// comparison, IBR_ARNOLDI in the environment selects classical Gram-Schmidt
+// with reorthogonalisation (CGS2, four FP64 FMAs per entry and basis vector)
+// pipelined on bulk copies: "cgs2" over the FP64 basis, "df" over a
+// double-float basis (pairs of floats, a 48-bit significand, arithmetic on the
+// FP32 pipe).
+enum { ARN_MGS = 0, ARN_CGS2 = 1, ARN_DF = 2 };
+int arnoldi_kind() {
+    static const int kind = [] {
         const char* e = std::getenv("IBR_ARNOLDI");
-        return e && std::string(e) == "df";
+        if (e && std::string(e) == "cgs2") return (int)ARN_CGS2;
+        if (e && std::string(e) == "df") return (int)ARN_DF;
+        return (int)ARN_MGS;
     }();
-    return df;
+    return kind;
 }
 
 // warm: start from the x already in G->x (time stepping), else from x = 0
@@ -1258,13 +1274,14 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
         // its fluid part is written by the same pass
         float* rs32 = G->precision == IBR_MIXED ? G->pc32->rs : nullptr;
         const long long lp = G->len_pad();
-        const bool df = arnoldi_double_float();
+        const int arn = arnoldi_kind();
+        const bool df = arn == ARN_DF;
         // double-float basis: the preconditioner reads the fluid part from
         // rs32 (mixed) or vk64 (FP64), the constraint part from vk64
         const long long from64 = rs32 ? G->nS : 0;
         dflt* Vd = reinterpret_cast<dflt*>(G->V);
         if (df) {
-            scale_df(lp, len, G->sc + 0, G->w, Vd, rs32, G->nS, G->vk64, from64, s);
+            scale_df(lp, len, G->sc + 2, G->w, Vd, rs32, G->nS, G->vk64, from64, s);
         } else if (rs32) {
             scale_rsqrt<double, float>(len, G->sc + 2, G->w, G->V, rs32, G->nS, s);
         } else {
@@ -1277,17 +1294,17 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
             double* Vj = G->V + (long long)j * lp;
             pc_apply(G, df ? G->vk64 : Vj, Zj, true);
             full_matvec(G, Zj, G->w);
-            if (df) {
-                cgs_orthonormalize_df(lp, len, Vd, lp, j + 1, G->w, Vd + (long long)(j + 1) * lp, rs32, G->nS,
-                                      G->vk64, from64, G->partial, G->h1, G->h2, G->hk2, G->st, s);
-            } else if (rs32) {
-                cgs_orthonormalize<double, float>(len, G->V, lp, j + 1, G->w, Vj + lp, rs32, G->nS, G->partial,
-                                                  G->h1, G->h2, G->hk2, G->st, s);
+            // the FP64 basis: the preconditioner reads V_{j+1} itself (and, mixed,
+            // the FP32 copy of its fluid part in rs32)
+            if (arn == ARN_MGS) {
+                mgs_orthonormalize(lp, G->V, lp, j + 1, G->w, Vj + lp, rs32, G->nS, G->partial, G->h1, G->st, s);
             } else {
-                cgs_orthonormalize<double, double>(len, G->V, lp, j + 1, G->w, Vj + lp, nullptr, 0, G->partial,
-                                                   G->h1, G->h2, G->hk2, G->st, s);
+                cgs_orthonormalize_pipe(df, lp, len, G->V, lp, j + 1, G->w, Vj + lp, rs32, G->nS,
+                                        df ? G->vk64 : nullptr, from64, G->partial, G->h1, G->h2, G->hk2, G->st,
+                                        G->wait_err, s);
             }
-            arnoldi_column(G->H, m + 1, G->h1, G->h2, G->st + 2, j, G->cs, G->sn, G->gv, G->sc + 3, G->sc + 4, s);
+            arnoldi_column(G->H, m + 1, G->h1, arn == ARN_MGS ? nullptr : G->h2, G->st + 2, j, G->cs, G->sn, G->gv,
+                           G->sc + 3, G->sc + 4, s);
             k = j + 1;
             info.iters++;
             double est = read_scalar(G, G->sc + 3);
@@ -1302,6 +1319,13 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
             if (est <= target) last_cycle_converged_est = true;
             if (est <= target || info.iters >= o.max_iters) break;
             if (o.time_cap_ms > 0 && now_ms() - t0 > o.time_cap_ms) break;
+        }
+        {
+            // the pipelined Gram-Schmidt passes flag a wait that timed out
+            int werr = 0;
+            IBR_CUDA_TRY(cudaMemcpyAsync(&werr, G->wait_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            IBR_CUDA_TRY(cudaStreamSynchronize(s));
+            if (werr) throw Error{IBR_ECUDA, "a pipelined Gram-Schmidt pass timed out waiting for its copies"};
         }
         hess_solve(G->H, m + 1, G->gv, k, G->yv, s);
         combine<double, double>(len, G->Z, len, k, G->yv, G->x, true, s);

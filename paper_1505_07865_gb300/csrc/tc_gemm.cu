@@ -29,11 +29,7 @@ constexpr int NSTAGE = 3;                 // slices in flight
 constexpr int SLICE_BYTES = GT * GK * 4;  // one 128 x 32 FP32 slice: 16 KB
 constexpr int STAGE_BYTES = 4 * SLICE_BYTES;  // A hi, A lo, B hi, B lo
 constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 256;
-constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ULL;  // 4 s per wait
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t r;
@@ -76,29 +72,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// bounded wait for the phase with the given parity; false after WAIT_LIMIT_NS
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    const unsigned long long t0 = global_ns();
-    for (long long it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 255) == 255 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
-    }
-}
-
 // Operand packing: the TF32 high and low parts of a row-major FP32 matrix
 // (rows a multiple of 128, K a multiple of 32), each 128 x 32 slice stored as
 // one contiguous 16 KB block already in the canonical shared-memory layout
@@ -126,11 +99,6 @@ __global__ void k_pack_tf32(const float* __restrict__ X, int ld, int rows, int K
     *reinterpret_cast<float4*>(lo + off) = l;
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
-}
 
 // One CTA per 128 x 128 tile of C.  Thread 32 (producer) fills a free stage
 // with the four slices of K slice kc (bulk copies, completion counted in
@@ -284,7 +252,11 @@ __global__ void __launch_bounds__(DB_THREADS) k_diag_block(float* __restrict__ A
     for (int kb = 0; kb < 4; ++kb) {
         const int o = kb * 32;
         if (warp == 0) {
+            // lane i holds row i; the finished column j goes through shared
+            // memory (col), so that the updates of the later columns read it
+            // as independent broadcast loads instead of a chain of shuffles
             float r[32], x[32];
+            float* col = T;
 #pragma unroll
             for (int c = 0; c < 32; ++c) r[c] = L[(o + lane) * DB_LD + o + c];
 #pragma unroll
@@ -296,24 +268,33 @@ __global__ void __launch_bounds__(DB_THREADS) k_diag_block(float* __restrict__ A
                 }
                 const float sq = sqrtf(djj);
                 r[j] = lane == j ? sq : (lane > j ? r[j] / sq : r[j]);
+                col[lane] = r[j];
+                __syncwarp();
 #pragma unroll
-                for (int c = j + 1; c < 32; ++c) {
-                    const float lcj = __shfl_sync(FULL, r[j], c);
-                    if (lane >= c) r[c] -= r[j] * lcj;
-                }
+                for (int c = j + 1; c < 32; ++c)
+                    if (lane >= c) r[c] -= r[j] * col[c];
+                __syncwarp();
             }
-            // column `lane` of the inverse by forward substitution
+#pragma unroll
+            for (int c = 0; c < 32; ++c) L[(o + lane) * DB_LD + o + c] = c <= lane ? r[c] : 0.0f;
+            __syncwarp();
+            // column `lane` of the inverse by forward substitution; row rr of the
+            // factor is read from shared memory (broadcast), two partial sums
 #pragma unroll
             for (int rr = 0; rr < 32; ++rr) {
-                float s = lane == rr ? 1.0f : 0.0f;
+                const float* Lr = L + (o + rr) * DB_LD + o;
+                float s0 = lane == rr ? 1.0f : 0.0f, s1 = 0.0f;
 #pragma unroll
-                for (int q = 0; q < rr; ++q) s -= __shfl_sync(FULL, r[q], rr) * x[q];
-                const float lrr = __shfl_sync(FULL, r[rr], rr);
-                x[rr] = rr >= lane ? s / lrr : 0.0f;
+                for (int q = 0; q < rr; ++q) {
+                    if (q & 1)
+                        s1 -= Lr[q] * x[q];
+                    else
+                        s0 -= Lr[q] * x[q];
+                }
+                x[rr] = rr >= lane ? (s0 + s1) / Lr[rr] : 0.0f;
             }
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-                L[(o + lane) * DB_LD + o + c] = c <= lane ? r[c] : 0.0f;
                 W[(kb * 32 + c) * 33 + lane] = x[c];
                 X[(o + c) * DB_LD + o + lane] = x[c];
             }
