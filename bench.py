@@ -460,7 +460,8 @@ def run_ours(args, world, rank, local):
     abi.profile_enable(True)
     prof_total, _, _, _ = timed_solves(abi, torch, G, wl, stream, UOs, 0, args.profile_steps)
     abi.profile_enable(False)
-    prof = abi.profile_read()
+    prof4 = abi.profile_read(with_flops=True)
+    prof = {k: v[:3] for k, v in prof4.items()}
     abi.profile_reset()
 
     # ---- end to end through the C ABI with host buffers ---------------------
@@ -533,6 +534,18 @@ def run_ours(args, world, rank, local):
         roof["note"] = ("finest-level half sweeps in red-black split layout (k_rb_first/k_rb_half, 3 stacked fields): "
                         "in the solve the level's u and f (50 MB) stay in L2 between half sweeps, so ncu in situ "
                         "measures almost no DRAM traffic per launch; the HBM copy rate is the denominator all the same")
+    # the outer orthogonalisation's passes (modified Gram-Schmidt: V_i, V_{i+1}
+    # and w read, w written; two FP64 FMAs per entry): HBM and FP64 fractions
+    orth = None
+    mg = prof4.get("krylov_update_mdot@large")
+    if mg and mg[0] > 0 and os.environ.get("IBR_ARNOLDI", "") == "":
+        gbs = mg[2] / (mg[1] * 1e-3) / 1e9
+        tflops = mg[3] / (mg[1] * 1e-3) / 1e12
+        fp64_peak = 1.19  # TFLOP/s, measured on this machine's GB300 (FMA-throughput probe)
+        orth = {"kernel": "k_mgs_step", "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "fp64_tflops": tflops, "fp64_frac": tflops / fp64_peak,
+                "avg_launch_us": mg[1] / mg[0] * 1000.0, "launches_per_step": mg[0] / args.profile_steps,
+                "algorithmic_bytes_per_launch": mg[2] / mg[0]}
     breakdown = {k: {"launches_per_step": v[0] / args.profile_steps, "ms_per_step": v[1] / args.profile_steps,
                      "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -572,6 +585,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(launches),
         "roofline": roof,
         "tensor_roofline": tensor_roof,
+        "orthogonalisation_roofline": orth,
         "smoother_tiles": [{"level": list(t[:3]), "fields": t[3], "bytes": t[4], "block": [32, t[5]], "kz": t[6]}
                            for t in abi.tuned_smoother_tiles()],
         "vcycle_schedules": [{"finest": list(t[:3]), "levels": t[3], "fields": t[4], "bytes": t[5],

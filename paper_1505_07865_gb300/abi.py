@@ -446,7 +446,7 @@ def profile_reset():
 
 
 def profile_read(with_flops=False):
-    """{kernel class: (launches, total_ms, total_algorithmic_bytes[, tensor_flops])}
+    """{kernel class: (launches, total_ms, total_algorithmic_bytes[, flops])}
     for every class with at least one timed launch."""
     out = {}
     i = 0

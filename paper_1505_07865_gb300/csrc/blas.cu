@@ -930,7 +930,7 @@ __global__ void k_df_scale(long long n, const double* __restrict__ inv_norm, con
 // sum per block; the next pass reduces them itself, in every block and in a
 // fixed order (bitwise the same value everywhere, no separate reduction
 // kernel), and block 0 records the coefficient.
-constexpr int MG_BLOCKS = RED_BLOCKS;  // 4 x 152
+constexpr int MG_BLOCKS = 5 * 152;  // five resident blocks of 256 threads per SM (<= 48 registers)
 
 // the sum of the previous pass' partials (fixed order), broadcast to the block
 __device__ __forceinline__ double mgs_prev(const double* __restrict__ pin, int nblk, double* sh) {
@@ -944,7 +944,7 @@ __device__ __forceinline__ double mgs_prev(const double* __restrict__ pin, int n
 // mode 0: pout = V_0 . w.  mode 1: h = sum(pin), hcol[i] = h (block 0),
 // w -= h V_i, pout = V_{i+1} . w (i + 1 < K) or w . w (i + 1 == K).
 // n2: entry pairs (n even, a zero pad entry), V_i: rows of ld doubles.
-__global__ void __launch_bounds__(RED_THREADS) k_mgs_step(long long n2, const double* __restrict__ Vi,
+__global__ void __launch_bounds__(RED_THREADS, 5) k_mgs_step(long long n2, const double* __restrict__ Vi,
                                                           const double* __restrict__ Vn, double* __restrict__ w,
                                                           const double* __restrict__ pin, double* __restrict__ pout,
                                                           double* __restrict__ hcol, int mode) {
@@ -958,12 +958,33 @@ __global__ void __launch_bounds__(RED_THREADS) k_mgs_step(long long n2, const do
     const double2* v2 = reinterpret_cast<const double2*>(Vi);
     const double2* n2p = reinterpret_cast<const double2*>(Vn);  // NULL: the norm of w
     double2* w2 = reinterpret_cast<double2*>(w);
-    double a0 = 0.0, a1 = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n2;
-         p += (long long)gridDim.x * blockDim.x) {
+    // two pairs per trip (p and p + stride): their loads are issued together
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; p + stride < n2; p += 2 * stride) {
+        const long long q = p + stride;
+        double2 x = w2[p], y = w2[q];
+        if (mode == 1) {
+            const double2 v = __ldcs(v2 + p), vq = __ldcs(v2 + q);  // last use of V_i in this step
+            x.x = fma(-h, v.x, x.x);
+            x.y = fma(-h, v.y, x.y);
+            y.x = fma(-h, vq.x, y.x);
+            y.y = fma(-h, vq.y, y.y);
+            w2[p] = x;
+            w2[q] = y;
+        }
+        const double2 u = mode == 0 ? __ldg(v2 + p) : (n2p ? __ldg(n2p + p) : x);
+        const double2 uq = mode == 0 ? __ldg(v2 + q) : (n2p ? __ldg(n2p + q) : y);
+        a0 = fma(u.x, x.x, a0);
+        a1 = fma(u.y, x.y, a1);
+        b0 = fma(uq.x, y.x, b0);
+        b1 = fma(uq.y, y.y, b1);
+    }
+    if (p < n2) {
         double2 x = w2[p];
         if (mode == 1) {
-            const double2 v = __ldcs(v2 + p);  // last use of V_i in this step
+            const double2 v = __ldcs(v2 + p);
             x.x = fma(-h, v.x, x.x);
             x.y = fma(-h, v.y, x.y);
             w2[p] = x;
@@ -972,14 +993,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_mgs_step(long long n2, const do
         a0 = fma(u.x, x.x, a0);
         a1 = fma(u.y, x.y, a1);
     }
-    double v[1] = {a0 + a1};
+    double v[1] = {(a0 + a1) + (b0 + b1)};
     block_sum<1>(v, sh);
     if (threadIdx.x == 0) pout[blockIdx.x] = sh[0];
 }
 
 // nu^2 = sum(pin) = |w|^2; st[2] = nu^2, st[3] = 1 / nu (block 0);
 // V_K = w / nu, out32 (first n32 entries, float) its FP32 copy
-__global__ void __launch_bounds__(RED_THREADS) k_mgs_norm(long long n2, const double* __restrict__ w,
+__global__ void __launch_bounds__(RED_THREADS, 5) k_mgs_norm(long long n2, const double* __restrict__ w,
                                                           const double* __restrict__ pin, double* __restrict__ st,
                                                           double* __restrict__ vout, float* __restrict__ out32,
                                                           long long n32) {
@@ -1156,7 +1177,7 @@ void mgs_orthonormalize(long long n, const double* V, long long ld, int k, doubl
     }
     for (int i = 0; i < k; ++i) {
         // V_i, V_{i+1} (or the norm) and w read, w written
-        ProfScope ps(KID_UPD_MDOT, s, (i + 1 < k ? 4.0 : 3.0) * n * 8.0);
+        ProfScope ps(KID_UPD_MDOT, s, (i + 1 < k ? 4.0 : 3.0) * n * 8.0, 4.0 * n);
         const double* Vn = i + 1 < k ? V + (long long)(i + 1) * ld : nullptr;
         launch_k(k_mgs_step, dim3(MG_BLOCKS), dim3(RED_THREADS), 0, s, n2, V + (long long)i * ld, Vn, w,
                  (const double*)pa, pb, h + i, 1);

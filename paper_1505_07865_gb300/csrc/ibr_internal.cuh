@@ -395,7 +395,7 @@ struct __align__(8) dflt {
 // st[2] = |w_perp|^2, st[3] its inverse square root, st[1] = 0.  k + 2
 // launches, two FP64 FMAs per entry and basis vector; w is overwritten.  n and
 // ld even (entries past the system length are a zero pad of w and of every
-// basis vector), V, w, vout 16-byte aligned; partial holds 2 * 608 doubles.
+// basis vector), V, w, vout 16-byte aligned; partial holds 2 * 760 doubles.
 void mgs_orthonormalize(long long n, const double* V, long long ld, int k, double* w, double* vout, float* out32,
                         long long n32, double* partial, double* h, double* st, cudaStream_t s);
 // cgs_orthonormalize of the outer FGMRES basis, pipelined on bulk copies: V
