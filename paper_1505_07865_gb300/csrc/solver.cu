@@ -1098,6 +1098,12 @@ void ensure_outer(ibr_grid* G, int m) {
     if (G->m_alloc >= m && G->V && G->len_alloc >= G->len) {
         if (G->w_len != G->len) {
             IBR_CUDA_TRY(cudaMemsetAsync(G->w, 0, ((G->len_alloc + 1) & ~1LL) * sizeof(double), G->stream));
+            // the basis columns now have the new length's stride: their pad
+            // entries (read by the paired Gram-Schmidt passes) must be zero
+            const long long lpn = G->len_pad();
+            if (lpn > G->len)
+                IBR_CUDA_TRY(cudaMemset2DAsync(G->V + G->len, lpn * sizeof(double), 0,
+                                               (lpn - G->len) * sizeof(double), G->m_alloc + 1, G->stream));
             G->w_len = G->len;
         }
         return;
@@ -1283,9 +1289,10 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
         if (df) {
             scale_df(lp, len, G->sc + 2, G->w, Vd, rs32, G->nS, G->vk64, from64, s);
         } else if (rs32) {
-            scale_rsqrt<double, float>(len, G->sc + 2, G->w, G->V, rs32, G->nS, s);
+            // over the padded length: V_0's pad entry is w's (zero)
+            scale_rsqrt<double, float>(lp, G->sc + 2, G->w, G->V, rs32, G->nS, s);
         } else {
-            scale_rsqrt<double, double>(len, G->sc + 2, G->w, G->V, nullptr, 0, s);
+            scale_rsqrt<double, double>(lp, G->sc + 2, G->w, G->V, nullptr, 0, s);
         }
         int k = 0;
         last_cycle_converged_est = false;

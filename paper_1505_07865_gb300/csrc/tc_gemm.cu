@@ -322,20 +322,35 @@ __global__ void __launch_bounds__(DB_THREADS) k_diag_block(float* __restrict__ A
                 if (e < ne) L[(R0 + (e >> 5)) * DB_LD + o + (e & 31)] = pv[u];
             }
             __syncthreads();
-            // trailing update of the lower part at rows, columns >= R0
+            // trailing update of the lower part at rows, columns >= R0: thread
+            // (lane, warp) owns rows warp + 16 a and columns lane + 32 b, an
+            // 8 x 4 register tile, so each panel entry loaded from shared
+            // memory serves four (row) or eight (column) products
             const int tx = lane, ty = warp;
+            float acc[GT / 16][GT / 32];
+#pragma unroll
+            for (int a = 0; a < GT / 16; ++a)
+#pragma unroll
+                for (int b = 0; b < GT / 32; ++b) acc[a][b] = 0.0f;
+#pragma unroll 4
+            for (int q = 0; q < 32; ++q) {
+                float li[GT / 16], lc[GT / 32];
+#pragma unroll
+                for (int a = 0; a < GT / 16; ++a) li[a] = L[(ty + 16 * a) * DB_LD + o + q];
+#pragma unroll
+                for (int b = 0; b < GT / 32; ++b) lc[b] = L[(tx + 32 * b) * DB_LD + o + q];
+#pragma unroll
+                for (int a = 0; a < GT / 16; ++a)
+#pragma unroll
+                    for (int b = 0; b < GT / 32; ++b) acc[a][b] += li[a] * lc[b];
+            }
 #pragma unroll
             for (int a = 0; a < GT / 16; ++a) {
                 const int i = ty + 16 * a;
-                if (i < R0) continue;
 #pragma unroll
                 for (int b = 0; b < GT / 32; ++b) {
                     const int c = tx + 32 * b;
-                    if (c < R0 || c > i) continue;
-                    float acc = 0.0f;
-#pragma unroll 8
-                    for (int q = 0; q < 32; ++q) acc += L[i * DB_LD + o + q] * L[c * DB_LD + o + q];
-                    L[i * DB_LD + c] -= acc;
+                    if (i >= R0 && c >= R0 && c <= i) L[i * DB_LD + c] -= acc[a][b];
                 }
             }
             __syncthreads();
