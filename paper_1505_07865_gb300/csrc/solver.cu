@@ -1196,23 +1196,28 @@ void project_solution(ibr_grid* G, double* x) {
         subtract_means<double>(n, 1, x + (long long)d * n, G->means + d, s);
 }
 
-// The outer Arnoldi orthogonalisation.  Default: modified Gram-Schmidt over
-// the FP64 basis, in both precisions (two FP64 FMAs per entry and basis
-// vector; on this part the FP64 pipe, not HBM, bounds these passes).  For
-// comparison, IBR_ARNOLDI in the environment selects classical Gram-Schmidt
-// with reorthogonalisation (CGS2, four FP64 FMAs per entry and basis vector)
-// pipelined on bulk copies: "cgs2" over the FP64 basis, "df" over a
-// double-float basis (pairs of floats, a 48-bit significand, arithmetic on the
-// FP32 pipe).
+// The outer Arnoldi orthogonalisation, over the FP64 basis in both
+// precisions.  Systems of at least ARN_MGS_MIN_LEN entries: modified
+// Gram-Schmidt (two FP64 FMAs per entry and basis vector; on this part the
+// FP64 pipe, not HBM, bounds these passes, and MGS halves their work).
+// Smaller systems: classical Gram-Schmidt with reorthogonalisation (CGS2, four
+// FMAs) pipelined on bulk copies, three launches per step instead of MGS's
+// k + 2 (there the passes are short and launch latency decides).
+// IBR_ARNOLDI in the environment forces one: "mgs", "cgs2", or "df" (CGS2 over
+// a double-float basis: pairs of floats, a 48-bit significand, arithmetic on
+// the FP32 pipe; for comparison).
 enum { ARN_MGS = 0, ARN_CGS2 = 1, ARN_DF = 2 };
-int arnoldi_kind() {
-    static const int kind = [] {
+constexpr long long ARN_MGS_MIN_LEN = 2000000;
+int arnoldi_kind(long long len) {
+    static const int forced = [] {
         const char* e = std::getenv("IBR_ARNOLDI");
+        if (e && std::string(e) == "mgs") return (int)ARN_MGS;
         if (e && std::string(e) == "cgs2") return (int)ARN_CGS2;
         if (e && std::string(e) == "df") return (int)ARN_DF;
-        return (int)ARN_MGS;
+        return -1;
     }();
-    return kind;
+    if (forced >= 0) return forced;
+    return len >= ARN_MGS_MIN_LEN ? (int)ARN_MGS : (int)ARN_CGS2;
 }
 
 // warm: start from the x already in G->x (time stepping), else from x = 0
@@ -1280,7 +1285,7 @@ int fgmres(ibr_grid* G, const ibr_solve_opts& o, ibr_solve_info& info, bool warm
         // its fluid part is written by the same pass
         float* rs32 = G->precision == IBR_MIXED ? G->pc32->rs : nullptr;
         const long long lp = G->len_pad();
-        const int arn = arnoldi_kind();
+        const int arn = arnoldi_kind(len);
         const bool df = arn == ARN_DF;
         // double-float basis: the preconditioner reads the fluid part from
         // rs32 (mixed) or vk64 (FP64), the constraint part from vk64
