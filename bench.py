@@ -530,10 +530,16 @@ def run_ours(args, world, rank, local):
         "all_launches": {"launches_per_step": kl / args.profile_steps, "achieved_GBps": kbytes / (kms * 1e-3) / 1e9,
                          "share_of_profiled_step": kms / prof_total},
     }
+    if kname == "krylov_update_mdot":
+        roof["note"] = ("outer orthogonalisation passes (modified Gram-Schmidt over the FP64 basis, k_mgs_step: V_i, "
+                        "V_{i+1} and w read, w written, two FP64 FMAs per entry); bound by HBM and the FP64 pipe "
+                        "together, see orthogonalisation_roofline for the FP64 fraction")
     if kname == "mg_smooth_rbgs":
-        roof["note"] = ("finest-level half sweeps in red-black split layout (k_rb_first/k_rb_half, 3 stacked fields): "
-                        "in the solve the level's u and f (50 MB) stay in L2 between half sweeps, so ncu in situ "
-                        "measures almost no DRAM traffic per launch; the HBM copy rate is the denominator all the same")
+        roof["note"] = ("finest-level half sweeps in red-black split layout (k_rb_first/k_rb_half, 3 stacked fields), "
+                        "timed per pre- or post-smoothing sequence of back-to-back launches (two CUDA events per "
+                        "sequence, the average over its launches); in the solve the level's u and f (50 MB) stay in "
+                        "L2 between half sweeps, so ncu in situ measures almost no DRAM traffic per launch; the HBM "
+                        "copy rate is the denominator all the same")
     # the outer orthogonalisation's passes (modified Gram-Schmidt: V_i, V_{i+1}
     # and w read, w written; two FP64 FMAs per entry): HBM and FP64 fractions
     orth = None

@@ -182,9 +182,13 @@ enum KernelId {
 // records CUDA events around the launches in its scope when profiling is on;
 // bytes = the algorithmic bytes those launches move, flops = the
 // floating-point operations they execute (tensor-core products; 0 elsewhere)
+// One timed region of the CUDA-event profile: count back-to-back launches of
+// one kernel class between two events (bytes and flops are their totals), so
+// that a sequence of short dependent launches is timed as it runs, without an
+// event between each pair.
 class ProfScope {
   public:
-    ProfScope(int kid, cudaStream_t s, double bytes, double flops = 0.0);
+    ProfScope(int kid, cudaStream_t s, double bytes, double flops = 0.0, int count = 1);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;
@@ -193,6 +197,7 @@ class ProfScope {
     int kid_;
     cudaStream_t s_;
     double bytes_, flops_;
+    int count_;
     void* a_;
 };
 

@@ -29,6 +29,7 @@ struct Pending {
     int kid;
     cudaEvent_t a, b;
     double bytes, flops;
+    int count;
 };
 struct Acc {
     long long launches = 0;
@@ -76,8 +77,8 @@ static cudaEvent_t get_event() {
     return e;
 }
 
-ProfScope::ProfScope(int kid, cudaStream_t s, double bytes, double flops)
-    : kid_(kid), s_(s), bytes_(bytes), flops_(flops), a_(nullptr) {
+ProfScope::ProfScope(int kid, cudaStream_t s, double bytes, double flops, int count)
+    : kid_(kid), s_(s), bytes_(bytes), flops_(flops), count_(count), a_(nullptr) {
     if (!g_prof) return;
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = get_event();
@@ -90,7 +91,7 @@ ProfScope::~ProfScope() {
     cudaEvent_t b = get_event();
     if (!b) return;
     cudaEventRecord(b, s_);
-    g_pending.push_back({kid_, (cudaEvent_t)a_, b, bytes_, flops_});
+    g_pending.push_back({kid_, (cudaEvent_t)a_, b, bytes_, flops_, count_});
 }
 
 static void drain() {
@@ -99,9 +100,9 @@ static void drain() {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p.a, p.b);
         for (int q = 0; q < 2; ++q) {
-            if (q == 1 && p.bytes < kLargeBytes) break;
+            if (q == 1 && p.bytes < kLargeBytes * p.count) break;
             Acc& a = g_acc[p.kid + q * KID_COUNT];
-            a.launches++;
+            a.launches += p.count;
             a.ms += ms;
             a.bytes += p.bytes;
             a.flops += p.flops;

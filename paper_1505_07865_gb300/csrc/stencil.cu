@@ -1675,11 +1675,11 @@ bool rb_split_ok(const Geo& g, const T* F0, const T* U0, const T* rb_u, const T*
            (((uintptr_t)F0 | (uintptr_t)U0 | (uintptr_t)rb_u | (uintptr_t)rb_f) % al) == 0;
 }
 
+// (the caller's profile scope covers the launch)
 template <typename T>
 void rb_launch_half(const Geo& g, int C, T* us, const T* fs, T kh2, T inv, int color, T* unat, cudaStream_t s) {
     const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
     const int hq = g.n0 / (2 * RB_V);
-    ProfScope ps(KID_RBGS, s, (unat ? 2.5 : 1.5) * C * g.ncell * sizeof(T));
     launch_k(k_rb_half<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, us, fs, g.n0, g.n1, g.n2, nth,
              make_fastdiv(hq), make_fastdiv(g.n1), make_fastdiv(g.n2), kh2, inv, color, unat);
     IBR_CHECK_LAUNCH();
@@ -1708,15 +1708,16 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
             const Geo& g = lev[0];
             const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
             {
-                ProfScope ps(KID_RBGS, s, 2.5 * C * g.ncell * sizeof(T));
+                // the pre-smoothing half sweeps, timed as one back-to-back sequence
+                ProfScope ps(KID_RBGS, s, (1.0 + 3.0 * pre) * C * g.ncell * sizeof(T), 0.0, 2 * pre);
                 launch_k(k_rb_first<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, F0, rb_f, rb_u, g.n0, g.n1, g.n2,
                          nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2), rb_inv);
                 IBR_CHECK_LAUNCH();
-            }
-            rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
-            for (int it = 1; it < pre; ++it) {
-                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, (T*)nullptr, s);
                 rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                for (int it = 1; it < pre; ++it) {
+                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, (T*)nullptr, s);
+                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                }
             }
             const Geo& gc = lev[1];
             const long long ncc = gc.ncell * C;
@@ -1794,9 +1795,14 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
                          g.n2, nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2));
                 IBR_CHECK_LAUNCH();
             }
-            for (int it = 0; it < post; ++it) {
-                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
-                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, it + 1 == post ? U[0] : (T*)nullptr, s);
+            {
+                // the post-smoothing half sweeps (the last one also writes u in the
+                // natural layout), timed as one sequence
+                ProfScope ps(KID_RBGS, s, (3.0 * post + 1.0) * C * g.ncell * sizeof(T), 0.0, 2 * post);
+                for (int it = 0; it < post; ++it) {
+                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, it + 1 == post ? U[0] : (T*)nullptr, s);
+                }
             }
             continue;
         }
