@@ -1037,14 +1037,216 @@ __global__ void __launch_bounds__(RED_THREADS, 5) k_mgs_norm(long long n2, const
     }
 }
 
+// ---- 16-byte vector variants of the Krylov vector kernels ------------------
+// The same operations as k_mdot_norm, k_cgs_sub, k_cgs_normalize, k_norm2,
+// k_scale_rsqrt and k_combine over chunks of W = 16 / sizeof(T) entries (one
+// 128-bit load per vector and chunk, so four times the bytes in flight of the
+// scalar FP32 kernels); the entries past the last whole chunk are handled by
+// block 0.  Used when every vector's base is 16-byte aligned (the host checks).
+template <typename U, int W>
+struct alignas(W * sizeof(U)) PackN {
+    U v[W];
+};
+template <typename T>
+using Pk = PackN<T, 16 / (int)sizeof(T)>;
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_norm_v(long long n, const T* __restrict__ V, long long ld, int k,
+                                                             const T* __restrict__ w, double* __restrict__ partial,
+                                                             const double* __restrict__ st) {
+    if (st && st[1] == 0.0) return;
+    constexpr int W = 16 / (int)sizeof(T);
+    const int K1 = k + 1;
+    const long long nc = n / W, stride = (long long)gridDim.x * blockDim.x;
+    const Pk<T>* w4 = reinterpret_cast<const Pk<T>*>(w);
+    for (int j0 = 0; j0 < K1; j0 += MDOT_CHUNK) {
+        const int nq = min(MDOT_CHUNK, K1 - j0);
+        T tacc[MDOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MDOT_CHUNK; ++q) tacc[q] = T(0);
+        for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += stride) {
+            const Pk<T> wv = w4[c];
+#pragma unroll
+            for (int q = 0; q < MDOT_CHUNK; ++q) {
+                if (q < nq) {
+                    const int j = j0 + q;
+                    const Pk<T> vv = j < k ? reinterpret_cast<const Pk<T>*>(V + (long long)j * ld)[c] : wv;
+                    T a = tacc[q];
+#pragma unroll
+                    for (int e = 0; e < W; ++e) a += vv.v[e] * wv.v[e];
+                    tacc[q] = a;
+                }
+            }
+        }
+        if (blockIdx.x == 0) {
+            for (long long i = nc * W + threadIdx.x; i < n; i += blockDim.x) {
+                const T wi = w[i];
+#pragma unroll
+                for (int q = 0; q < MDOT_CHUNK; ++q) {
+                    const int j = j0 + q;
+                    if (q < nq) tacc[q] += (j < k ? V[(long long)j * ld + i] : wi) * wi;
+                }
+            }
+        }
+        __shared__ double outv[MDOT_CHUNK];
+        block_sum_t<T, MDOT_CHUNK>(tacc, nq, outv);
+        if (threadIdx.x < nq) partial[(long long)blockIdx.x * K1 + j0 + threadIdx.x] = outv[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// w -= sum_j h_j V_j (only when st[1] != 0)
+template <typename T>
+__global__ void k_cgs_sub_v(long long n, const T* __restrict__ V, long long ld, int k, const double* __restrict__ h,
+                            T* __restrict__ w, const double* __restrict__ st) {
+    if (st[1] == 0.0) return;
+    constexpr int W = 16 / (int)sizeof(T);
+    __shared__ T hs[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = (T)h[j];
+    __syncthreads();
+    const long long nc = n / W, stride = (long long)gridDim.x * blockDim.x;
+    Pk<T>* w4 = reinterpret_cast<Pk<T>*>(w);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += stride) {
+        Pk<T> x = w4[c];
+        for (int j = 0; j < k; ++j) {
+            const Pk<T> v = reinterpret_cast<const Pk<T>*>(V + (long long)j * ld)[c];
+            const T hj = hs[j];
+#pragma unroll
+            for (int e = 0; e < W; ++e) x.v[e] -= hj * v.v[e];
+        }
+        w4[c] = x;
+    }
+    if (blockIdx.x == 0) {
+        for (long long i = nc * W + threadIdx.x; i < n; i += blockDim.x) {
+            T x = w[i];
+            for (int j = 0; j < k; ++j) x -= hs[j] * V[(long long)j * ld + i];
+            w[i] = x;
+        }
+    }
+}
+
+// y = s * (x - sum_j h_j V_j) with s = st[3] (k >= 1, h = st[1] ? h2 : h1) or
+// s = *inv_norm (k == 0, no V); out2 (first n2 entries) its T2 copy
+template <typename T, typename T2>
+__global__ void k_scale_sub_v(long long n, const T* __restrict__ V, long long ld, int k, const double* __restrict__ h1,
+                              const double* __restrict__ h2, const double* __restrict__ st,
+                              const double* __restrict__ inv_norm, const T* x, T* y, T2* __restrict__ out2,
+                              long long n2) {
+    constexpr int W = 16 / (int)sizeof(T);
+    __shared__ T hs[128];
+    if (k > 0) {
+        const double* h = st[1] != 0.0 ? h2 : h1;
+        for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = (T)h[j];
+    }
+    __syncthreads();
+    const T sc = (T)(k > 0 ? st[3] : *inv_norm);
+    const long long nc = n / W, stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += stride) {
+        Pk<T> a = reinterpret_cast<const Pk<T>*>(x)[c];
+        for (int j = 0; j < k; ++j) {
+            const Pk<T> v = reinterpret_cast<const Pk<T>*>(V + (long long)j * ld)[c];
+            const T hj = hs[j];
+#pragma unroll
+            for (int e = 0; e < W; ++e) a.v[e] -= hj * v.v[e];
+        }
+#pragma unroll
+        for (int e = 0; e < W; ++e) a.v[e] *= sc;
+        reinterpret_cast<Pk<T>*>(y)[c] = a;
+        if (out2) {
+            const long long i0 = c * W;
+            if (i0 + W <= n2) {
+                PackN<T2, W> o;
+#pragma unroll
+                for (int e = 0; e < W; ++e) o.v[e] = (T2)a.v[e];
+                *reinterpret_cast<PackN<T2, W>*>(out2 + i0) = o;
+            } else {
+#pragma unroll
+                for (int e = 0; e < W; ++e)
+                    if (i0 + e < n2) out2[i0 + e] = (T2)a.v[e];
+            }
+        }
+    }
+    if (blockIdx.x == 0) {
+        for (long long i = nc * W + threadIdx.x; i < n; i += blockDim.x) {
+            T a = x[i];
+            for (int j = 0; j < k; ++j) a -= hs[j] * V[(long long)j * ld + i];
+            a *= sc;
+            y[i] = a;
+            if (out2 && i < n2) out2[i] = (T2)a;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_norm2_v(long long n, const T* __restrict__ w,
+                                                         double* __restrict__ partial) {
+    constexpr int W = 16 / (int)sizeof(T);
+    const long long nc = n / W, stride = (long long)gridDim.x * blockDim.x;
+    T acc = T(0);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += stride) {
+        const Pk<T> x = reinterpret_cast<const Pk<T>*>(w)[c];
+#pragma unroll
+        for (int e = 0; e < W; ++e) acc += x.v[e] * x.v[e];
+    }
+    if (blockIdx.x == 0)
+        for (long long i = nc * W + threadIdx.x; i < n; i += blockDim.x) acc += w[i] * w[i];
+    T v[1] = {acc};
+    __shared__ double o[1];
+    block_sum_t<T, 1>(v, 1, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = o[0];
+}
+
+// x (+)= sum_j y_j Z_j (T == Tz)
+template <typename T>
+__global__ void k_combine_v(long long n, const T* __restrict__ Z, long long ld, int k, const double* __restrict__ y,
+                            T* __restrict__ x, int accumulate) {
+    constexpr int W = 16 / (int)sizeof(T);
+    __shared__ T ys[128];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = (T)y[j];
+    __syncthreads();
+    const long long nc = n / W, stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += stride) {
+        Pk<T> a;
+        if (accumulate) {
+            a = reinterpret_cast<const Pk<T>*>(x)[c];
+        } else {
+#pragma unroll
+            for (int e = 0; e < W; ++e) a.v[e] = T(0);
+        }
+        for (int j = 0; j < k; ++j) {
+            const Pk<T> z = reinterpret_cast<const Pk<T>*>(Z + (long long)j * ld)[c];
+            const T yj = ys[j];
+#pragma unroll
+            for (int e = 0; e < W; ++e) a.v[e] += yj * z.v[e];
+        }
+        reinterpret_cast<Pk<T>*>(x)[c] = a;
+    }
+    if (blockIdx.x == 0) {
+        for (long long i = nc * W + threadIdx.x; i < n; i += blockDim.x) {
+            T a = accumulate ? x[i] : T(0);
+            for (int j = 0; j < k; ++j) a += ys[j] * Z[(long long)j * ld + i];
+            x[i] = a;
+        }
+    }
+}
+
+inline bool vec16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+template <typename T>
+inline bool vec16_basis(const T* V, long long ld) { return vec16(V) && (ld * (long long)sizeof(T)) % 16 == 0; }
+
 }  // namespace
 
 template <typename T, typename T2>
 void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* vout, T2* out2, long long n2,
                         double* partial, double* h1, double* h2, double* hk2, double* st, cudaStream_t s) {
+    // 16-byte vector kernels when every vector is 16-byte aligned
+    const bool v = vec16_basis(V, ld) && vec16(w) && vec16(vout) && (!out2 || vec16(out2));
     {
         ProfScope ps(KID_MDOT, s, (k + 1.0) * n * sizeof(T));
-        k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
+        if (v)
+            k_mdot_norm_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
+        else
+            k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
         IBR_CHECK_LAUNCH();
         k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, h1);
         IBR_CHECK_LAUNCH();
@@ -1057,9 +1259,15 @@ void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* v
     {
         // second pass, skipped inside the kernels unless st[1] != 0
         ProfScope ps(KID_UPD_MDOT, s, 0.0);
-        k_cgs_sub<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, w, st);
-        IBR_CHECK_LAUNCH();
-        k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, st);
+        if (v) {
+            k_cgs_sub_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, w, st);
+            IBR_CHECK_LAUNCH();
+            k_mdot_norm_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, st);
+        } else {
+            k_cgs_sub<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, w, st);
+            IBR_CHECK_LAUNCH();
+            k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, st);
+        }
         IBR_CHECK_LAUNCH();
         k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, hk2);
         IBR_CHECK_LAUNCH();
@@ -1068,7 +1276,11 @@ void cgs_orthonormalize(long long n, const T* V, long long ld, int k, T* w, T* v
     }
     {
         ProfScope ps(KID_UPD_NORM, s, (k + 2.0) * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
-        k_cgs_normalize<T, T2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, h2, st, w, vout, out2, n2);
+        if (v)
+            k_scale_sub_v<T, T2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, h2, st, nullptr, w, vout, out2,
+                                                                    n2);
+        else
+            k_cgs_normalize<T, T2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, h1, h2, st, w, vout, out2, n2);
         IBR_CHECK_LAUNCH();
     }
 }
@@ -1078,7 +1290,10 @@ void cgs_coeffs_only(long long n, const T* V, long long ld, int k, const T* w, d
                      double* h2, double* st, cudaStream_t s) {
     {
         ProfScope ps(KID_MDOT, s, (k + 1.0) * n * sizeof(T));
-        k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
+        if (vec16_basis(V, ld) && vec16(w))
+            k_mdot_norm_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
+        else
+            k_mdot_norm<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, V, ld, k, w, partial, nullptr);
         IBR_CHECK_LAUNCH();
         k_finalize<<<k + 1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, k + 1, h1);
         IBR_CHECK_LAUNCH();
@@ -1091,7 +1306,11 @@ void cgs_coeffs_only(long long n, const T* V, long long ld, int k, const T* w, d
 template <typename T, typename T2>
 void scale_rsqrt(long long n, const double* inv_norm, const T* x, T* y, T2* out2, long long n2, cudaStream_t s) {
     ProfScope ps(KID_SCALE, s, 2.0 * n * sizeof(T) + (out2 ? (double)n2 * sizeof(T2) : 0.0));
-    k_scale_rsqrt<T, T2><<<blocks_for(n), 256, 0, s>>>(n, inv_norm, x, y, out2, n2);
+    if (vec16(x) && vec16(y) && (!out2 || vec16(out2)))
+        k_scale_sub_v<T, T2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, (const T*)nullptr, 0, 0, nullptr, nullptr, nullptr,
+                                                                inv_norm, x, y, out2, n2);
+    else
+        k_scale_rsqrt<T, T2><<<blocks_for(n), 256, 0, s>>>(n, inv_norm, x, y, out2, n2);
     IBR_CHECK_LAUNCH();
 }
 
@@ -1257,7 +1476,10 @@ void update_norm2(long long n, const T* V, long long ld, int k, const double* h,
 template <typename T>
 void norm2(long long n, const T* w, double* partial, double* out, cudaStream_t s) {
     ProfScope ps(KID_NORM2, s, (double)n * sizeof(T));
-    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w, partial);
+    if (vec16(w))
+        k_norm2_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w, partial);
+    else
+        k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, w, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, 1, out);
     IBR_CHECK_LAUNCH();
@@ -1265,6 +1487,13 @@ void norm2(long long n, const T* w, double* partial, double* out, cudaStream_t s
 template <typename T, typename Tz>
 void combine(long long n, const Tz* Z, long long ld, int k, const double* y, T* x, bool accumulate, cudaStream_t s) {
     ProfScope ps(KID_COMBINE, s, (double)n * (k * sizeof(Tz) + (accumulate ? 2 : 1) * sizeof(T)));
+    if constexpr (std::is_same<T, Tz>::value) {
+        if (vec16_basis(Z, ld) && vec16(x) && k <= 128) {
+            k_combine_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, Z, ld, k, y, x, accumulate ? 1 : 0);
+            IBR_CHECK_LAUNCH();
+            return;
+        }
+    }
     k_combine<T, Tz><<<blocks_for(n), 256, 0, s>>>(n, Z, ld, k, y, x, accumulate ? 1 : 0);
     IBR_CHECK_LAUNCH();
 }
