@@ -1230,6 +1230,61 @@ __global__ void k_combine_v(long long n, const T* __restrict__ Z, long long ld, 
     }
 }
 
+// four entries per thread and trip, 16-byte aligned (one or two 16-byte
+// accesses per operand)
+template <typename U>
+struct alignas(16) Q4 {
+    U v[4];
+};
+
+template <typename Ti, typename To>
+__global__ void k_convert_v(long long n, const Ti* __restrict__ x, To* __restrict__ y) {
+    const long long nc = n / 4, stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += stride) {
+        const Q4<Ti> a = reinterpret_cast<const Q4<Ti>*>(x)[c];
+        Q4<To> b;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) b.v[e] = (To)a.v[e];
+        reinterpret_cast<Q4<To>*>(y)[c] = b;
+    }
+    if (blockIdx.x == 0)
+        for (long long i = nc * 4 + threadIdx.x; i < n; i += blockDim.x) y[i] = (To)x[i];
+}
+
+// partial[blk*C + c] = this block's sum of component c (m entries each, m % 4 == 0)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_block_sums_v(long long m, int C, const T* __restrict__ x,
+                                                              double* __restrict__ partial) {
+    const long long mc = m / 4, stride = (long long)gridDim.x * blockDim.x;
+    for (int c = 0; c < C; ++c) {
+        const Q4<T>* xc = reinterpret_cast<const Q4<T>*>(x + (long long)c * m);
+        T t0 = T(0), t1 = T(0);
+        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < mc; q += stride) {
+            const Q4<T> a = xc[q];
+            t0 += a.v[0] + a.v[2];
+            t1 += a.v[1] + a.v[3];
+        }
+        T v[1] = {t0 + t1};
+        __shared__ double o[1];
+        block_sum_t<T, 1>(v, 1, o);
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * C + c] = o[0];
+    }
+}
+
+// component c = blockIdx.y (m % 4 == 0)
+template <typename T>
+__global__ void k_subtract_means_v(long long m, T* __restrict__ x, const double* __restrict__ means) {
+    const T mu = (T)means[blockIdx.y];
+    Q4<T>* xc = reinterpret_cast<Q4<T>*>(x + (long long)blockIdx.y * m);
+    const long long mc = m / 4;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < mc; q += (long long)gridDim.x * blockDim.x) {
+        Q4<T> a = xc[q];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a.v[e] -= mu;
+        xc[q] = a;
+    }
+}
+
 inline bool vec16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 template <typename T>
 inline bool vec16_basis(const T* V, long long ld) { return vec16(V) && (ld * (long long)sizeof(T)) % 16 == 0; }
@@ -1444,7 +1499,10 @@ void vec_scale_copy(long long n, const double* scale_dev, bool invert, const T* 
 template <typename Ti, typename To>
 void vec_convert(long long n, const Ti* x, To* y, cudaStream_t s) {
     ProfScope ps(KID_CONVERT, s, (double)n * (sizeof(Ti) + sizeof(To)));
-    k_convert<Ti, To><<<blocks_for(n), 256, 0, s>>>(n, x, y);
+    if (vec16(x) && vec16(y))
+        k_convert_v<Ti, To><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, y);
+    else
+        k_convert<Ti, To><<<blocks_for(n), 256, 0, s>>>(n, x, y);
     IBR_CHECK_LAUNCH();
 }
 template <typename T>
@@ -1500,7 +1558,10 @@ void combine(long long n, const Tz* Z, long long ld, int k, const double* y, T* 
 template <typename T>
 void block_means(long long m, int C, const T* x, double* partial, double* out, cudaStream_t s) {
     ProfScope ps(KID_BLOCK_MEANS, s, (double)m * C * sizeof(T));
-    k_block_sums<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(m, C, x, partial);
+    if (m % 4 == 0 && vec16(x))
+        k_block_sums_v<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(m, C, x, partial);
+    else
+        k_block_sums<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(m, C, x, partial);
     IBR_CHECK_LAUNCH();
     k_finalize<<<C, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, C, out);
     IBR_CHECK_LAUNCH();
@@ -1510,7 +1571,10 @@ void block_means(long long m, int C, const T* x, double* partial, double* out, c
 template <typename T>
 void subtract_means(long long m, int C, T* x, const double* means, cudaStream_t s) {
     ProfScope ps(KID_SUB_MEANS, s, 2.0 * m * C * sizeof(T));
-    k_subtract_means<T><<<dim3(blocks_for(m), C), 256, 0, s>>>(m, x, means);
+    if (m % 4 == 0 && vec16(x))
+        k_subtract_means_v<T><<<dim3(blocks_for(m / 4), C), 256, 0, s>>>(m, x, means);
+    else
+        k_subtract_means<T><<<dim3(blocks_for(m), C), 256, 0, s>>>(m, x, means);
     IBR_CHECK_LAUNCH();
 }
 
