@@ -273,11 +273,12 @@ constexpr long long MG_TAIL_MAX_CELLS = 4096;
 constexpr size_t MG_TAIL_MAX_SMEM = 200 * 1024;
 // rb_u, rb_f: scratch of C * lev[0].ncell each (or NULL): with them a periodic
 // 3-D finest level (n0 a multiple of 8) of a zero-start V-cycle with pre, post
-// >= 1 runs in red-black split layout (the same arithmetic, bitwise)
+// >= 1 runs in red-black split layout (the same arithmetic, bitwise); rb_u1,
+// rb_f1 (C * lev[1].ncell each, or NULL) do the same for level 1
 template <typename T>
 void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
                double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s,
-               T* rb_u = nullptr, T* rb_f = nullptr);
+               T* rb_u = nullptr, T* rb_f = nullptr, T* rb_u1 = nullptr, T* rb_f1 = nullptr);
 // red-black sweeps of the coarsest-level solve: enough for a preconditioner
 // (the coarsest grid has at most a few hundred cells)
 inline int mg_coarse_sweeps(const Geo& g) {

@@ -67,7 +67,8 @@ template <typename T>
 struct Multigrid {
     std::vector<Geo> lev;
     std::vector<T*> u, f;  // index 0 unused (caller's buffers)
-    T *rb_u = nullptr, *rb_f = nullptr;  // finest level in red-black split layout (periodic 3-D)
+    T *rb_u = nullptr, *rb_f = nullptr;    // finest level in red-black split layout (periodic 3-D)
+    T *rb_u1 = nullptr, *rb_f1 = nullptr;  // level 1 in the same layout
     int cmax = 0;
     int coarse_sweeps = 40;
 
@@ -102,10 +103,16 @@ struct Multigrid {
             rb_u = dalloc<T>((size_t)cmax * g0.ncell);
             rb_f = dalloc<T>((size_t)cmax * g0.ncell);
         }
+        if (g0.d == 3 && !g0.wall && lev.size() > 2 && lev[1].n0 % 8 == 0) {
+            rb_u1 = dalloc<T>((size_t)cmax * lev[1].ncell);
+            rb_f1 = dalloc<T>((size_t)cmax * lev[1].ncell);
+        }
     }
     void release() {
         dfree(rb_u);
         dfree(rb_f);
+        dfree(rb_u1);
+        dfree(rb_f1);
         for (auto& p : u) dfree(p);
         for (auto& p : f) dfree(p);
         u.clear();
@@ -120,7 +127,7 @@ struct Multigrid {
         std::vector<T*> U(u);
         U[0] = u0;
         mg_vcycle<T>(lev.data(), L, U.data(), f.data(), f0, C, fld0, sigma, kappa, zero_start, pre, post,
-                     coarse_sweeps, s, rb_u, rb_f);
+                     coarse_sweeps, s, rb_u, rb_f, rb_u1, rb_f1);
     }
 };
 
@@ -1516,8 +1523,9 @@ long long estimate_grid_bytes(int d, const int* n, int B, const int* Nb, int res
     }
     t += pg(e * (ns + 1) * nS) + pg(e * ns * nS) + 4 * pg(e * nS) + pg(e * d * nc) + 3 * pg(e * nc);
     t += pg(8.0 * RED_BLOCKS * std::max(ns + 1, 4)) + 2 * pg(e * dN) + pg(8.0 * dN);
-    // the finest level's red-black split copies of u and f (periodic 3-D)
+    // the red-black split copies of u and f of the finest level and level 1 (periodic 3-D)
     if (d == 3 && g.n0 % 8 == 0) t += 2 * pg(e * d * nc);
+    if (d == 3 && g.n0 % 16 == 0 && Multigrid<float>::can_coarsen(g)) t += 2 * pg(e * d * nc / 8);
     // markers: positions, lever arms, windows (index, FP64 and FP32 weights),
     // face-major gather lists (at most 4^d faces per marker and component)
     const double win = (double)N * d * d * 4;

@@ -1688,12 +1688,17 @@ void rb_launch_half(const Geo& g, int C, T* us, const T* fs, T kh2, T inv, int c
 template <typename T>
 void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, int C, int fld0, double sigma,
                double kappa, bool zero_start, int pre, int post, int coarse_sweeps, cudaStream_t s, T* rb_u,
-               T* rb_f) {
+               T* rb_f, T* rb_u1, T* rb_f1) {
     auto Fl = [&](int l) -> const T* { return l == 0 ? F0 : Fw[l]; };
-    // periodic 3-D finest level: red-black split layout (conversions folded
-    // into its first and last half sweeps)
-    const bool split = L > 1 && (long long)C * lev[0].ncell < (1LL << 31) &&
-                       rb_split_ok<T>(lev[0], F0, U[0], rb_u, rb_f, zero_start, pre, post);
+    // periodic 3-D: the finest level and the next in red-black split layout
+    // (conversions folded into the first and last half sweeps of each)
+    T* rbu[2] = {rb_u, rb_u1};
+    T* rbf[2] = {rb_f, rb_f1};
+    bool split_l[2];
+    for (int l = 0; l < 2; ++l)
+        split_l[l] = L > l + 1 && (long long)C * lev[l].ncell < (1LL << 31) &&
+                     rb_split_ok<T>(lev[l], Fl(l), U[l], rbu[l], rbf[l], l > 0 || zero_start, pre, post);
+    auto split = [&](int l) { return l < 2 && split_l[l]; };
     // periodic 3-D: the coarse levels on one thread-block cluster per field
     ClusterLevels cl;
     int top = 0;
@@ -1701,29 +1706,31 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
     const bool use_cluster =
         want != -2 && cluster_plan<T>(lev, L, sigma, kappa, want, top, cl) && cluster_ok<T>();
     const int lt = use_cluster ? top : tail_start<T>(lev, L);
-    const T rb_kh2 = (T)(kappa / (lev[0].h * lev[0].h));
-    const T rb_inv = rbgs_inv_diag<3, T>((T)sigma, rb_kh2);
     for (int l = 0; l < lt; ++l) {
-        if (l == 0 && split) {
-            const Geo& g = lev[0];
+        if (split(l)) {
+            const Geo& g = lev[l];
+            T* ru = rbu[l];
+            T* rf = rbf[l];
+            const T rb_kh2 = (T)(kappa / (g.h * g.h));
+            const T rb_inv = rbgs_inv_diag<3, T>((T)sigma, rb_kh2);
             const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
             {
                 // the pre-smoothing half sweeps, timed as one back-to-back sequence
                 ProfScope ps(KID_RBGS, s, (1.0 + 3.0 * pre) * C * g.ncell * sizeof(T), 0.0, 2 * pre);
-                launch_k(k_rb_first<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, F0, rb_f, rb_u, g.n0, g.n1, g.n2,
+                launch_k(k_rb_first<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, Fl(l), rf, ru, g.n0, g.n1, g.n2,
                          nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2), rb_inv);
                 IBR_CHECK_LAUNCH();
-                rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                rb_launch_half<T>(g, C, ru, rf, rb_kh2, rb_inv, 1, (T*)nullptr, s);
                 for (int it = 1; it < pre; ++it) {
-                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, (T*)nullptr, s);
-                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                    rb_launch_half<T>(g, C, ru, rf, rb_kh2, rb_inv, 0, (T*)nullptr, s);
+                    rb_launch_half<T>(g, C, ru, rf, rb_kh2, rb_inv, 1, (T*)nullptr, s);
                 }
             }
-            const Geo& gc = lev[1];
+            const Geo& gc = lev[l + 1];
             const long long ncc = gc.ncell * C;
             ProfScope ps(KID_RESTRICT, s, (2.0 * g.ncell + gc.ncell) * C * sizeof(T));
-            launch_k(k_rb_restrict<T>, dim3(grid_1d(ncc, 256)), dim3(256), 0, s, (const T*)rb_u, (const T*)rb_f,
-                     Fw[1], g.n0, g.n1, g.n2, C, (T)sigma, rb_kh2, make_fastdiv(gc.n0), make_fastdiv(gc.n1),
+            launch_k(k_rb_restrict<T>, dim3(grid_1d(ncc, 256)), dim3(256), 0, s, (const T*)ru, (const T*)rf,
+                     Fw[l + 1], g.n0, g.n1, g.n2, C, (T)sigma, rb_kh2, make_fastdiv(gc.n0), make_fastdiv(gc.n1),
                      make_fastdiv(gc.n2));
             IBR_CHECK_LAUNCH();
             continue;
@@ -1786,13 +1793,17 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
         IBR_CHECK_LAUNCH();
     }
     for (int l = lt - 1; l >= 0; --l) {
-        if (l == 0 && split) {
-            const Geo& g = lev[0];
+        if (split(l)) {
+            const Geo& g = lev[l];
+            T* ru = rbu[l];
+            T* rf = rbf[l];
+            const T rb_kh2 = (T)(kappa / (g.h * g.h));
+            const T rb_inv = rbgs_inv_diag<3, T>((T)sigma, rb_kh2);
             {
                 const int nth = (int)((long long)C * g.ncell / (2 * RB_V));
-                ProfScope ps(KID_PROLONG, s, (1.0 * g.ncell + lev[1].ncell) * C * sizeof(T));
-                launch_k(k_rb_prolong<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, rb_u, (const T*)U[1], g.n0, g.n1,
-                         g.n2, nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2));
+                ProfScope ps(KID_PROLONG, s, (1.0 * g.ncell + lev[l + 1].ncell) * C * sizeof(T));
+                launch_k(k_rb_prolong<T>, dim3(grid_1d(nth, 256)), dim3(256), 0, s, ru, (const T*)U[l + 1], g.n0,
+                         g.n1, g.n2, nth, make_fastdiv(g.n0 / (2 * RB_V)), make_fastdiv(g.n1), make_fastdiv(g.n2));
                 IBR_CHECK_LAUNCH();
             }
             {
@@ -1800,8 +1811,8 @@ void mg_vcycle(const Geo* lev, int L, T* const* U, T* const* Fw, const T* F0, in
                 // natural layout), timed as one sequence
                 ProfScope ps(KID_RBGS, s, (3.0 * post + 1.0) * C * g.ncell * sizeof(T), 0.0, 2 * post);
                 for (int it = 0; it < post; ++it) {
-                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 1, (T*)nullptr, s);
-                    rb_launch_half<T>(g, C, rb_u, rb_f, rb_kh2, rb_inv, 0, it + 1 == post ? U[0] : (T*)nullptr, s);
+                    rb_launch_half<T>(g, C, ru, rf, rb_kh2, rb_inv, 1, (T*)nullptr, s);
+                    rb_launch_half<T>(g, C, ru, rf, rb_kh2, rb_inv, 0, it + 1 == post ? U[l] : (T*)nullptr, s);
                 }
             }
             continue;
@@ -1959,7 +1970,7 @@ void wall_lift(const Geo& g, int a, int side, const double* data, double* b, dou
     template void mg_tune_smoother<T>(const Geo&, int, cudaStream_t);                                       \
     template void mg_tune_cluster<T>(const Geo*, int, T* const*, T* const*, int, int, cudaStream_t);          \
     template void mg_vcycle<T>(const Geo*, int, T* const*, T* const*, const T*, int, int, double, double, bool, \
-                               int, int, int, cudaStream_t, T*, T*);                                        \
+                               int, int, int, cudaStream_t, T*, T*, T*, T*);                                \
     template void ps_divergence<T>(const Geo&, const T*, const T*, T*, double, T*, cudaStream_t);         \
     template void ps_finish<T>(const Geo&, const T*, const T*, const T*, T*, double, double, cudaStream_t);
 IBR_INST(double)

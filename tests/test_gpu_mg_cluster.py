@@ -109,8 +109,8 @@ abi.destroy_grid(G)
 @pytest.mark.parametrize("n,prec", [((64, 48, 32), "MIXED"), ((128, 128, 128), "MIXED"), ((64, 64, 64), "FP64"),
                                     ((96, 96, 96), "MIXED")])
 def test_split_layout_finest_level_equals_natural(tmp_path, n, prec):
-    # one application of P_S (its zero-start V-cycles run the finest level in
-    # red-black split layout) against the same with IBR_MG_SPLIT=0
+    # one application of P_S (its zero-start V-cycles run the finest level and
+    # level 1 in red-black split layout) against the same with IBR_MG_SPLIT=0
     outs = []
     for split in ("1", "0"):
         out = str(tmp_path / f"z_{split}.npy")
